@@ -1,0 +1,765 @@
+/*
+ * qc_oracle.c -- CPU oracle for compressed full-state quantum circuit simulation
+ * (Wu et al., "Full-State Quantum Circuit Simulation by Using Data Compression", SC'19).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call
+ * this file: it is used by tests/, by __graft_entry__.smoke() and by the
+ * cpu_baseline leg of bench.py.  It shares no code, header, table or helper with the
+ * CUDA library; the only thing both sides see is the seeded circuit description.
+ *
+ * Plain, slow, sequential fp64 C.  Compiled with -ffp-contract=off so that every
+ * product and every fma below is exactly the operation written.
+ *
+ * Contents
+ *   1. Bit-plane truncation (Section 4.2, Solution C, Eq. sigbits; interval of Section 3.7)
+ *   2. XOR leading-zero coding with a 2-bit code (Section 4.2, Solution C, step 1)
+ *   3. Chunk image format: modes ZERO/CONST/PERIOD/STREAM/RAW standing in for the
+ *      Zstd stage (Section 3.7 lossless stage, Section 4.2 Solution C step 3)
+ *   4. Gate application on amplitude pairs (Section 3.1, Eq. matrix1 and Eq. matrix2)
+ *   5. Uncompressed state vector simulator (Section 2.1, Eq. 2nrep / Eq. psi)
+ *   6. Compressed simulator: decode -> apply -> encode per work item, with the
+ *      per-timestep error-bound controller (Section 3.1, Eq. totalnbBytes; Section 3.7)
+ *   7. Fidelity (Section 3.8, Eq. idealsim) and its lower bounds
+ *   8. Measurement sampling
+ *
+ * Every function returns ORC_OK (0) or a negative ORC_ERR_* code.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define ORC_OK 0
+#define ORC_ERR_INVALID (-1)
+#define ORC_ERR_OOM (-2)
+#define ORC_ERR_CORRUPT (-4)
+#define ORC_ERR_STATE (-6)
+
+#define ORC_MODE_ZERO 0
+#define ORC_MODE_CONST 1
+#define ORC_MODE_PERIOD 2
+#define ORC_MODE_STREAM 3
+#define ORC_MODE_RAW 4
+#define ORC_NMODES 5
+
+/* Planted-mistake switch used only by the mutation tests: each nonzero value
+ * introduces one plausible bug so the tests can show that some pin catches it. */
+static int g_mutant = 0;
+void orc_set_mutant(int m) { g_mutant = m; }
+
+/* ------------------------------------------------------------------------- */
+/* 1. Bit-plane truncation                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* EXP(eps): the exponent of eps in its IEEE-754 binary64 representation
+ * (Section 4.2, Eq. sigbits; the paper's example is EXP(0.01) = -7). */
+int orc_exp_of(double eps) {
+  uint64_t b;
+  memcpy(&b, &eps, 8);
+  int field = (int)((b >> 52) & 0x7ff);
+  return field - 1023;
+}
+
+/* Sig_Bit_Count = Bit_Count(Sign&Exp) - EXP(eps), with 12 sign+exponent bits for
+ * binary64 (Eq. sigbits).  eps == 0 selects the lossless stage: all 64 bits.
+ * Valid lossy bounds are normal doubles in [2^-52, 1); others are rejected. */
+int orc_sig_bits(double eps) {
+  if (eps == 0.0) return 64;
+  if (!(eps > 0.0) || !(eps < 1.0)) return ORC_ERR_INVALID;
+  int e = orc_exp_of(eps);
+  if (e < -52) return ORC_ERR_INVALID;
+  int s = 12 - e;
+  if (g_mutant == 1) s = 12 - e - 1; /* mutant: one bit too few (the worked example's count) */
+  return s > 64 ? 64 : s;
+}
+
+/* Keep the S leading bits (sign, exponent, S-12 mantissa bits) and zero the rest:
+ * truncation toward zero, so |t| <= |x| and |x - t| < 2^(12-S) |x| for a normal x,
+ * which is the interval (|D(1-delta)|, |D|] of Section 3.7.  A negative zero is
+ * stored as +0 (equal value; the paper is silent on signed zeros). */
+uint64_t orc_truncate(uint64_t bits, int S) {
+  uint64_t t = bits;
+  if (S < 64) {
+    int drop = 64 - S;
+    if (g_mutant == 2) drop = drop + 1; /* mutant: drops one kept bit */
+    t = bits & ~((((uint64_t)1) << drop) - 1);
+  }
+  if (t == 0x8000000000000000ull) t = 0;
+  return t;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 2. XOR leading-zero coding (Solution C step 1)                             */
+/* ------------------------------------------------------------------------- */
+
+/* Number of identical leading bytes of a and its predecessor p (0..8). */
+static int leading_equal_bytes(uint64_t a, uint64_t p) {
+  uint64_t d = a ^ p;
+  int n = 0;
+  for (int k = 7; k >= 0; --k) {
+    if (((d >> (8 * k)) & 0xff) != 0) break;
+    n++;
+  }
+  return n;
+}
+
+/* The 2-bit code: c = min(identical leading bytes, 3). */
+static int xor_code(uint64_t v, uint64_t prev) {
+  int L = leading_equal_bytes(v, prev);
+  if (g_mutant == 3) return L < 2 ? L : 2; /* mutant: caps the code at 2 */
+  return L < 3 ? L : 3;
+}
+
+/* Residual length: the significant bits that the leading bytes did not cover. */
+static int residual_len(int c, int S) {
+  int r = S - 8 * c;
+  return r > 0 ? r : 0;
+}
+
+/* Bit writer over 64-bit words, most significant bit first. */
+typedef struct { uint64_t* w; size_t nwords; uint64_t pos; } bitw;
+
+static void bw_put(bitw* b, uint64_t val, int r) {
+  if (r == 0) return;
+  size_t wi = (size_t)(b->pos >> 6);
+  int off = (int)(b->pos & 63);
+  if (off + r <= 64) {
+    b->w[wi] |= val << (64 - off - r);
+  } else {
+    b->w[wi] |= val >> (off + r - 64);
+    b->w[wi + 1] |= val << (128 - off - r);
+  }
+  b->pos += (uint64_t)r;
+}
+
+static uint64_t bw_get(const uint64_t* w, uint64_t pos, int r) {
+  if (r == 0) return 0;
+  size_t wi = (size_t)(pos >> 6);
+  int off = (int)(pos & 63);
+  uint64_t hi = w[wi] << off; /* first bit now at bit 63 */
+  if (off + r > 64) hi |= w[wi + 1] >> (64 - off);
+  return hi >> (64 - r);
+}
+
+/* ------------------------------------------------------------------------- */
+/* 3. Chunk image                                                             */
+/* ------------------------------------------------------------------------- */
+/*
+ * A chunk holds 2^kc amplitudes = N = 2^(kc+1) binary64 values in the order
+ * re0, im0, re1, im1, ...  Its image is a 16-byte header then a payload whose
+ * length is a multiple of 16 bytes.
+ *   header: [0] mode  [1] S (0 for ZERO)  [2] log2 period P in amplitudes (PERIOD)
+ *           [3] flags = 0   [4..7] payload bytes   [8..11] coded values
+ *           [12..15] residual bits   (all little-endian)
+ *   ZERO   : every truncated value is +0; no payload.
+ *   CONST  : every amplitude equals amplitude 0; payload = its two values (16 B).
+ *   PERIOD : smallest power of two P, 2 <= P < 2^kc, with amp[i] == amp[i-P] for all
+ *            i >= P; payload = XOR coding of the first 2P values.
+ *   STREAM : XOR coding of all N values.
+ *   RAW    : the N truncated values verbatim.
+ * XOR coding layout: the 2-bit codes, four per byte with the first code in the top
+ * two bits, padded to 16 bytes; then the residual bit stream in 64-bit
+ * little-endian words, first bit = bit 63 of word 0, padded to 16 bytes.
+ * The smallest image wins; ties go to the lower mode number.
+ */
+
+static size_t pad16(size_t x) { return (x + 15) & ~(size_t)15; }
+static size_t codes_area(size_t nv) { return pad16((nv + 3) / 4); }
+static size_t resid_area(uint64_t bits) { return (size_t)((bits + 127) / 128) * 16; }
+
+static void put_u32(uint8_t* p, uint32_t v) {
+  p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+}
+static uint32_t get_u32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+static void put_u64(uint8_t* p, uint64_t v) {
+  for (int k = 0; k < 8; ++k) p[k] = (uint8_t)(v >> (8 * k));
+}
+static uint64_t get_u64(const uint8_t* p) {
+  uint64_t v = 0;
+  for (int k = 0; k < 8; ++k) v |= (uint64_t)p[k] << (8 * k);
+  return v;
+}
+
+/* Total residual bits of the XOR coding of t[0..nv). */
+static uint64_t xor_bits(const uint64_t* t, size_t nv, int S) {
+  uint64_t bits = 0, prev = 0;
+  for (size_t j = 0; j < nv; ++j) {
+    bits += (uint64_t)residual_len(xor_code(t[j], prev), S);
+    prev = t[j];
+  }
+  return bits;
+}
+
+/* Writes codes + residual stream of t[0..nv) into payload p (zeroed by caller). */
+static void xor_write(const uint64_t* t, size_t nv, int S, uint8_t* p, uint64_t bits) {
+  size_t ca = codes_area(nv);
+  size_t nwords = resid_area(bits) / 8;
+  uint64_t* w = (uint64_t*)calloc(nwords + 1, 8);
+  bitw b = {w, nwords, 0};
+  uint64_t prev = 0;
+  for (size_t j = 0; j < nv; ++j) {
+    int c = xor_code(t[j], prev);
+    int r = residual_len(c, S);
+    p[j >> 2] |= (uint8_t)(c << (6 - 2 * (int)(j & 3)));
+    if (r > 0) bw_put(&b, (t[j] << (8 * c)) >> (64 - r), r);
+    prev = t[j];
+  }
+  for (size_t k = 0; k < nwords; ++k) put_u64(p + ca + 8 * k, w[k]);
+  free(w);
+}
+
+/* Reads nv values; checks that the residual bits add up. */
+static int xor_read(const uint8_t* p, size_t plen, size_t nv, int S, uint64_t bits, uint64_t* out) {
+  size_t ca = codes_area(nv);
+  size_t ra = resid_area(bits);
+  if (ca + ra != plen) return ORC_ERR_CORRUPT;
+  size_t nwords = ra / 8;
+  uint64_t* w = (uint64_t*)calloc(nwords + 1, 8);
+  for (size_t k = 0; k < nwords; ++k) w[k] = get_u64(p + ca + 8 * k);
+  uint64_t pos = 0, prev = 0;
+  int rc = ORC_OK;
+  for (size_t j = 0; j < nv; ++j) {
+    int c = (p[j >> 2] >> (6 - 2 * (int)(j & 3))) & 3;
+    int r = residual_len(c, S);
+    if (pos + (uint64_t)r > bits) { rc = ORC_ERR_CORRUPT; break; }
+    uint64_t e = bw_get(w, pos, r);
+    pos += (uint64_t)r;
+    uint64_t explicit_bits = r ? ((e << (64 - r)) >> (8 * c)) : 0;
+    uint64_t top = c ? (~(uint64_t)0) << (64 - 8 * c) : 0;
+    uint64_t v = (prev & top) | explicit_bits;
+    out[j] = v;
+    prev = v;
+  }
+  if (rc == ORC_OK && pos != bits) rc = ORC_ERR_CORRUPT;
+  free(w);
+  return rc;
+}
+
+/* Chunk-wide significant bit count: a nonzero subnormal anywhere forces 64 bits
+ * (truncating a subnormal would not keep the relative bound).  Non-finite -> error. */
+int orc_chunk_sig_bits(const uint64_t* v, size_t nv, int S) {
+  int s = S;
+  for (size_t j = 0; j < nv; ++j) {
+    uint64_t e = (v[j] >> 52) & 0x7ff;
+    if (e == 0x7ff) return ORC_ERR_INVALID;
+    if (e == 0 && (v[j] & 0x000fffffffffffffull) != 0) s = 64;
+  }
+  return s;
+}
+
+/* Smallest power-of-two period p = log2 P in [1, kc) (amplitudes), or -1. */
+static int find_period(const uint64_t* t, int kc) {
+  size_t A = (size_t)1 << kc;
+  for (int p = 1; p < kc; ++p) {
+    size_t P = (size_t)1 << p;
+    int ok = 1;
+    for (size_t i = P; i < A && ok; ++i)
+      if (t[2 * i] != t[2 * (i - P)] || t[2 * i + 1] != t[2 * (i - P) + 1]) ok = 0;
+    if (ok) return p;
+  }
+  return -1;
+}
+
+/* Size in bytes of the image in mode m, or 0 if m does not apply. */
+static size_t mode_size(int m, const uint64_t* t, int kc, int S, int period) {
+  size_t N = (size_t)2 << kc;
+  switch (m) {
+    case ORC_MODE_ZERO:
+      for (size_t j = 0; j < N; ++j) if (t[j] != 0) return 0;
+      return 16;
+    case ORC_MODE_CONST:
+      for (size_t j = 2; j < N; j += 2) if (t[j] != t[0] || t[j + 1] != t[1]) return 0;
+      return 32;
+    case ORC_MODE_PERIOD: {
+      if (period < 0) return 0;
+      size_t nv = (size_t)2 << period;
+      return 16 + codes_area(nv) + resid_area(xor_bits(t, nv, S));
+    }
+    case ORC_MODE_STREAM:
+      return 16 + codes_area(N) + resid_area(xor_bits(t, N, S));
+    case ORC_MODE_RAW:
+      return 16 + 8 * N;
+  }
+  return 0;
+}
+
+/* Size of the image the encoder would write for each mode (0 = not applicable).
+ * Inputs are the raw bit patterns of the N values. */
+int orc_mode_sizes(const uint64_t* x, int kc, int S_req, uint64_t* sizes_out) {
+  size_t N = (size_t)2 << kc;
+  int S = orc_chunk_sig_bits(x, N, S_req);
+  if (S < 0) return S;
+  uint64_t* t = (uint64_t*)malloc(N * 8);
+  for (size_t j = 0; j < N; ++j) t[j] = orc_truncate(x[j], S);
+  int period = find_period(t, kc);
+  for (int m = 0; m < ORC_NMODES; ++m) sizes_out[m] = mode_size(m, t, kc, S, period);
+  free(t);
+  return ORC_OK;
+}
+
+/* Encode one chunk (raw bit patterns x[0..N)) with requested bits S_req.
+ * force_mode < 0 selects the smallest image.  Returns the image length or an error. */
+long orc_encode_chunk(const uint64_t* x, int kc, int S_req, int force_mode, uint8_t* out, size_t cap) {
+  if (kc < 0 || kc > 20) return ORC_ERR_INVALID;
+  if (S_req < 13 || S_req > 64) return ORC_ERR_INVALID;
+  size_t N = (size_t)2 << kc;
+  int S = orc_chunk_sig_bits(x, N, S_req);
+  if (S < 0) return S;
+  uint64_t* t = (uint64_t*)malloc(N * 8);
+  for (size_t j = 0; j < N; ++j) t[j] = orc_truncate(x[j], S);
+  int period = find_period(t, kc);
+  size_t best = 0;
+  int mode = -1;
+  if (force_mode >= 0) {
+    if (force_mode >= ORC_NMODES) { free(t); return ORC_ERR_INVALID; }
+    best = mode_size(force_mode, t, kc, S, period);
+    mode = force_mode;
+    if (best == 0) { free(t); return ORC_ERR_INVALID; }
+  } else {
+    for (int m = 0; m < ORC_NMODES; ++m) {
+      size_t s = mode_size(m, t, kc, S, period);
+      if (s != 0 && (mode < 0 || s < best)) { best = s; mode = m; }
+    }
+  }
+  if (best > cap) { free(t); return ORC_ERR_INVALID; }
+  memset(out, 0, best);
+  uint8_t* p = out + 16;
+  uint32_t nv = 0;
+  uint64_t bits = 0;
+  out[0] = (uint8_t)mode;
+  out[1] = (uint8_t)(mode == ORC_MODE_ZERO ? 0 : S);
+  out[2] = (uint8_t)(mode == ORC_MODE_PERIOD ? period : 0);
+  out[3] = 0;
+  switch (mode) {
+    case ORC_MODE_ZERO: break;
+    case ORC_MODE_CONST:
+      nv = 2;
+      put_u64(p, t[0]);
+      put_u64(p + 8, t[1]);
+      break;
+    case ORC_MODE_PERIOD:
+    case ORC_MODE_STREAM:
+      nv = (uint32_t)(mode == ORC_MODE_PERIOD ? ((size_t)2 << period) : N);
+      bits = xor_bits(t, nv, S);
+      xor_write(t, nv, S, p, bits);
+      break;
+    case ORC_MODE_RAW:
+      nv = (uint32_t)N;
+      for (size_t j = 0; j < N; ++j) put_u64(p + 8 * j, t[j]);
+      break;
+  }
+  put_u32(out + 4, (uint32_t)(best - 16));
+  put_u32(out + 8, nv);
+  put_u32(out + 12, (uint32_t)bits);
+  free(t);
+  return (long)best;
+}
+
+/* Decode an image into N raw bit patterns. */
+int orc_decode_chunk(const uint8_t* img, size_t len, int kc, uint64_t* out) {
+  if (len < 16 || kc < 0 || kc > 20) return ORC_ERR_CORRUPT;
+  size_t N = (size_t)2 << kc;
+  int mode = img[0], S = img[1], lp = img[2];
+  uint32_t plen = get_u32(img + 4), nv = get_u32(img + 8), bits = get_u32(img + 12);
+  if (img[3] != 0 || (size_t)plen + 16 != len || (plen & 15) != 0) return ORC_ERR_CORRUPT;
+  if (mode != ORC_MODE_ZERO && (S < 13 || S > 64)) return ORC_ERR_CORRUPT;
+  const uint8_t* p = img + 16;
+  switch (mode) {
+    case ORC_MODE_ZERO:
+      if (S != 0 || lp != 0 || plen != 0 || nv != 0 || bits != 0) return ORC_ERR_CORRUPT;
+      memset(out, 0, N * 8);
+      return ORC_OK;
+    case ORC_MODE_CONST:
+      if (lp != 0 || plen != 16 || nv != 2 || bits != 0) return ORC_ERR_CORRUPT;
+      for (size_t j = 0; j < N; j += 2) { out[j] = get_u64(p); out[j + 1] = get_u64(p + 8); }
+      return ORC_OK;
+    case ORC_MODE_PERIOD: {
+      if (lp < 1 || lp >= kc || nv != ((uint32_t)2 << lp)) return ORC_ERR_CORRUPT;
+      int rc = xor_read(p, plen, nv, S, bits, out);
+      if (rc) return rc;
+      for (size_t j = nv; j < N; ++j) out[j] = out[j - nv];
+      return ORC_OK;
+    }
+    case ORC_MODE_STREAM:
+      if (lp != 0 || nv != N) return ORC_ERR_CORRUPT;
+      return xor_read(p, plen, nv, S, bits, out);
+    case ORC_MODE_RAW:
+      if (lp != 0 || nv != N || bits != 0 || plen != 8 * N) return ORC_ERR_CORRUPT;
+      for (size_t j = 0; j < N; ++j) out[j] = get_u64(p + 8 * j);
+      return ORC_OK;
+  }
+  return ORC_ERR_CORRUPT;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 4. Gate application (Eq. matrix1, Eq. matrix2)                             */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  int32_t target;
+  int32_t kind; /* caller's hint; the oracle ignores it */
+  uint64_t ctrl_mask;
+  uint64_t ctrl_vals;
+  double u[8]; /* u00r u00i u01r u01i u10r u10i u11r u11i */
+} orc_gate;
+
+/* One real component of a complex 2x2 row times (a, b): the sum of four products,
+ * taken in the order written; a product whose coefficient is exactly zero is left
+ * out, the first kept product is rounded once and each later one is added with a
+ * single fused multiply-add.  With no product kept the result is +0. */
+static double row_sum(double c1, double x1, double c2, double x2, double c3, double x3, double c4, double x4) {
+  double cs[4] = {c1, c2, c3, c4}, xs[4] = {x1, x2, x3, x4};
+  double acc = 0.0;
+  int have = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (cs[k] == 0.0) continue;
+    if (!have) { acc = cs[k] * xs[k]; have = 1; }
+    else acc = fma(cs[k], xs[k], acc);
+  }
+  return acc;
+}
+
+/* (a, b) <- U (a, b) for one amplitude pair: a has bit t = 0, b has bit t = 1. */
+static void apply_pair(const double* u, double* a, double* b) {
+  double ar = a[0], ai = a[1], br = b[0], bi = b[1];
+  double u00r = u[0], u00i = u[1], u01r = u[2], u01i = u[3];
+  double u10r = u[4], u10i = u[5], u11r = u[6], u11i = u[7];
+  if (g_mutant == 4) { double s = u01r; u01r = u10r; u10r = s; s = u01i; u01i = u10i; u10i = s; } /* mutant: U transposed */
+  if (g_mutant == 5) u01i = -u01i; /* mutant: wrong sign */
+  a[0] = row_sum(u00r, ar, -u00i, ai, u01r, br, -u01i, bi);
+  a[1] = row_sum(u00r, ai, u00i, ar, u01r, bi, u01i, br);
+  b[0] = row_sum(u10r, ar, -u10i, ai, u11r, br, -u11i, bi);
+  b[1] = row_sum(u10r, ai, u10i, ar, u11r, bi, u11i, br);
+  if (g_mutant == 6) b[1] = row_sum(u10r, ai, u10i, ar, u11r, bi, 0.0, br); /* mutant: dropped term */
+}
+
+/* Gate checks: target in range, controls inside the register and not on the
+ * target, control values inside the mask, finite entries, and U^H U = I within 1e-12. */
+int orc_gate_check(const orc_gate* g, int n) {
+  if (g->target < 0 || g->target >= n) return ORC_ERR_INVALID;
+  uint64_t all = (n >= 64) ? ~(uint64_t)0 : ((((uint64_t)1) << n) - 1);
+  if (g->ctrl_mask & ~all) return ORC_ERR_INVALID;
+  if ((g->ctrl_mask >> g->target) & 1) return ORC_ERR_INVALID;
+  if (g->ctrl_vals & ~g->ctrl_mask) return ORC_ERR_INVALID;
+  for (int k = 0; k < 8; ++k) if (!isfinite(g->u[k])) return ORC_ERR_INVALID;
+  /* columns of U: c0 = (u00, u10), c1 = (u01, u11) */
+  double c0r[2] = {g->u[0], g->u[4]}, c0i[2] = {g->u[1], g->u[5]};
+  double c1r[2] = {g->u[2], g->u[6]}, c1i[2] = {g->u[3], g->u[7]};
+  double n0 = 0, n1 = 0, dr = 0, di = 0;
+  for (int k = 0; k < 2; ++k) {
+    n0 += c0r[k] * c0r[k] + c0i[k] * c0i[k];
+    n1 += c1r[k] * c1r[k] + c1i[k] * c1i[k];
+    dr += c0r[k] * c1r[k] + c0i[k] * c1i[k]; /* <c0|c1> */
+    di += c0r[k] * c1i[k] - c0i[k] * c1r[k];
+  }
+  if (fabs(n0 - 1.0) > 1e-12 || fabs(n1 - 1.0) > 1e-12 || fabs(dr) > 1e-12 || fabs(di) > 1e-12) return ORC_ERR_INVALID;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 5. Uncompressed state vector (interleaved re, im; index bit k = qubit k)   */
+/* ------------------------------------------------------------------------- */
+
+void orc_sv_init(double* psi, int n) {
+  size_t A = (size_t)1 << n;
+  memset(psi, 0, 2 * A * sizeof(double));
+  psi[0] = 1.0;
+}
+
+int orc_sv_apply(double* psi, int n, const orc_gate* g) {
+  int rc = orc_gate_check(g, n);
+  if (rc) return rc;
+  size_t A = (size_t)1 << n, tb = (size_t)1 << g->target;
+  for (size_t i = 0; i < A; ++i) {
+    if (i & tb) continue;
+    if ((i & g->ctrl_mask) != g->ctrl_vals) continue;
+    apply_pair(g->u, psi + 2 * i, psi + 2 * (i | tb));
+  }
+  return ORC_OK;
+}
+
+int orc_sv_run(double* psi, int n, const orc_gate* gates, size_t ng) {
+  for (size_t k = 0; k < ng; ++k) {
+    int rc = orc_sv_apply(psi, n, gates + k);
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}
+
+/* Sum of |a_i|^2 in index order (Eq. psi), each term fma(re, re, im*im). */
+double orc_sv_norm2(const double* psi, int n) {
+  size_t A = (size_t)1 << n;
+  double s = 0.0;
+  for (size_t i = 0; i < A; ++i) s += fma(psi[2 * i], psi[2 * i], psi[2 * i + 1] * psi[2 * i + 1]);
+  return s;
+}
+
+/* <x|y> = sum conj(x_i) y_i in index order. */
+void orc_sv_inner(const double* x, const double* y, int n, double* out2) {
+  size_t A = (size_t)1 << n;
+  double re = 0.0, im = 0.0;
+  for (size_t i = 0; i < A; ++i) {
+    double xr = x[2 * i], xi = x[2 * i + 1], yr = y[2 * i], yi = y[2 * i + 1];
+    re += xr * yr + xi * yi;
+    im += xr * yi - xi * yr;
+  }
+  out2[0] = re;
+  out2[1] = im;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 8. Measurement (one shot, splitmix64 draw)                                 */
+/* ------------------------------------------------------------------------- */
+
+/* splitmix64 (Steele, Lea, Flood 2014): one output for one 64-bit state. */
+uint64_t orc_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* u = (splitmix64(seed) >> 11) 2^-53; outcome = smallest i whose running sum of
+ * |a|^2 reaches u * total.  prob = |a_outcome|^2 / total. */
+int orc_sv_measure(const double* psi, int n, uint64_t seed, uint64_t* outcome, double* prob) {
+  size_t A = (size_t)1 << n;
+  double total = orc_sv_norm2(psi, n);
+  double u = (double)(orc_splitmix64(seed) >> 11) * (1.0 / 9007199254740992.0);
+  double target = u * total, run = 0.0;
+  size_t pick = A - 1;
+  for (size_t i = 0; i < A; ++i) {
+    double p = fma(psi[2 * i], psi[2 * i], psi[2 * i + 1] * psi[2 * i + 1]);
+    run += p;
+    if (run >= target && p > 0.0) { pick = i; break; }
+  }
+  *outcome = pick;
+  *prob = fma(psi[2 * pick], psi[2 * pick], psi[2 * pick + 1] * psi[2 * pick + 1]) / total;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 6. Compressed simulator                                                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  uint64_t gates, encoded_bytes, max_encoded_bytes, raw_bytes, inflight_bytes, chunks_by_mode[8];
+  double min_ratio, eps_current, fid_lb_sum, fid_lb_prod;
+  int64_t eps_switch_gate;
+  int32_t S_current, level;
+} orc_stats;
+
+typedef struct {
+  int n, b, kc, ladder, S_cur, level, nlevels;
+  double levels[8];
+  double eps_max, tau;
+  uint64_t budget, thresh, inflight, nchunks, E, Emax, gates;
+  int64_t switch_gate;
+  double lb_sum, lb_prod;
+  uint8_t** img;
+  uint32_t* len;
+  int poisoned;
+} orc_csim;
+
+void orc_csim_destroy(orc_csim* s);
+
+static int csim_store(orc_csim* s, uint64_t c, const uint64_t* vals) {
+  size_t cap = 16 + 8 * ((size_t)2 << s->kc);
+  uint8_t* buf = (uint8_t*)malloc(cap);
+  long L = orc_encode_chunk(vals, s->kc, s->S_cur, -1, buf, cap);
+  if (L < 0) { free(buf); return (int)L; }
+  uint8_t* fit = (uint8_t*)realloc(buf, (size_t)L);
+  if (fit) buf = fit;
+  if (s->img[c]) { s->E -= s->len[c]; free(s->img[c]); }
+  s->img[c] = buf;
+  s->len[c] = (uint32_t)L;
+  s->E += (uint64_t)L;
+  return ORC_OK;
+}
+
+/* ladder: 0 = jump from lossless straight to eps_max, 1 = the paper's ladder
+ * 1e-5, 1e-4, ... one level per gate up to eps_max (Section 3.7).
+ * Blocks hold 2^block_log2 amplitudes (Section 3.1); each block is coded as
+ * 2^(block_log2 - chunk_log2) independent chunks. */
+orc_csim* orc_csim_create(int n, int block_log2, int chunk_log2, double eps_max, uint64_t budget, double tau,
+                          int ladder) {
+  if (n < 1 || n > 40 || block_log2 < 0 || chunk_log2 < 0) return NULL;
+  if (eps_max != 0.0 && orc_sig_bits(eps_max) < 0) return NULL;
+  orc_csim* s = (orc_csim*)calloc(1, sizeof(orc_csim));
+  s->n = n;
+  s->b = block_log2 < n ? block_log2 : n;
+  s->kc = chunk_log2 < s->b ? chunk_log2 : s->b;
+  s->eps_max = eps_max;
+  s->tau = tau;
+  s->budget = budget;
+  s->thresh = (uint64_t)floor(tau * (double)budget);
+  /* Eq. totalnbBytes with r = 1: two decompressed blocks are in flight. */
+  s->inflight = (uint64_t)2 << (s->b + 4);
+  s->ladder = ladder;
+  s->S_cur = 64;
+  s->switch_gate = -1;
+  s->lb_sum = 0.0;
+  s->lb_prod = 1.0;
+  static const double paper_levels[5] = {1e-5, 1e-4, 1e-3, 1e-2, 1e-1};
+  s->nlevels = 0;
+  if (eps_max > 0.0) {
+    if (ladder == 1)
+      for (int k = 0; k < 5; ++k) if (paper_levels[k] < eps_max) s->levels[s->nlevels++] = paper_levels[k];
+    s->levels[s->nlevels++] = eps_max;
+  }
+  s->nchunks = (uint64_t)1 << (n - s->kc);
+  s->img = (uint8_t**)calloc(s->nchunks, sizeof(uint8_t*));
+  s->len = (uint32_t*)calloc(s->nchunks, sizeof(uint32_t));
+  size_t N = (size_t)2 << s->kc;
+  uint64_t* vals = (uint64_t*)calloc(N, 8);
+  for (uint64_t c = 0; c < s->nchunks; ++c) {
+    memset(vals, 0, N * 8);
+    if (c == 0) { double one = 1.0; memcpy(&vals[0], &one, 8); }
+    if (csim_store(s, c, vals)) { free(vals); orc_csim_destroy(s); return NULL; }
+  }
+  free(vals);
+  s->Emax = s->E;
+  return s;
+}
+
+void orc_csim_destroy(orc_csim* s) {
+  if (!s) return;
+  for (uint64_t c = 0; c < s->nchunks; ++c) free(s->img[c]);
+  free(s->img);
+  free(s->len);
+  free(s);
+}
+
+/* Error-bound controller, evaluated before each gate (Section 3.7): the memory the
+ * gate needs is nbBytes = E + W (Eq. totalnbBytes, r = 1), with E the current sum of
+ * image bytes and W two decompressed blocks.  If nbBytes exceeds floor(tau * budget)
+ * the bound is relaxed: the jump ladder goes from lossless to eps_max at once, the
+ * paper's ladder steps one level per gate.  The bound never tightens. */
+static void controller(orc_csim* s) {
+  if (s->nlevels == 0) return;
+  if (s->E + s->inflight <= s->thresh) return;
+  if (s->level >= s->nlevels) return;
+  if (s->ladder == 1) s->level += 1;
+  else s->level = s->nlevels;
+  s->S_cur = orc_sig_bits(s->levels[s->level - 1]);
+  if (s->switch_gate < 0) s->switch_gate = (int64_t)s->gates;
+}
+
+int orc_csim_apply(orc_csim* s, const orc_gate* g) {
+  if (s->poisoned) return ORC_ERR_STATE;
+  int rc = orc_gate_check(g, s->n);
+  if (rc) return rc;
+  int kc = s->kc, t = g->target;
+  size_t A = (size_t)1 << kc, N = 2 * A;
+  controller(s);
+  uint64_t hi_mask = g->ctrl_mask >> kc, hi_vals = g->ctrl_vals >> kc;
+  uint64_t lo_mask = g->ctrl_mask & (A - 1), lo_vals = g->ctrl_vals & (A - 1);
+  uint64_t* x0 = (uint64_t*)malloc(N * 8);
+  uint64_t* x1 = (uint64_t*)malloc(N * 8);
+  for (uint64_t q = 0; q < s->nchunks && rc == ORC_OK; ++q) {
+    if ((q & hi_mask) != hi_vals) continue;
+    if (t < kc) {
+      rc = orc_decode_chunk(s->img[q], s->len[q], kc, x0);
+      if (rc) break;
+      double* d = (double*)x0;
+      for (size_t i = 0; i < A; ++i) {
+        if ((i >> t) & 1) continue;
+        if ((i & lo_mask) != lo_vals) continue;
+        apply_pair(g->u, d + 2 * i, d + 2 * (i | ((size_t)1 << t)));
+      }
+      rc = csim_store(s, q, x0);
+    } else {
+      uint64_t qb = (uint64_t)1 << (t - kc);
+      if (q & qb) continue;
+      uint64_t q1 = q | qb;
+      rc = orc_decode_chunk(s->img[q], s->len[q], kc, x0);
+      if (!rc) rc = orc_decode_chunk(s->img[q1], s->len[q1], kc, x1);
+      if (rc) break;
+      double *d0 = (double*)x0, *d1 = (double*)x1;
+      for (size_t i = 0; i < A; ++i) {
+        if ((i & lo_mask) != lo_vals) continue;
+        apply_pair(g->u, d0 + 2 * i, d1 + 2 * i);
+      }
+      rc = csim_store(s, q, x0);
+      if (!rc) rc = csim_store(s, q1, x1);
+    }
+  }
+  free(x0);
+  free(x1);
+  if (rc) { s->poisoned = 1; return rc; }
+  if (s->S_cur < 64) {
+    double delta = ldexp(1.0, 12 - s->S_cur); /* 2^EXP(eps): the bound each value keeps */
+    s->lb_sum += delta;
+    s->lb_prod *= (1.0 - delta);
+  }
+  s->gates += 1;
+  if (s->E > s->Emax) s->Emax = s->E;
+  return ORC_OK;
+}
+
+int orc_csim_run(orc_csim* s, const orc_gate* gates, size_t ng) {
+  for (size_t k = 0; k < ng; ++k) {
+    int rc = orc_csim_apply(s, gates + k);
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}
+
+/* Decodes the whole state into interleaved doubles. */
+int orc_csim_amplitudes(const orc_csim* s, double* out) {
+  size_t N = (size_t)2 << s->kc;
+  for (uint64_t c = 0; c < s->nchunks; ++c) {
+    int rc = orc_decode_chunk(s->img[c], s->len[c], s->kc, (uint64_t*)(out + c * N));
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}
+
+/* Copies chunk c's image; *len receives its length. */
+int orc_csim_image(const orc_csim* s, uint64_t c, uint8_t* out, size_t cap, uint64_t* len) {
+  if (c >= s->nchunks) return ORC_ERR_INVALID;
+  *len = s->len[c];
+  if (s->len[c] > cap) return ORC_ERR_INVALID;
+  memcpy(out, s->img[c], s->len[c]);
+  return ORC_OK;
+}
+
+/* Replaces chunk c's image (used to start the oracle from a stored state). */
+int orc_csim_set_image(orc_csim* s, uint64_t c, const uint8_t* img, size_t len) {
+  if (c >= s->nchunks) return ORC_ERR_INVALID;
+  size_t N = (size_t)2 << s->kc;
+  uint64_t* tmp = (uint64_t*)malloc(N * 8);
+  int rc = orc_decode_chunk(img, len, s->kc, tmp);
+  free(tmp);
+  if (rc) return rc;
+  uint8_t* b = (uint8_t*)malloc(len);
+  memcpy(b, img, len);
+  s->E -= s->len[c];
+  free(s->img[c]);
+  s->img[c] = b;
+  s->len[c] = (uint32_t)len;
+  s->E += len;
+  return ORC_OK;
+}
+
+void orc_csim_stats(const orc_csim* s, orc_stats* st) {
+  memset(st, 0, sizeof(*st));
+  st->gates = s->gates;
+  st->encoded_bytes = s->E;
+  st->max_encoded_bytes = s->Emax;
+  st->raw_bytes = (uint64_t)16 << s->n;
+  st->inflight_bytes = s->inflight;
+  for (uint64_t c = 0; c < s->nchunks; ++c) st->chunks_by_mode[s->img[c][0] & 7] += 1;
+  st->min_ratio = (double)st->raw_bytes / (double)s->Emax;
+  st->eps_current = s->level ? s->levels[s->level - 1] : 0.0;
+  st->fid_lb_sum = 1.0 - s->lb_sum;
+  st->fid_lb_prod = s->lb_prod;
+  st->eps_switch_gate = s->switch_gate;
+  st->S_current = s->S_cur;
+  st->level = s->level;
+}
+
+uint64_t orc_csim_nchunks(const orc_csim* s) { return s->nchunks; }
+int orc_csim_chunk_log2(const orc_csim* s) { return s->kc; }
+int orc_csim_block_log2(const orc_csim* s) { return s->b; }

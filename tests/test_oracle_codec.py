@@ -1,0 +1,258 @@
+"""Pins of the oracle's codec against facts that do not come from the oracle.
+
+Section 4.2 (Solution C): bit-plane truncation to Sig_Bit_Count = 12 - EXP(eps) bits
+(Eq. sigbits), XOR leading-zero coding with a 2-bit code; Section 3.7: the decoded
+value lies in (|D(1 - delta)|, |D|]; Section 4.2 worked example (3.9921875 -> 3.96875).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "codec_hand_streams.json")
+LEVELS = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5]
+
+
+def np_truncate(bits: np.ndarray, S: int) -> np.ndarray:
+    """Independent numpy restatement used only to check the oracle: keep the S
+    leading bits, store -0 as +0."""
+    bits = bits.astype(np.uint64)
+    if S < 64:
+        mask = np.uint64((0xFFFFFFFFFFFFFFFF << (64 - S)) & 0xFFFFFFFFFFFFFFFF)
+        bits = bits & mask
+    bits = np.where(bits == np.uint64(0x8000000000000000), np.uint64(0), bits)
+    return bits
+
+
+# ----------------------------------------------------------- Eq. sigbits --- #
+
+def test_exp_of_paper_example():
+    # Section 4.2: "EXP(0.01) = -7"
+    assert O.exp_of(0.01) == -7
+
+
+@pytest.mark.parametrize("eps", LEVELS)
+def test_sig_bits_matches_frexp(eps):
+    # frexp gives eps = f 2^e with f in [0.5, 1): the IEEE exponent is e - 1.
+    f, e = math.frexp(eps)
+    assert 0.5 <= f < 1.0
+    assert O.exp_of(eps) == e - 1
+    assert O.sig_bits(eps) == 12 - (e - 1)
+
+
+def test_sig_bits_table_and_lossless():
+    # 12 sign+exponent bits for binary64 (Eq. sigbits): S = 16, 19, 22, 26, 29.
+    assert [O.sig_bits(e) for e in LEVELS] == [16, 19, 22, 26, 29]
+    assert O.sig_bits(0.0) == 64
+    for bad in (1.0, 2.0, -1e-3, float("nan"), float("inf"), 1e-300):
+        assert O.sig_bits(bad) < 0
+
+
+def test_worked_example_float32():
+    # Section 4.2: 3.9921875 kept to 15 leading bits -> 3.96875, relative error 0.005871.
+    # Read in float32 (9 sign+exponent bits): 15 bits = 6 mantissa bits.  numpy only:
+    f = np.array([3.9921875], dtype=np.float32).view(np.uint32)
+    t = (f & np.uint32(0xFFFFFFFF << (32 - 15) & 0xFFFFFFFF)).view(np.float32)[0]
+    assert float(t) == 3.96875
+    assert round((3.9921875 - 3.96875) / 3.9921875, 6) == 0.005871
+
+
+def test_worked_example_oracle():
+    # The same value in binary64 keeps the same 6 mantissa bits with S = 12 + 6.
+    t6 = O.truncate_double(3.9921875, 12 + 6)
+    assert t6 == 3.96875
+    assert round((3.9921875 - t6) / 3.9921875, 6) == 0.005871
+    # Eq. sigbits itself gives S = 12 - EXP(0.01) = 19 (7 mantissa bits): within the bound.
+    t7 = O.truncate_double(3.9921875, O.sig_bits(0.01))
+    assert t7 == 3.984375
+    assert (3.9921875 - t7) / 3.9921875 < 0.01
+
+
+# --------------------------------------------------- truncation interval --- #
+
+def _random_doubles(rng, n):
+    mant = rng.integers(0, 1 << 52, size=n, dtype=np.uint64)
+    expo = rng.integers(1, 2047, size=n).astype(np.uint64)
+    sign = rng.integers(0, 2, size=n).astype(np.uint64)
+    return (sign << np.uint64(63)) | (expo << np.uint64(52)) | mant
+
+
+@pytest.mark.parametrize("eps", LEVELS)
+def test_truncation_interval(eps):
+    rng = np.random.default_rng(7)
+    S = O.sig_bits(eps)
+    bits = _random_doubles(rng, 4000)
+    edge = np.array([0x0010000000000000, 0x7FEFFFFFFFFFFFFF, 0x3FFFFFFFFFFFFFFF, 0x3FF0000000000000,
+                     0xBFF0000000000001], dtype=np.uint64)
+    bits = np.concatenate([bits, edge])
+    t = np.array([O.truncate(int(b), S) for b in bits], dtype=np.uint64)
+    assert np.array_equal(t, np_truncate(bits, S))
+    x = bits.view(np.float64)
+    tv = t.view(np.float64)
+    assert np.all(np.signbit(x) == np.signbit(tv))
+    assert np.all(np.abs(tv) <= np.abs(x))
+    # |x - t| < 2^(12-S) |x| <= eps |x|   (Section 3.7: D' in (|D(1-delta)|, |D|])
+    rel = np.abs(x - tv) / np.abs(x)
+    assert np.all(rel < 2.0 ** (12 - S))
+    assert np.all(rel < eps)
+
+
+def test_truncation_float32_sweep():
+    # every float32 exponent with random and extreme mantissas, widened to binary64
+    rng = np.random.default_rng(3)
+    exps = np.arange(1, 255, dtype=np.uint32)
+    mant = np.concatenate([rng.integers(0, 1 << 23, size=(254, 6), dtype=np.uint32),
+                           np.full((254, 1), (1 << 23) - 1, dtype=np.uint32),
+                           np.zeros((254, 1), dtype=np.uint32)], axis=1)
+    f32 = ((exps[:, None] << np.uint32(23)) | mant).ravel().view(np.float32)
+    x = f32.astype(np.float64)
+    for eps in LEVELS:
+        S = O.sig_bits(eps)
+        t = np.array([O.truncate(int(b), S) for b in x.view(np.uint64)], dtype=np.uint64).view(np.float64)
+        rel = np.abs(x - t) / np.abs(x)
+        assert np.all(rel < eps) and np.all(np.abs(t) <= np.abs(x))
+
+
+def test_zero_and_negative_zero():
+    for S in (16, 26, 64):
+        assert O.truncate(0, S) == 0
+        assert O.truncate(0x8000000000000000, S) == 0
+
+
+# ---------------------------------------------------- hand-derived images --- #
+
+def _expected_image(case) -> bytes:
+    h = case["header"]
+    head = bytes([h["mode"], h["S"], h["log2P"], 0]) + h["payload_bytes"].to_bytes(4, "little") + \
+        h["n_values"].to_bytes(4, "little") + h["resid_bits"].to_bytes(4, "little")
+    payload = b""
+    if "codes_byte_bits" in case:
+        codes = bytes([int(case["codes_byte_bits"], 2)]).ljust(16, b"\0")
+        bits = "".join(case["residual_bits"])
+        nwords = (len(bits) + 127) // 128 * 2
+        bits = bits.ljust(64 * nwords, "0")
+        words = [int(bits[64 * k: 64 * (k + 1)], 2) for k in range(nwords)]
+        payload = codes + b"".join(w.to_bytes(8, "little") for w in words)
+    elif "payload_hex_le_words" in case:
+        payload = b"".join(int(w, 16).to_bytes(8, "little") for w in case["payload_hex_le_words"])
+    assert len(payload) == h["payload_bytes"]
+    return head + payload
+
+
+@pytest.mark.parametrize("case", json.load(open(GOLDEN))["cases"], ids=lambda c: c["name"])
+def test_hand_derived_image(case):
+    vals = np.array([int(v, 16) for v in case["values_hex"]], dtype=np.uint64)
+    img = O.encode_chunk(vals, case["kc"], case["S"])
+    assert img[0] == case["expect_mode"]
+    assert img == _expected_image(case)
+    dec = O.decode_chunk(img, case["kc"]).view(np.uint64)
+    assert np.array_equal(dec, np_truncate(vals, case["S"] if case["expect_mode"] else 64))
+
+
+# ------------------------------------------------------------ round trips --- #
+
+def _chunks(rng, kc):
+    A = 1 << kc
+    yield "normal", (rng.standard_normal(A) + 1j * rng.standard_normal(A)) * 2.0 ** -8
+    yield "sparse", np.where(rng.random(A) < 0.1, rng.standard_normal(A) + 1j * rng.standard_normal(A), 0)
+    yield "const", np.full(A, 0.25 - 0.125j)
+    yield "zero", np.zeros(A, dtype=np.complex128)
+    if kc >= 2:
+        P = 1 << int(rng.integers(1, kc))
+        base = rng.standard_normal(P) + 1j * rng.standard_normal(P)
+        yield "period", np.tile(base, A // P)
+    yield "phases", np.exp(1j * rng.uniform(0, 2 * np.pi, A)) / np.sqrt(A)
+    sub = rng.standard_normal(A) + 0j
+    sub[rng.integers(0, A)] = 5e-320
+    yield "subnormal", sub
+    neg = rng.standard_normal(A) + 0j
+    neg[::3] = -0.0
+    yield "negzero", neg
+
+
+@pytest.mark.parametrize("kc", [0, 1, 2, 3, 5, 8, 10])
+def test_roundtrip(kc):
+    rng = np.random.default_rng(100 + kc)
+    for name, a in _chunks(rng, kc):
+        bits = np.ascontiguousarray(a, dtype=np.complex128).view(np.uint64)
+        has_sub = np.any(((bits >> np.uint64(52)) & np.uint64(0x7FF) == 0) & (bits & np.uint64((1 << 52) - 1) != 0))
+        for S in (64, 29, 26, 22, 19, 16):
+            img = O.encode_chunk(a, kc, S)
+            assert len(img) % 16 == 0
+            eff = 64 if has_sub else S
+            if img[0] != 0:
+                assert img[1] == eff, (name, S)
+            dec = O.decode_chunk(img, kc).view(np.uint64)
+            assert np.array_equal(dec, np_truncate(bits, eff)), (name, kc, S)
+
+
+def _smallest_period(t: np.ndarray, kc: int):
+    amps = t.reshape(-1, 2)
+    for p in range(1, kc):
+        P = 1 << p
+        if all(np.array_equal(amps[i], amps[i % P]) for i in range(1 << kc)):
+            return p
+    return None
+
+
+@pytest.mark.parametrize("kc", [1, 2, 4, 6])
+def test_selector_is_minimal_and_modes_apply(kc):
+    rng = np.random.default_rng(kc)
+    for name, a in _chunks(rng, kc):
+        for S in (64, 26, 16):
+            bits = np.ascontiguousarray(a, dtype=np.complex128).view(np.uint64)
+            t = np_truncate(bits, S if name != "subnormal" else 64)
+            applicable = {
+                0: bool(np.all(t == 0)),
+                1: bool(np.all(t.reshape(-1, 2) == t[:2])),
+                2: _smallest_period(t, kc) is not None,
+                3: True,
+                4: True,
+            }
+            sizes = {}
+            for m in range(5):
+                if applicable[m]:
+                    sizes[m] = len(O.encode_chunk(a, kc, S, force_mode=m))
+                else:
+                    with pytest.raises(O.OracleError):
+                        O.encode_chunk(a, kc, S, force_mode=m)
+            auto = O.encode_chunk(a, kc, S)
+            best = min(sizes.values())
+            assert len(auto) == best
+            assert auto[0] == min(m for m, s in sizes.items() if s == best)
+            if applicable[2]:
+                assert O.encode_chunk(a, kc, S, force_mode=2)[2] == _smallest_period(t, kc)
+            assert sizes[4] == 16 + 16 * (1 << kc)
+
+
+def test_subnormal_forces_full_width():
+    a = np.full(8, 0.5 + 0.25j)
+    a[3] = 1e-310 + 0j
+    img = O.encode_chunk(a, 3, 26)
+    assert img[1] == 64
+    assert np.array_equal(O.decode_chunk(img, 3), a)
+
+
+def test_nonfinite_rejected():
+    for bad in (np.inf, np.nan):
+        a = np.zeros(4, dtype=np.complex128)
+        a[1] = bad
+        with pytest.raises(O.OracleError):
+            O.encode_chunk(a, 2, 26)
+
+
+def test_corrupt_images_rejected():
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(64) + 1j * rng.standard_normal(64)
+    img = bytearray(O.encode_chunk(a, 6, 26))
+    for pos, val in ((0, 9), (1, 5), (3, 1), (4, 16), (8, 7), (12, 3)):
+        bad = bytearray(img)
+        bad[pos] = (bad[pos] + val) & 0xFF
+        with pytest.raises(O.OracleError):
+            O.decode_chunk(bytes(bad), 6)
+    with pytest.raises(O.OracleError):
+        O.decode_chunk(bytes(img[:-16]), 6)
