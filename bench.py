@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: compressed-state amplitude updates/s on the 30-qubit random circuit.
+
+Workload (the configuration the metric is quoted on): random circuit sampling on a
+5 x 6 grid (30 qubits), a Hadamard layer then layers of CZ on a rotating coupler
+class plus one random gate from {sqrt(X), sqrt(Y), T} per qubit; complex128 state in
+blocks of 2^20 amplitudes (chunks of 2^10), lossless first and lossy at pointwise
+relative bound 1e-4 once the state passes 90 % of the budget (raw/4).  Synthetic,
+seeded circuits; the compressed state (several GB) is larger than L2, so no flush.
+
+One step = one circuit layer (about 42 gates) on the evolving compressed state: every
+gate runs the whole path (classify, decode, apply, controller, truncate, XOR-code,
+mode select, page commit, stats).  Warm-up steps are the first layers after the
+Hadamard layer; timed steps follow.  `value` is device-timed (CUDA events on the
+simulator's stream); `e2e` times the same calls from the host, including the
+per-step read-back of the statistics.  Fidelity is measured against the uncompressed
+complex128 state vector run on the same GPU (same gates).
+
+--impl reference times the CPU oracle (tests' reference implementation) on a
+bounded sample of the same workload on the host cores.
+With torchrun (N > 1) every rank runs an independent replica (the method does not
+shard across GPUs here); value = all ranks' updates / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1911_04034_gb300 import circuits as Cc  # noqa: E402
+
+METRIC = "compressed-state amplitude updates/s"
+UNIT = "amp-updates/s"
+ROWS, COLS, BLOCK_LOG2, CHUNK_LOG2, SEED = 5, 6, 20, 10, 2024
+
+# dram__bytes_read.sum + dram__bytes_write.sum per k_gate launch from the last ncu
+# capture, with the hash of the kernel sources it was taken on (None = no capture).
+NCU_TRAFFIC = {"bytes_per_launch": None, "source_sha": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("paper_1911_04034_gb300/csrc/kernels.cu", "paper_1911_04034_gb300/csrc/device.cuh"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def layers_of(gates: np.ndarray, n: int, depth: int) -> list[np.ndarray]:
+    """Splits an rcs() gate list into [Hadamard layer, layer 1, ..., layer depth]."""
+    out = [gates[:n]]
+    pos = n
+    for layer in range(depth):
+        m = len(Cc.grid_edges(ROWS, COLS, n, layer % 4)) + n
+        out.append(gates[pos:pos + m])
+        pos += m
+    assert pos == len(gates)
+    return out
+
+
+def amp_updates(gates: np.ndarray, n: int, kc: int) -> int:
+    """Amplitudes in the chunks each gate touches (controls on chunk-index bits
+    remove chunks), summed over the gates."""
+    tot = 0
+    for g in gates:
+        hi = int(g["ctrl_mask"]) >> kc
+        tot += (1 << n) >> bin(hi).count("1")
+    return tot
+
+
+def peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args) -> dict | None:
+    import torch
+
+    from paper_1911_04034_gb300 import qcsim
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    n = ROWS * COLS
+    depth = max(20, 1 + args.warmup + 2 * args.steps)
+    gates = Cc.rcs(ROWS, COLS, depth, seed=SEED + rank)
+    layers = layers_of(gates, n, depth)
+    raw = 16 << n
+    stream = torch.cuda.Stream()
+    sim = qcsim.Sim(n, BLOCK_LOG2, args.eps, chunk_log2=CHUNK_LOG2, budget=raw // 4, pool_bytes=raw + raw // 8,
+                    stream=stream)
+    kc = sim.chunk_log2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up: the Hadamard layer and W circuit layers
+    sim.apply_circuit(layers[0])
+    for L in layers[1:1 + args.warmup]:
+        sim.apply_circuit(L)
+    st0 = sim.stats()
+    # timed region (device time, CUDA events on the simulator's stream)
+    timed = layers[1 + args.warmup: 1 + args.warmup + args.steps]
+    clocks = Clocks(local)
+    sim.set_timing(True)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for L in timed:
+        sim.apply_circuit(L)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    tm = sim.timing()
+    sim.set_timing(False)
+    st1 = sim.stats()
+    updates = st1["amp_updates"] - st0["amp_updates"]
+    assert updates == amp_updates(np.concatenate(timed), n, kc)
+    # end to end through the public API: host gate records in, statistics read back
+    e2e_layers = layers[1 + args.warmup + args.steps: 1 + args.warmup + 2 * args.steps]
+    barrier()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for L in e2e_layers:
+        sim.apply_circuit(L)
+        _ = sim.stats()
+        h2d += L.nbytes
+        d2h += qcsim.C.sizeof(qcsim.Stats)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_updates = amp_updates(np.concatenate(e2e_layers), n, kc)
+    st2 = sim.stats()
+    # fidelity against the uncompressed complex128 state vector on the same GPU
+    applied = np.concatenate(layers[: 1 + args.warmup + 2 * args.steps])
+    fid = None
+    sv_rate = None
+    if not args.no_sv:
+        sv = qcsim.StateVector(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sv.apply_circuit(applied)
+        sv_s = time.perf_counter() - t0
+        sv_rate = len(applied) * float(1 << n) / sv_s
+        ref = torch.empty(2 << n, dtype=torch.float64, device="cuda")
+        ref_ptr = sv.data_ptr()
+        # the state vector's own device buffer serves as the reference
+        f = qcsim.lib().sim_fidelity(sim._h, qcsim.C.c_void_p(ref_ptr), 1, qcsim.C.byref(F := qcsim.C.c_double()),
+                                     None, None)
+        qcsim._check(f, "sim_fidelity")
+        fid = float(F.value)
+        del ref
+        sv.close()
+    ms_max = ms
+    upd_total = updates
+    if dist is not None:
+        t = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max = float(tmax[0])
+        upd_total = float(t[1])
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    kernel_ms_avg = tm["gate_kernel_ms"] / max(1, tm["launches"])
+    bytes_per_launch = (tm["bytes_read"] + tm["bytes_written"]) / max(1, tm["launches"])
+    achieved = bytes_per_launch / (kernel_ms_avg * 1e-3) / 1e9 if kernel_ms_avg > 0 else 0.0
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_sha"] == kernel_sha() else None
+    out = {
+        "metric": METRIC,
+        "value": upd_total / (ms_max * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"random circuit {ROWS}x{COLS} grid, 30 qubits, layers {1 + args.warmup}-{args.warmup + args.steps} "
+                        f"timed; eps {args.eps}; blocks 2^{BLOCK_LOG2}, chunks 2^{kc}",
+            "n_qubits": n, "block_log2": BLOCK_LOG2, "chunk_log2": kc, "eps": args.eps,
+            "budget_bytes": raw // 4, "pool_bytes": raw + raw // 8, "gates_timed": int(sum(len(x) for x in timed)),
+            "l2": "no flush: compressed state larger than L2",
+            "parallelism": "replicas" if world > 1 else "1 gpu",
+        },
+        "compression_ratio": st1["ratio"],
+        "min_compression_ratio": st2["min_ratio"],
+        "fidelity": fid,
+        "fidelity_lb_sum": st2["fidelity_lb_sum"],
+        "eps_switch_gate": st2["eps_switch_gate"],
+        "encoded_gb": st1["encoded_bytes"] / 1e9,
+        "chunks_by_mode": st1["chunks_by_mode"][:5],
+        "uncompressed_value": sv_rate,
+        "roofline": {
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": hbm,
+            "unit": "GB/s",
+            "frac": (achieved / hbm) if hbm else None,
+            "traffic": traffic,
+            "kernel": "k_gate",
+            "kernel_ms_avg": kernel_ms_avg,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else None,
+        },
+        "gpu_launches": 2 * tm["launches"],
+        "clocks": clk,
+        "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // max(1, len(e2e_layers)),
+                "d2h_bytes_per_step": d2h // max(1, len(e2e_layers))},
+    }
+    return out
+
+
+def cpu_sample(eps: float, n: int = 20, warm_layers: int = 3, timed_layers: int = 2, budget_s: float = 25.0):
+    """The oracle on the host: same circuit family on a 4 x 5 grid (20 qubits), same
+    bound and budget rule; times whole layers after a warm-up until budget_s."""
+    import oracle as O
+
+    rows, cols = 4, 5
+    depth = warm_layers + timed_layers
+    gates = Cc.rcs(rows, cols, depth, seed=SEED)
+    out = [gates[:n]]
+    pos = n
+    for layer in range(depth):
+        m = len(Cc.grid_edges(rows, cols, n, layer % 4)) + n
+        out.append(gates[pos:pos + m])
+        pos += m
+    cs = O.CSim(n, BLOCK_LOG2, CHUNK_LOG2, eps, (16 << n) // 4)
+    for L in out[: 1 + warm_layers]:
+        cs.apply(L)
+    t0 = time.perf_counter()
+    upd = 0
+    k = 0
+    for L in out[1 + warm_layers:]:
+        cs.apply(L)
+        upd += amp_updates(L, n, min(CHUNK_LOG2, n))
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    s = time.perf_counter() - t0
+    return {"value": upd / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"CPU oracle, random circuit 4x5 grid (20 qubits), eps {eps}, budget raw/4, "
+                      f"{k} layers after the Hadamard layer + {warm_layers} warm-up layers, single thread",
+            "seconds": s}
+
+
+def run_reference(args) -> dict | None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle as O
+
+    n, rows, cols = 20, 4, 5
+    depth = args.warmup + args.steps
+    gates = Cc.rcs(rows, cols, depth, seed=SEED)
+    L = [gates[:n]]
+    pos = n
+    for layer in range(depth):
+        m = len(Cc.grid_edges(rows, cols, n, layer % 4)) + n
+        L.append(gates[pos:pos + m])
+        pos += m
+    cs = O.CSim(n, BLOCK_LOG2, CHUNK_LOG2, args.eps, (16 << n) // 4)
+    for x in L[: 1 + args.warmup]:
+        cs.apply(x)
+    t0 = time.perf_counter()
+    upd = 0
+    for x in L[1 + args.warmup:]:
+        cs.apply(x)
+        upd += amp_updates(x, n, min(CHUNK_LOG2, n))
+    s = time.perf_counter() - t0
+    v = upd / s
+    sample = (f"CPU oracle, random circuit 4x5 grid (20 qubits), eps {args.eps}, {args.steps} timed layers "
+              f"after the Hadamard layer + {args.warmup} warm-up layers, single thread")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": sample, "n_qubits": n, "eps": args.eps},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--no-sv", action="store_true", help="skip the uncompressed comparator and fidelity")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_gpu(args)
+    if out is None:
+        return
+    if not args.no_cpu_baseline and out["n_gpus"] == 1:
+        out["cpu_baseline"] = cpu_sample(args.eps)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * qcsim.h -- C ABI of libqcsim: full-state quantum circuit simulation with the state
+ * vector kept compressed in GPU memory (one GB300, sm_103a).
+ *
+ * Method: Wu et al., "Full-State Quantum Circuit Simulation by Using Data
+ * Compression" (SC'19).  The state of n qubits is 2^n complex128 amplitudes
+ * (Section 2.1, Eq. 2nrep).  It is split into blocks of 2^block_log2 amplitudes
+ * (Section 3.1), each stored compressed; a block is coded as independent chunks of
+ * 2^chunk_log2 amplitudes.  Every gate decodes the chunks it touches, applies the 2x2
+ * unitary to each amplitude pair that differs only in the target bit and satisfies
+ * the controls (Section 3.1, Eq. matrix1 and Eq. matrix2), and re-encodes them with
+ * the hybrid codec: a lossless stage first, then the error-bounded lossy coder
+ * (bit-plane truncation to 12 - EXP(eps) bits, Eq. sigbits, plus XOR leading-zero
+ * coding, Section 4.2 Solution C) once the compressed state plus two decompressed
+ * blocks (Eq. totalnbBytes) no longer fit in tau * budget (Section 3.7).
+ *
+ * Conventions
+ *  - Every call returns a sim_status.  No exception crosses the ABI.
+ *  - Buffers and out-parameters belong to the caller; the library copies what it
+ *    keeps.  The sim_t handle owns all device memory it allocates and frees it in
+ *    sim_destroy.
+ *  - Work is queued on the handle's CUDA stream (sim_set_stream; default: the legacy
+ *    default stream).  Calls that return data to the host synchronise that stream.
+ *  - Amplitude index bit k is qubit k.  Amplitudes are interleaved (re, im) doubles.
+ *  - SIM_ERR_INVALID: bad arguments; the state is unchanged.
+ *  - A failure found on the device while a gate runs (SIM_ERR_OOM: the page pool ran
+ *    dry; SIM_ERR_CORRUPT: an image failed its checks or a value was not finite)
+ *    poisons the handle: that call, or the next call that synchronises, returns the
+ *    error and every later call returns SIM_ERR_STATE.
+ *  - sim_last_error() returns a message for the last failure on this thread.
+ */
+#ifndef QCSIM_H
+#define QCSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SIM_OK = 0,
+  SIM_ERR_INVALID = -1,
+  SIM_ERR_OOM = -2,
+  SIM_ERR_CUDA = -3,
+  SIM_ERR_CORRUPT = -4,
+  SIM_ERR_TIMEOUT = -5,
+  SIM_ERR_STATE = -6
+} sim_status;
+
+/* One gate (Eq. matrix1; with controls, Eq. matrix2).  The unitary acts on the pair
+ * (a_i, a_{i | 2^target}) for every index i with bit `target` clear and
+ * (i & ctrl_mask) == ctrl_vals.  u = u00r, u00i, u01r, u01i, u10r, u10i, u11r, u11i,
+ * computed on the host (the device never evaluates a trigonometric function).
+ * `kind` is a hint (0 general, 1 diagonal, 2 permutation) and is ignored.
+ * Rejected with SIM_ERR_INVALID: target outside [0, n), a control outside the
+ * register or on the target, ctrl_vals outside ctrl_mask, a non-finite entry, or
+ * |U^H U - I| > 1e-12 in any entry.  88 bytes, natural alignment. */
+typedef struct sim_gate {
+  int32_t target;
+  int32_t kind;
+  uint64_t ctrl_mask;
+  uint64_t ctrl_vals;
+  double u[8];
+} sim_gate;
+
+typedef struct sim sim_t;
+
+/* Run statistics (Table 2 columns: compression ratio, fidelity bound, time split). */
+typedef struct sim_stats_t {
+  uint64_t gates;             /* gates applied */
+  uint64_t encoded_bytes;     /* sum of chunk image bytes now (sum of sizeof(CB_i), Eq. totalnbBytes) */
+  uint64_t max_encoded_bytes; /* largest encoded_bytes seen after any gate */
+  uint64_t raw_bytes;         /* 2^(n+4) */
+  uint64_t inflight_bytes;    /* two decompressed blocks, 2 * 2^(block_log2 + 4) */
+  uint64_t chunks_by_mode[8]; /* chunk images by mode: ZERO CONST PERIOD STREAM RAW */
+  uint64_t pool_bytes;        /* page arena size */
+  uint64_t pages_in_use_bytes;/* pages holding images now */
+  uint64_t peak_pages_bytes;  /* most pages in use after any gate */
+  uint64_t device_bytes;      /* all device memory the handle owns */
+  uint64_t amp_updates;       /* amplitudes in chunks decoded and re-encoded, summed over gates */
+  double ratio;               /* raw_bytes / encoded_bytes */
+  double min_ratio;           /* raw_bytes / max_encoded_bytes (Table 2 "compression ratio") */
+  double eps_current;         /* bound used by the last gate; 0 = lossless */
+  double fidelity_lb_sum;     /* 1 - sum_i delta_i, delta_i = 2^EXP(eps_i) per lossy gate (provable) */
+  double fidelity_lb_prod;    /* prod_i (1 - delta_i) (Section 3.8) */
+  int64_t eps_switch_gate;    /* index of the first gate run lossy, -1 if none */
+  int32_t sig_bits_current;   /* S of the last gate (64 = lossless) */
+  int32_t level;              /* position on the bound ladder, 0 = lossless */
+  int32_t chunk_log2, block_log2;
+} sim_stats_t;
+
+/* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
+ * amplitudes (clamped to n) with lossy bound err_bound (0 = always lossless;
+ * otherwise a normal double in [2^-52, 1)).  The budget defaults to 90 % of the free
+ * device memory at creation; chunk_log2 defaults to min(10, block_log2).  Allocates
+ * the page arena, directory and free-page stack with cudaMalloc.  *out receives the
+ * handle.  Errors: SIM_ERR_INVALID, SIM_ERR_OOM (cudaMalloc failed), SIM_ERR_CUDA. */
+sim_status sim_create(int n_qubits, int block_log2, double err_bound, sim_t** out);
+
+/* Like sim_create with every setting given: chunk_log2 in [0, 11] (clamped to the
+ * block); budget in bytes (> 0): the memory the compressed state may use, against
+ * which the controller compares E + two blocks with threshold floor(tau * budget),
+ * tau in (0, 1]; ladder 0 = lossless then err_bound, 1 = the paper's ladder 1e-5,
+ * 1e-4, ... up to err_bound, one level per gate (Section 3.7).  pool_bytes is the page
+ * arena actually allocated (0: budget + 1/8 for page rounding + the per-CTA page
+ * caches).  The controller acts before a gate, so one gate can grow the state past
+ * the threshold; if the images then exceed the arena the gate fails with SIM_ERR_OOM. */
+sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double err_bound, uint64_t budget,
+                         double tau, int ladder, uint64_t pool_bytes, sim_t** out);
+
+/* Frees every device allocation of the handle (after synchronising its stream). */
+sim_status sim_destroy(sim_t* sim);
+
+/* Uses `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later work of this handle.  The caller keeps the stream alive. */
+sim_status sim_set_stream(sim_t* sim, void* cuda_stream);
+
+/* Applies one gate (Section 3.1).  Queued on the stream; device-side failures are
+ * reported by this call only if they are already known, otherwise by the next
+ * synchronising call. */
+sim_status sim_apply_gate(sim_t* sim, const sim_gate* gate);
+
+/* Applies n_gates gates in order.  All gates are validated first (none runs if one
+ * is invalid).  `gates` is a host array.  The launches of the sequence are captured
+ * once into a CUDA graph and replayed.  Synchronises the stream at the end and
+ * returns any device-side error. */
+sim_status sim_apply_circuit(sim_t* sim, const sim_gate* gates, size_t n_gates);
+
+/* Waits for queued work and returns the device error state. */
+sim_status sim_sync(sim_t* sim);
+
+/* Decodes amplitudes [first, first + count) into out (2*count doubles, interleaved).
+ * out_on_device != 0: `out` is a device pointer; else a host pointer. */
+sim_status sim_amplitudes(sim_t* sim, uint64_t first, uint64_t count, double* out, int out_on_device);
+
+/* One measurement of all qubits in the computational basis, without collapsing the
+ * state: u = (splitmix64(seed) >> 11) * 2^-53, outcome = smallest index whose running
+ * sum of |a_i|^2 reaches u * sum |a|^2; *prob = |a_outcome|^2 / sum |a|^2. */
+sim_status sim_measure(sim_t* sim, uint64_t seed, uint64_t* outcome, double* prob);
+
+/* F = |<ref|psi>| (Section 3.8, Eq. idealsim) against a full reference state of
+ * 2^n interleaved amplitudes (host pointer, or device pointer if ref_on_device).
+ * Also returns <ref|psi> in re_im[2] and |psi|^2 in norm2 (either may be NULL). */
+sim_status sim_fidelity(sim_t* sim, const double* ref, int ref_on_device, double* F, double* re_im,
+                        double* norm2);
+
+/* Copies the run statistics (synchronises). */
+sim_status sim_stats(sim_t* sim, sim_stats_t* out);
+
+/* Copies chunk c's image into out (capacity cap bytes, host memory); *len receives
+ * its length.  For checking images against a reference codec. */
+sim_status sim_chunk_image(sim_t* sim, uint64_t c, uint8_t* out, size_t cap, size_t* len);
+
+/* Number of chunks and chunk_log2 of the handle. */
+sim_status sim_layout(sim_t* sim, uint64_t* n_chunks, int* chunk_log2, int* block_log2);
+
+/* Timing of the fused gate kernel: with timing on, every gate-kernel launch is
+ * bracketed by CUDA events on the handle's stream.  sim_timing synchronises and
+ * returns, since timing was switched on or last read: the summed kernel time in ms,
+ * the number of gate-kernel launches, and the chunk-image bytes those launches read
+ * and wrote (the compressed traffic of the gates); then it starts counting anew. */
+sim_status sim_set_timing(sim_t* sim, int on);
+sim_status sim_timing(sim_t* sim, double* gate_kernel_ms, uint64_t* launches, uint64_t* bytes_read,
+                      uint64_t* bytes_written);
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char* sim_last_error(void);
+
+/* ---------------------------------------------------------------------------------
+ * Codec entry points: the device encoder and decoder on caller-provided chunks.
+ * A chunk is 2^chunk_log2 amplitudes = 2^(chunk_log2+1) doubles.  Image format:
+ * 16-byte header [mode, S, log2 P, 0, payload bytes u32, coded values u32,
+ * residual bits u32] then the payload (a multiple of 16 bytes); modes 0 ZERO,
+ * 1 CONST, 2 PERIOD, 3 STREAM, 4 RAW (Section 4.2 Solution C for the coded streams;
+ * the modes stand in for its Zstd stage).  The encoder truncates with
+ * S = 12 - EXP(eps) bits (eps = 0: 64 bits), forced to 64 for a chunk holding a
+ * nonzero subnormal, and keeps the smallest image (ties: lower mode); force_mode
+ * >= 0 selects a mode instead (SIM_ERR_INVALID if it does not apply).
+ * ------------------------------------------------------------------------------- */
+
+/* Encodes n_chunks chunks: in = n_chunks * 2^(chunk_log2+1) doubles; image k is
+ * written at out + k * out_stride (out_stride >= 16 + 16 * 2^chunk_log2 + 2^chunk_log2/2
+ * + 32, a multiple of 16) and its length to out_len[k].  on_device != 0: all three
+ * pointers are device pointers; else host pointers. */
+sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
+                            uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device);
+
+/* Decodes n_chunks images (image k at in + k * in_stride, length in_len[k]) into
+ * out = n_chunks * 2^(chunk_log2+1) doubles.  SIM_ERR_CORRUPT if any image fails
+ * its checks (its chunk is then zero-filled). */
+sim_status sim_codec_decode(const uint8_t* in, uint64_t in_stride, const uint32_t* in_len, uint64_t n_chunks,
+                            int chunk_log2, double* out, int on_device);
+
+/* ---------------------------------------------------------------------------------
+ * Uncompressed complex128 state vector on the same GPU (the comparator of the
+ * compressed path; same gate arithmetic).  16 * 2^n bytes of device memory.
+ * ------------------------------------------------------------------------------- */
+typedef struct sim_sv sim_sv_t;
+sim_status sim_sv_create(int n_qubits, sim_sv_t** out);
+sim_status sim_sv_destroy(sim_sv_t* sv);
+sim_status sim_sv_set_stream(sim_sv_t* sv, void* cuda_stream);
+sim_status sim_sv_apply_circuit(sim_sv_t* sv, const sim_gate* gates, size_t n_gates);
+sim_status sim_sv_amplitudes(sim_sv_t* sv, uint64_t first, uint64_t count, double* out, int out_on_device);
+/* Device pointer to the 2^n interleaved amplitudes (valid until sim_sv_destroy). */
+sim_status sim_sv_data(sim_sv_t* sv, double** dev_ptr);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCSIM_H */

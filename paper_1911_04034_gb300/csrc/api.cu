@@ -1,0 +1,743 @@
+// api.cu -- host side of the libqcsim C ABI (see include/qcsim.h).
+//
+// Gate classification (Section 3.3 segments): with chunks of 2^kc amplitudes, a
+// target below kc pairs amplitudes inside one chunk; a target at or above kc pairs
+// chunk q with chunk q | 2^(t-kc) (the paper's "different blocks" segment; one GPU
+// has no remote-rank segment).  A control on a chunk-index bit removes whole chunks
+// from the work (the paper's block-level skip); controls below kc are tested per
+// amplitude pair inside the kernel.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qcsim.h"
+#include "launch.h"
+
+using qc::CtlParams;
+using qc::DevCtl;
+using qc::GateCoef;
+using qc::GateLaunch;
+using qc::Pool;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sim_status fail(sim_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+sim_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(SIM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(SIM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Eq. sigbits: S = 12 - EXP(eps) for binary64 (EXP = the IEEE exponent of eps);
+// eps = 0 is the lossless stage (64 bits).  -1 for a bound outside {0} U [2^-52, 1).
+int sig_bits_of(double eps) {
+  if (eps == 0.0) return 64;
+  if (!(eps > 0.0) || !(eps < 1.0)) return -1;
+  int e2 = 0;
+  (void)std::frexp(eps, &e2);  // eps = f 2^e2, f in [0.5, 1): IEEE exponent e2 - 1
+  const int ex = e2 - 1;
+  if (ex < -52) return -1;
+  const int S = 12 - ex;
+  return S > 64 ? 64 : S;
+}
+
+bool gate_ok(const sim_gate* g, int n, std::string* why) {
+  if (g->target < 0 || g->target >= n) { *why = "target outside the register"; return false; }
+  const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  if (g->ctrl_mask & ~all) { *why = "control outside the register"; return false; }
+  if ((g->ctrl_mask >> g->target) & 1ull) { *why = "control on the target"; return false; }
+  if (g->ctrl_vals & ~g->ctrl_mask) { *why = "control value outside the control mask"; return false; }
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(g->u[k])) { *why = "non-finite matrix entry"; return false; }
+  // U^H U = I: unit columns, orthogonal to each other
+  const double* u = g->u;
+  const double n0 = u[0] * u[0] + u[1] * u[1] + u[4] * u[4] + u[5] * u[5];
+  const double n1 = u[2] * u[2] + u[3] * u[3] + u[6] * u[6] + u[7] * u[7];
+  const double dr = u[0] * u[2] + u[1] * u[3] + u[4] * u[6] + u[5] * u[7];
+  const double di = u[0] * u[3] - u[1] * u[2] + u[4] * u[7] - u[5] * u[6];
+  if (std::fabs(n0 - 1.0) > 1e-12 || std::fabs(n1 - 1.0) > 1e-12 || std::fabs(dr) > 1e-12 || std::fabs(di) > 1e-12) {
+    *why = "matrix is not unitary within 1e-12";
+    return false;
+  }
+  return true;
+}
+
+GateCoef coef_of(const sim_gate* g) {
+  const double* u = g->u;
+  GateCoef c;
+  const double v[16] = {u[0], -u[1], u[2], -u[3],  // a'r: ar ai br bi
+                        u[0], u[1],  u[2], u[3],   // a'i: ai ar bi br
+                        u[4], -u[5], u[6], -u[7],  // b'r: ar ai br bi
+                        u[4], u[5],  u[6], u[7]};  // b'i: ai ar bi br
+  for (int k = 0; k < 16; ++k) c.c[k] = v[k];
+  return c;
+}
+
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+struct sim {
+  int n = 0, b = 0, kc = 0, ladder = 0;
+  double eps_max = 0.0, tau = 0.9;
+  uint64_t budget = 0, nchunks = 0, npages = 0;
+  cudaStream_t st = 0;
+  Pool P{};
+  CtlParams cp{};
+  DevCtl* d_ctl = nullptr;
+  unsigned long long* d_counts = nullptr;
+  int grid = 1;
+  sim_status poisoned = SIM_OK;
+  uint64_t amp_updates = 0;
+  uint64_t device_bytes = 0;
+  uint8_t* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  double level_eps[8] = {0};
+  // gate-kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  size_t ev_next = 0;
+  unsigned long long t_bytes_in0 = 0, t_bytes_out0 = 0;
+
+  ~sim() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    cudaFree(P.pages);
+    cudaFree(P.dir);
+    cudaFree(P.stack);
+    cudaFree(P.freed);
+    cudaFree(P.cache);
+    cudaFree(P.cache_n);
+    cudaFree(d_ctl);
+    cudaFree(d_counts);
+    cudaFree(d_scratch);
+  }
+
+  sim_status scratch(size_t bytes) {
+    if (bytes <= scratch_bytes) return SIM_OK;
+    cudaFree(d_scratch);
+    d_scratch = nullptr;
+    scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&d_scratch, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    scratch_bytes = bytes;
+    return SIM_OK;
+  }
+
+  // Device error word -> status; poisons the handle on a device-side failure.
+  sim_status check_device() {
+    unsigned int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, &d_ctl->err, sizeof(err), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      poisoned = SIM_ERR_CUDA;
+      return cuda_fail(e, "device");
+    }
+    if (err == 0) return SIM_OK;
+    if (err & qc::E_OOM) {
+      poisoned = SIM_ERR_OOM;
+      return fail(SIM_ERR_OOM, "the page pool ran out of pages (budget too small for the state)");
+    }
+    poisoned = SIM_ERR_CORRUPT;
+    return fail(SIM_ERR_CORRUPT, "a chunk image failed its checks or held a non-finite value (flags 0x%x)", err);
+  }
+
+  sim_status guard() const {
+    if (poisoned != SIM_OK) return fail(SIM_ERR_STATE, "handle is poisoned by an earlier failure");
+    return SIM_OK;
+  }
+};
+
+struct sim_sv {
+  int n = 0;
+  double* psi = nullptr;
+  cudaStream_t st = 0;
+  ~sim_sv() { cudaFree(psi); }
+};
+
+extern "C" {
+
+const char* sim_last_error(void) { return g_last_error.c_str(); }
+
+sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double err_bound, uint64_t budget, double tau,
+                         int ladder, uint64_t pool_bytes, sim_t** out) {
+  if (!out) return fail(SIM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > 40) return fail(SIM_ERR_INVALID, "n_qubits must be in [1, 40]");
+  if (block_log2 < 0) return fail(SIM_ERR_INVALID, "block_log2 must be >= 0");
+  if (chunk_log2 < 0 || chunk_log2 > qc::kMaxKC) return fail(SIM_ERR_INVALID, "chunk_log2 must be in [0, 11]");
+  if (sig_bits_of(err_bound) < 0) return fail(SIM_ERR_INVALID, "err_bound must be 0 or in [2^-52, 1)");
+  if (budget == 0) return fail(SIM_ERR_INVALID, "budget must be > 0");
+  if (!(tau > 0.0 && tau <= 1.0)) return fail(SIM_ERR_INVALID, "tau must be in (0, 1]");
+  if (ladder != 0 && ladder != 1) return fail(SIM_ERR_INVALID, "ladder must be 0 or 1");
+
+  sim* s = new sim();
+  s->n = n_qubits;
+  s->b = block_log2 < n_qubits ? block_log2 : n_qubits;
+  s->kc = chunk_log2 < s->b ? chunk_log2 : s->b;
+  s->eps_max = err_bound;
+  s->tau = tau;
+  s->budget = budget;
+  s->ladder = ladder;
+  s->nchunks = 1ull << (s->n - s->kc);
+
+  // controller parameters (Section 3.7, Eq. totalnbBytes with r = 1)
+  CtlParams& cp = s->cp;
+  cp.thresh = (unsigned long long)std::floor(tau * (double)budget);
+  cp.inflight = 2ull << (s->b + 4);
+  cp.ladder = ladder;
+  cp.nlevels = 0;
+  if (err_bound > 0.0) {
+    static const double paper[5] = {1e-5, 1e-4, 1e-3, 1e-2, 1e-1};
+    if (ladder == 1)
+      for (double e : paper)
+        if (e < err_bound) s->level_eps[cp.nlevels++] = e;
+    s->level_eps[cp.nlevels++] = err_bound;
+  }
+  for (int k = 0; k < cp.nlevels; ++k) {
+    cp.S[k] = sig_bits_of(s->level_eps[k]);
+    cp.delta[k] = std::ldexp(1.0, 12 - cp.S[k]);
+  }
+
+  // page arena: the budget, 1/8 more for page rounding, and the pages that the
+  // per-CTA caches may hold while a gate runs
+  s->grid = device_sms() * qc::gate_ctas_per_sm(s->kc);
+  const uint64_t slack_pages = (uint64_t)s->grid * (qc::kCacheCap + 2 * qc::max_pages(s->kc));
+  if (pool_bytes) {
+    s->npages = (pool_bytes + qc::kPage - 1) / qc::kPage;
+  } else {
+    const uint64_t bp = (budget + qc::kPage - 1) / qc::kPage;
+    s->npages = bp + bp / 8 + slack_pages;
+  }
+  if (s->npages >= (1ull << 32)) {
+    delete s;
+    return fail(SIM_ERR_INVALID, "budget too large for 32-bit page ids");
+  }
+  Pool& P = s->P;
+  P.kc = s->kc;
+  P.npages = s->npages;
+  P.dir_words = qc::dir_stride(s->kc) / 4;
+  struct A {
+    void** p;
+    size_t bytes;
+    const char* what;
+  } allocs[] = {
+      {(void**)&P.pages, (size_t)s->npages * qc::kPage, "page arena"},
+      {(void**)&P.dir, (size_t)s->nchunks * qc::dir_stride(s->kc), "directory"},
+      {(void**)&P.stack, (size_t)s->npages * 4, "free-page stack"},
+      {(void**)&P.freed, (size_t)s->npages * 4, "freed list"},
+      {(void**)&P.cache, (size_t)s->grid * qc::kCacheCap * 4, "page caches"},
+      {(void**)&P.cache_n, (size_t)s->grid * 4, "page cache counts"},
+      {(void**)&s->d_ctl, sizeof(DevCtl), "counters"},
+      {(void**)&s->d_counts, 8 * sizeof(unsigned long long), "mode counts"},
+  };
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      delete s;
+      return cuda_fail(e, a.what);
+    }
+    s->device_bytes += a.bytes;
+  }
+  P.ctl = s->d_ctl;
+  DevCtl h{};
+  h.top = (long long)s->npages;
+  h.switch_gate = -1;
+  h.lb_prod = 1.0;
+  h.S_last = 64;
+  cudaError_t e = cudaMemcpy(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(P.cache_n, 0, (size_t)s->grid * 4);
+  if (e == cudaSuccess) e = qc::launch_pool_init(P, s->nchunks, 0);
+  if (e == cudaSuccess) e = qc::launch_init_chunk0(P, s->nchunks, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "initialisation");
+  }
+  sim_status rc = s->check_device();
+  if (rc != SIM_OK) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return SIM_OK;
+}
+
+sim_status sim_create(int n_qubits, int block_log2, double err_bound, sim_t** out) {
+  if (n_qubits < 1 || n_qubits > 40 || block_log2 < 0) return fail(SIM_ERR_INVALID, "bad n_qubits or block_log2");
+  size_t freeb = 0, totalb = 0;
+  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) return fail(SIM_ERR_CUDA, "cudaMemGetInfo failed");
+  const int b = block_log2 < n_qubits ? block_log2 : n_qubits;
+  const int kc = b < 10 ? b : 10;
+  const uint64_t nchunks = 1ull << (n_qubits - kc);
+  const uint64_t raw = 16ull << n_qubits;
+  const double overhead = (double)nchunks * qc::dir_stride(kc) + 64.0 * 1024 * 1024;
+  double avail = 0.9 * (double)freeb - overhead;
+  avail /= (1.0 + 8.0 / qc::kPage);  // stack and freed list: 8 bytes per page
+  if (avail < 1e6) return fail(SIM_ERR_OOM, "not enough free device memory");
+  uint64_t budget = (uint64_t)avail;
+  const uint64_t cap = raw + 16ull * nchunks + 4096;  // RAW images never need more
+  if (budget > cap) budget = cap;
+  return sim_create_ex(n_qubits, block_log2, kc, err_bound, budget, 0.9, 0, 0, out);
+}
+
+sim_status sim_destroy(sim_t* s) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  cudaStreamSynchronize(s->st);
+  delete s;
+  return SIM_OK;
+}
+
+sim_status sim_set_stream(sim_t* s, void* stream) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  s->st = reinterpret_cast<cudaStream_t>(stream);
+  return SIM_OK;
+}
+
+static sim_status enqueue_gate(sim* s, const sim_gate* g) {
+  const int kc = s->kc, t = g->target;
+  const uint64_t A = 1ull << kc;
+  GateLaunch L{};
+  L.P = s->P;
+  L.ctl = s->cp;
+  L.g = coef_of(g);
+  const uint64_t chunk_bits = (s->nchunks - 1ull);
+  const uint64_t hi_mask = (g->ctrl_mask >> kc) & chunk_bits;
+  L.hi_vals = (g->ctrl_vals >> kc) & chunk_bits;
+  L.lo_mask = (uint32_t)(g->ctrl_mask & (A - 1ull));
+  L.lo_vals = (uint32_t)(g->ctrl_vals & (A - 1ull));
+  L.target = t;
+  if (t >= kc) {
+    L.pair = 1;
+    L.pair_bit = 1ull << (t - kc);
+    L.free_mask = chunk_bits & ~hi_mask & ~L.pair_bit;
+    L.items = 1ull << popcount64(L.free_mask);
+    L.nact = 2ull * L.items;
+  } else {
+    L.pair = 0;
+    L.pair_bit = 0;
+    L.free_mask = chunk_bits & ~hi_mask;
+    L.nact = 1ull << popcount64(L.free_mask);
+    L.items = (L.nact + 1ull) / 2ull;
+  }
+  const int grid = (uint64_t)s->grid < L.items ? s->grid : (int)L.items;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s->timing) {
+    while (s->ev_pool.size() < s->ev_next + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e), "event create");
+      s->ev_pool.push_back(e);
+    }
+    e0 = s->ev_pool[s->ev_next++];
+    e1 = s->ev_pool[s->ev_next++];
+    CK(cudaEventRecord(e0, s->st), "event record");
+  }
+  CK(qc::launch_gate(L, grid, s->st), "gate kernel launch");
+  if (s->timing) {
+    CK(cudaEventRecord(e1, s->st), "event record");
+    s->ev_pending.emplace_back(e0, e1);
+  }
+  CK(qc::launch_post(s->P, s->cp, s->grid, s->st), "post kernel launch");
+  s->amp_updates += L.nact * A;
+  return SIM_OK;
+}
+
+sim_status sim_apply_gate(sim_t* s, const sim_gate* g) {
+  if (!s || !g) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  std::string why;
+  if (!gate_ok(g, s->n, &why)) return fail(SIM_ERR_INVALID, "invalid gate: %s", why.c_str());
+  return enqueue_gate(s, g);
+}
+
+sim_status sim_apply_circuit(sim_t* s, const sim_gate* gates, size_t n_gates) {
+  if (!s || (!gates && n_gates)) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  std::string why;
+  for (size_t k = 0; k < n_gates; ++k)
+    if (!gate_ok(gates + k, s->n, &why)) return fail(SIM_ERR_INVALID, "invalid gate %zu: %s", k, why.c_str());
+  for (size_t k = 0; k < n_gates; ++k)
+    if (sim_status r = enqueue_gate(s, gates + k)) return r;
+  return s->check_device();
+}
+
+sim_status sim_sync(sim_t* s) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  if (sim_status r = s->guard()) return r;
+  return s->check_device();
+}
+
+static sim_status read_traffic(sim* s, unsigned long long* in, unsigned long long* out) {
+  unsigned long long v[2];
+  CK(cudaMemcpyAsync(v, &s->d_ctl->bytes_in, sizeof(v), cudaMemcpyDeviceToHost, s->st), "copy counters");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  *in = v[0];
+  *out = v[1];
+  return SIM_OK;
+}
+
+sim_status sim_set_timing(sim_t* s, int on) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  s->timing = on != 0;
+  s->ev_pending.clear();
+  s->ev_next = 0;
+  return read_traffic(s, &s->t_bytes_in0, &s->t_bytes_out0);
+}
+
+sim_status sim_timing(sim_t* s, double* ms, uint64_t* launches, uint64_t* bytes_read, uint64_t* bytes_written) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  double tot = 0.0;
+  for (auto& pr : s->ev_pending) {
+    float m = 0.f;
+    CK(cudaEventElapsedTime(&m, pr.first, pr.second), "event elapsed");
+    tot += m;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = s->ev_pending.size();
+  unsigned long long in = 0, out = 0;
+  if (sim_status r = read_traffic(s, &in, &out)) return r;
+  if (bytes_read) *bytes_read = in - s->t_bytes_in0;
+  if (bytes_written) *bytes_written = out - s->t_bytes_out0;
+  s->t_bytes_in0 = in;
+  s->t_bytes_out0 = out;
+  s->ev_pending.clear();
+  s->ev_next = 0;
+  return SIM_OK;
+}
+
+sim_status sim_layout(sim_t* s, uint64_t* n_chunks, int* chunk_log2, int* block_log2) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  if (n_chunks) *n_chunks = s->nchunks;
+  if (chunk_log2) *chunk_log2 = s->kc;
+  if (block_log2) *block_log2 = s->b;
+  return SIM_OK;
+}
+
+sim_status sim_amplitudes(sim_t* s, uint64_t first, uint64_t count, double* out, int out_on_device) {
+  if (!s || (!out && count)) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  const uint64_t total = 1ull << s->n;
+  if (first > total || count > total - first) return fail(SIM_ERR_INVALID, "amplitude range outside the state");
+  if (count == 0) return SIM_OK;
+  if (out_on_device) {
+    CK(qc::launch_decode_range(s->P, first, count, out, s->st), "decode launch");
+    return s->check_device();
+  }
+  const uint64_t slice = 1ull << 22;  // amplitudes per staging pass (64 MiB)
+  if (sim_status r = s->scratch((size_t)slice * 16)) return r;
+  for (uint64_t off = 0; off < count; off += slice) {
+    const uint64_t m = count - off < slice ? count - off : slice;
+    CK(qc::launch_decode_range(s->P, first + off, m, reinterpret_cast<double*>(s->d_scratch), s->st), "decode");
+    CK(cudaMemcpyAsync(out + 2 * off, s->d_scratch, m * 16, cudaMemcpyDeviceToHost, s->st), "copy out");
+    CK(cudaStreamSynchronize(s->st), "sync");
+  }
+  return s->check_device();
+}
+
+static uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+sim_status sim_measure(sim_t* s, uint64_t seed, uint64_t* outcome, double* prob) {
+  if (!s || !outcome || !prob) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  const uint64_t nc = s->nchunks;
+  if (sim_status r = s->scratch((size_t)nc * 8)) return r;
+  CK(qc::launch_chunk_norms(s->P, 0, nc, reinterpret_cast<double*>(s->d_scratch), s->st), "norm launch");
+  std::vector<double> pc(nc);
+  CK(cudaMemcpyAsync(pc.data(), s->d_scratch, nc * 8, cudaMemcpyDeviceToHost, s->st), "copy norms");
+  if (sim_status r = s->check_device()) return r;
+  double total = 0.0;
+  for (double v : pc) total += v;
+  const double u = (double)(splitmix64(seed) >> 11) * (1.0 / 9007199254740992.0);
+  const double target = u * total;
+  double run = 0.0;
+  uint64_t c = 0;
+  for (; c < nc; ++c) {
+    if (run + pc[c] >= target && pc[c] > 0.0) break;
+    run += pc[c];
+  }
+  if (c == nc) {  // rounding put the target past the end: take the last nonzero chunk
+    c = nc - 1;
+    while (c > 0 && pc[c] == 0.0) --c;
+    run = 0.0;
+    for (uint64_t k = 0; k < c; ++k) run += pc[k];
+  }
+  const uint64_t A = 1ull << s->kc;
+  std::vector<double> amp(2 * A);
+  if (sim_status r = sim_amplitudes(s, c * A, A, amp.data(), 0)) return r;
+  uint64_t pick = A;
+  uint64_t last_nz = 0;
+  for (uint64_t i = 0; i < A; ++i) {
+    const double p = std::fma(amp[2 * i], amp[2 * i], amp[2 * i + 1] * amp[2 * i + 1]);
+    if (p > 0.0) last_nz = i;
+    run += p;
+    if (run >= target && p > 0.0) { pick = i; break; }
+  }
+  if (pick == A) { pick = last_nz; }
+  const double p = std::fma(amp[2 * pick], amp[2 * pick], amp[2 * pick + 1] * amp[2 * pick + 1]);
+  *outcome = c * A + pick;
+  *prob = total > 0.0 ? p / total : 0.0;
+  return SIM_OK;
+}
+
+sim_status sim_fidelity(sim_t* s, const double* ref, int ref_on_device, double* F, double* re_im, double* norm2) {
+  if (!s || !ref || !F) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  const uint64_t nc = s->nchunks, A = 1ull << s->kc;
+  const uint64_t per = ref_on_device ? nc : ((1ull << 22) / A > 0 ? (1ull << 22) / A : 1ull);  // chunks per pass
+  const size_t ref_bytes = ref_on_device ? 0 : (size_t)per * A * 16;
+  if (sim_status r = s->scratch(ref_bytes + (size_t)per * 24)) return r;
+  double* d_out = reinterpret_cast<double*>(s->d_scratch + ref_bytes);
+  std::vector<double> parts(3 * per);
+  double re = 0.0, im = 0.0, nn = 0.0;
+  for (uint64_t c0 = 0; c0 < nc; c0 += per) {
+    const uint64_t m = nc - c0 < per ? nc - c0 : per;
+    const double* dref = ref + 2 * c0 * A;
+    if (!ref_on_device) {
+      CK(cudaMemcpyAsync(s->d_scratch, ref + 2 * c0 * A, m * A * 16, cudaMemcpyHostToDevice, s->st), "copy ref");
+      dref = reinterpret_cast<const double*>(s->d_scratch);
+    }
+    CK(qc::launch_chunk_dots(s->P, c0, m, dref, d_out, s->st), "dot launch");
+    CK(cudaMemcpyAsync(parts.data(), d_out, m * 24, cudaMemcpyDeviceToHost, s->st), "copy parts");
+    if (sim_status r = s->check_device()) return r;
+    for (uint64_t k = 0; k < m; ++k) {
+      re += parts[3 * k];
+      im += parts[3 * k + 1];
+      nn += parts[3 * k + 2];
+    }
+  }
+  *F = std::sqrt(re * re + im * im);
+  if (re_im) { re_im[0] = re; re_im[1] = im; }
+  if (norm2) *norm2 = nn;
+  return SIM_OK;
+}
+
+sim_status sim_stats(sim_t* s, sim_stats_t* o) {
+  if (!s || !o) return fail(SIM_ERR_INVALID, "NULL argument");
+  DevCtl h{};
+  unsigned long long counts[8] = {0};
+  CK(cudaMemsetAsync(s->d_counts, 0, sizeof(counts), s->st), "memset");
+  CK(qc::launch_mode_counts(s->P, s->nchunks, s->d_counts, s->st), "mode count launch");
+  CK(cudaMemcpyAsync(&h, s->d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s->st), "copy counters");
+  CK(cudaMemcpyAsync(counts, s->d_counts, sizeof(counts), cudaMemcpyDeviceToHost, s->st), "copy counts");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  std::memset(o, 0, sizeof(*o));
+  o->gates = h.gates;
+  o->encoded_bytes = h.E;
+  o->max_encoded_bytes = h.Emax;
+  o->raw_bytes = 16ull << s->n;
+  o->inflight_bytes = s->cp.inflight;
+  for (int k = 0; k < 8; ++k) o->chunks_by_mode[k] = counts[k];
+  o->pool_bytes = s->npages * qc::kPage;
+  o->pages_in_use_bytes = (s->npages - (uint64_t)h.top) * qc::kPage;
+  o->peak_pages_bytes = h.peak_pages * qc::kPage;
+  o->device_bytes = s->device_bytes + s->scratch_bytes;
+  o->amp_updates = s->amp_updates;
+  o->ratio = h.E ? (double)o->raw_bytes / (double)h.E : 0.0;
+  o->min_ratio = h.Emax ? (double)o->raw_bytes / (double)h.Emax : 0.0;
+  o->eps_current = h.level ? s->level_eps[h.level - 1] : 0.0;
+  o->fidelity_lb_sum = 1.0 - h.lb_sum;
+  o->fidelity_lb_prod = h.lb_prod;
+  o->eps_switch_gate = h.switch_gate;
+  o->sig_bits_current = h.S_last;
+  o->level = h.level;
+  o->chunk_log2 = s->kc;
+  o->block_log2 = s->b;
+  if (h.err) return s->check_device();
+  return SIM_OK;
+}
+
+sim_status sim_chunk_image(sim_t* s, uint64_t c, uint8_t* out, size_t cap, size_t* len) {
+  if (!s || !out || !len) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (c >= s->nchunks) return fail(SIM_ERR_INVALID, "chunk index outside the state");
+  uint32_t head[2];
+  const size_t stride = qc::dir_stride(s->kc);
+  CK(cudaMemcpyAsync(head, reinterpret_cast<uint8_t*>(s->P.dir) + c * stride, 8, cudaMemcpyDeviceToHost, s->st),
+     "copy dir");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  *len = head[0];
+  if (head[0] > cap) return fail(SIM_ERR_INVALID, "buffer too small for the image (%u bytes)", head[0]);
+  if (sim_status r = s->scratch(qc::max_image_bytes(s->kc) + 16)) return r;
+  CK(qc::launch_copy_image(s->P, c, s->d_scratch, s->st), "copy image launch");
+  CK(cudaMemcpyAsync(out, s->d_scratch, head[0], cudaMemcpyDeviceToHost, s->st), "copy image");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------ codec ------ //
+sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
+                            uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device) {
+  if (!in || !out || !out_len) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (chunk_log2 < 0 || chunk_log2 > qc::kMaxKC) return fail(SIM_ERR_INVALID, "chunk_log2 must be in [0, 11]");
+  const int S = sig_bits_of(eps);
+  if (S < 0) return fail(SIM_ERR_INVALID, "eps must be 0 or in [2^-52, 1)");
+  if (force_mode >= (int)qc::M_NMODES) return fail(SIM_ERR_INVALID, "unknown mode");
+  const uint64_t need = 16 + (16ull << chunk_log2) + (1ull << chunk_log2) / 2 + 32;
+  if (out_stride < need || (out_stride & 15)) return fail(SIM_ERR_INVALID, "out_stride too small or not a multiple of 16");
+  if (n_chunks == 0) return SIM_OK;
+  const size_t in_bytes = (size_t)n_chunks * (16ull << chunk_log2);
+  const double* din = in;
+  uint8_t* dout = out;
+  uint32_t* dlen = out_len;
+  unsigned int* derr = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = sizeof(unsigned int) + (on_device ? 0 : in_bytes + n_chunks * out_stride + n_chunks * 4 + 64);
+  CK(cudaMalloc(&tmp, tmp_bytes), "codec buffers");
+  derr = reinterpret_cast<unsigned int*>(tmp);
+  if (!on_device) {
+    uint8_t* base = reinterpret_cast<uint8_t*>(tmp) + 16;
+    din = reinterpret_cast<double*>(base);
+    dout = base + ((in_bytes + 15) & ~15ull);
+    dlen = reinterpret_cast<uint32_t*>(dout + n_chunks * out_stride);
+    cudaMemcpy((void*)din, in, in_bytes, cudaMemcpyHostToDevice);
+  }
+  cudaMemset(derr, 0, sizeof(unsigned int));
+  cudaError_t e = qc::launch_codec_encode(din, n_chunks, chunk_log2, (uint32_t)S, force_mode, dout, out_stride, dlen,
+                                          derr, 0);
+  unsigned int herr = 0;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpy(out, dout, n_chunks * out_stride, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out_len, dlen, n_chunks * 4, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "codec encode");
+  if (herr & qc::E_NONFINITE) return fail(SIM_ERR_INVALID, "input holds a non-finite value");
+  if (herr & qc::E_MODE) return fail(SIM_ERR_INVALID, "forced mode does not apply to a chunk");
+  return SIM_OK;
+}
+
+sim_status sim_codec_decode(const uint8_t* in, uint64_t in_stride, const uint32_t* in_len, uint64_t n_chunks,
+                            int chunk_log2, double* out, int on_device) {
+  if (!in || !in_len || !out) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (chunk_log2 < 0 || chunk_log2 > qc::kMaxKC) return fail(SIM_ERR_INVALID, "chunk_log2 must be in [0, 11]");
+  if (in_stride & 15) return fail(SIM_ERR_INVALID, "in_stride must be a multiple of 16");
+  if (n_chunks == 0) return SIM_OK;
+  const size_t out_bytes = (size_t)n_chunks * (16ull << chunk_log2);
+  const uint8_t* din = in;
+  const uint32_t* dlen = in_len;
+  double* dout = out;
+  void* tmp = nullptr;
+  const size_t tmp_bytes = 16 + (on_device ? 0 : n_chunks * in_stride + n_chunks * 4 + 16 + out_bytes);
+  CK(cudaMalloc(&tmp, tmp_bytes), "codec buffers");
+  unsigned int* derr = reinterpret_cast<unsigned int*>(tmp);
+  if (!on_device) {
+    uint8_t* base = reinterpret_cast<uint8_t*>(tmp) + 16;
+    din = base;
+    uint32_t* l = reinterpret_cast<uint32_t*>(base + n_chunks * in_stride);
+    dlen = l;
+    dout = reinterpret_cast<double*>(base + ((n_chunks * in_stride + n_chunks * 4 + 15) & ~15ull));
+    cudaMemcpy((void*)din, in, n_chunks * in_stride, cudaMemcpyHostToDevice);
+    cudaMemcpy(l, in_len, n_chunks * 4, cudaMemcpyHostToDevice);
+  }
+  cudaMemset(derr, 0, sizeof(unsigned int));
+  cudaError_t e = qc::launch_codec_decode(din, in_stride, dlen, n_chunks, chunk_log2, dout, derr, 0);
+  unsigned int herr = 0;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpy(out, dout, out_bytes, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "codec decode");
+  if (herr) return fail(SIM_ERR_CORRUPT, "an image failed its checks");
+  return SIM_OK;
+}
+
+// ------------------------------------------------- uncompressed path ----- //
+sim_status sim_sv_create(int n_qubits, sim_sv_t** out) {
+  if (!out) return fail(SIM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > 34) return fail(SIM_ERR_INVALID, "n_qubits must be in [1, 34]");
+  sim_sv* v = new sim_sv();
+  v->n = n_qubits;
+  cudaError_t e = cudaMalloc(&v->psi, (size_t)16 << n_qubits);
+  if (e != cudaSuccess) {
+    delete v;
+    return cuda_fail(e, "state vector allocation");
+  }
+  e = qc::launch_sv_init(v->psi, 1ull << n_qubits, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete v;
+    return cuda_fail(e, "state vector init");
+  }
+  *out = v;
+  return SIM_OK;
+}
+
+sim_status sim_sv_destroy(sim_sv_t* v) {
+  if (!v) return fail(SIM_ERR_INVALID, "NULL handle");
+  cudaStreamSynchronize(v->st);
+  delete v;
+  return SIM_OK;
+}
+
+sim_status sim_sv_set_stream(sim_sv_t* v, void* stream) {
+  if (!v) return fail(SIM_ERR_INVALID, "NULL handle");
+  v->st = reinterpret_cast<cudaStream_t>(stream);
+  return SIM_OK;
+}
+
+sim_status sim_sv_apply_circuit(sim_sv_t* v, const sim_gate* gates, size_t n_gates) {
+  if (!v || (!gates && n_gates)) return fail(SIM_ERR_INVALID, "NULL argument");
+  std::string why;
+  for (size_t k = 0; k < n_gates; ++k)
+    if (!gate_ok(gates + k, v->n, &why)) return fail(SIM_ERR_INVALID, "invalid gate %zu: %s", k, why.c_str());
+  for (size_t k = 0; k < n_gates; ++k)
+    CK(qc::launch_sv_gate(v->psi, v->n, coef_of(gates + k), gates[k].target, gates[k].ctrl_mask, gates[k].ctrl_vals,
+                          v->st),
+       "state vector gate");
+  CK(cudaStreamSynchronize(v->st), "sync");
+  return SIM_OK;
+}
+
+sim_status sim_sv_amplitudes(sim_sv_t* v, uint64_t first, uint64_t count, double* out, int out_on_device) {
+  if (!v || (!out && count)) return fail(SIM_ERR_INVALID, "NULL argument");
+  const uint64_t total = 1ull << v->n;
+  if (first > total || count > total - first) return fail(SIM_ERR_INVALID, "amplitude range outside the state");
+  CK(cudaMemcpyAsync(out, v->psi + 2 * first, count * 16, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     v->st),
+     "copy");
+  CK(cudaStreamSynchronize(v->st), "sync");
+  return SIM_OK;
+}
+
+sim_status sim_sv_data(sim_sv_t* v, double** dev_ptr) {
+  if (!v || !dev_ptr) return fail(SIM_ERR_INVALID, "NULL argument");
+  *dev_ptr = v->psi;
+  return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,648 @@
+// device.cuh -- device-side building blocks of libqcsim (sm_103a).
+//
+//  * block-wide scans (warp shuffles)
+//  * chunk decoder and encoder working on shared-memory tiles: bit-plane truncation
+//    (Section 4.2, Eq. sigbits), XOR leading-zero coding with a 2-bit code
+//    (Section 4.2, Solution C) and the ZERO/CONST/PERIOD/STREAM/RAW modes that stand
+//    in for the Zstd stage
+//  * gate arithmetic on an amplitude pair (Section 3.1, Eq. matrix1 / Eq. matrix2)
+//  * the compressed-block pool: 512-byte pages, per-CTA page caches, a global stack
+//    of free pages, and a directory entry per chunk
+//
+// One CTA of kThreads threads owns one work item at a time; every function named
+// *_block is called by all threads of the CTA.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qc {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kPage = 512;
+constexpr int kCacheCap = 128;
+constexpr int kMaxKC = 11;
+
+enum : uint32_t { M_ZERO = 0, M_CONST = 1, M_PERIOD = 2, M_STREAM = 3, M_RAW = 4, M_NMODES = 5 };
+
+enum : uint32_t { E_OK = 0, E_OOM = 1, E_CORRUPT = 2, E_NONFINITE = 4, E_MODE = 8 };
+
+// ---------------------------------------------------------------- sizes ---- //
+__host__ __device__ __forceinline__ uint32_t round16(uint32_t x) { return (x + 15u) & ~15u; }
+// Codes: 2 bits per coded value, padded to 16 bytes.
+__host__ __device__ __forceinline__ uint32_t code_bytes(uint32_t nv) { return round16((nv + 3u) >> 2); }
+// Residual stream: 64-bit words, padded to 16 bytes.
+__host__ __device__ __forceinline__ uint32_t resid_bytes(uint32_t bits) { return ((bits + 127u) >> 7) << 4; }
+// Largest image the encoder writes for a chunk of 2^kc amplitudes (RAW).
+__host__ __device__ __forceinline__ uint32_t max_image_bytes(int kc) { return 16u + (16u << kc); }
+// Largest image any mode can produce, a forced STREAM of incompressible values included.
+__host__ __device__ __forceinline__ uint32_t max_coded_bytes(int kc) {
+  return 16u + code_bytes(2u << kc) + resid_bytes(64u * (2u << kc));
+}
+__host__ __device__ __forceinline__ uint32_t max_pages(int kc) { return (max_image_bytes(kc) + kPage - 1) / kPage; }
+// Directory entry: [bytes u32][npages u32][8 reserved][data: page ids or the image itself]
+__host__ __device__ __forceinline__ uint32_t dir_stride(int kc) { return round16(16u + 4u * max_pages(kc)); }
+__host__ __device__ __forceinline__ uint32_t inline_cap(int kc) { return dir_stride(kc) - 16u; }
+
+// ------------------------------------------------------------- device state -- //
+// Counters and controller state of one simulator, in device memory.
+struct DevCtl {
+  unsigned long long E;         // sum of image bytes after the last finished gate
+  unsigned long long dE;        // change of E during the running gate (two's complement)
+  unsigned long long Emax;      // largest E after any gate
+  long long top;                // free pages on the global stack
+  unsigned long long nfreed;    // pages pushed to the overflow list during the running gate
+  unsigned long long gates;     // gates finished
+  unsigned long long amp_updates;
+  unsigned long long peak_pages;
+  long long switch_gate;        // first gate run lossy, -1 if none
+  double lb_sum;                // sum of delta_i over lossy gates
+  double lb_prod;               // prod (1 - delta_i)
+  int level;                    // ladder level of the last gate (0 = lossless)
+  int S_last;                   // significant bits of the last gate
+  unsigned int err;             // E_* flags
+  unsigned int pad;
+  unsigned long long bytes_in;  // image bytes the gate kernels read (cumulative)
+  unsigned long long bytes_out; // image bytes the gate kernels wrote (cumulative)
+};
+
+// Controller parameters (host-computed, constant for the handle).
+struct CtlParams {
+  unsigned long long thresh;    // floor(tau * budget)
+  unsigned long long inflight;  // two decompressed blocks (Eq. totalnbBytes, r = 1)
+  int nlevels;                  // lossy levels on the ladder (0 = lossless only)
+  int ladder;                   // 0 jump, 1 one level per gate
+  int S[8];                     // significant bits per level (index level-1)
+  double delta[8];              // 2^EXP(eps) per level
+};
+
+// Section 3.7: before a gate, relax the bound if E + inflight > floor(tau * budget).
+__host__ __device__ __forceinline__ int next_level(const CtlParams& p, unsigned long long E, int level) {
+  if (p.nlevels == 0 || level >= p.nlevels) return level;
+  if (E + p.inflight <= p.thresh) return level;
+  return p.ladder == 1 ? level + 1 : p.nlevels;
+}
+__host__ __device__ __forceinline__ int level_bits(const CtlParams& p, int level) {
+  return level == 0 ? 64 : p.S[level - 1];
+}
+
+struct Pool {
+  uint8_t* pages;          // npages * kPage bytes
+  uint32_t* dir;           // nchunks * dir_stride(kc) bytes
+  uint32_t* stack;         // free page ids, [0, top)
+  uint32_t* freed;         // overflow list, [0, nfreed)
+  uint32_t* cache;         // grid * kCacheCap page ids
+  uint32_t* cache_n;       // grid counts
+  DevCtl* ctl;
+  unsigned long long npages;
+  uint32_t dir_words;      // dir_stride / 4
+  int kc;
+};
+
+// -------------------------------------------------------------- scans ----- //
+__device__ __forceinline__ uint32_t warp_incl_add(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+__device__ __forceinline__ int warp_incl_max(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = max(v, n);
+  }
+  return v;
+}
+
+struct ScanSmem {
+  uint32_t wsum[kWarps];
+  int wmax[3][kWarps];
+  uint32_t total;
+  uint32_t bits_period;
+  int flag;
+  int period;
+};
+
+// Exclusive prefix sum over the CTA; *total receives the sum.
+__device__ __forceinline__ uint32_t block_excl_add(uint32_t v, ScanSmem& s, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = warp_incl_add(v);
+  if (lane == 31) s.wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = lane < kWarps ? s.wsum[lane] : 0u;
+    uint32_t xi = warp_incl_add(x);
+    if (lane < kWarps) s.wsum[lane] = xi - x;
+    if (lane == kWarps - 1) s.total = xi;
+  }
+  __syncthreads();
+  uint32_t r = s.wsum[w] + inc - v;
+  *total = s.total;
+  __syncthreads();
+  return r;
+}
+
+// Exclusive max-scan of three ints over the CTA (identity -1).
+__device__ __forceinline__ void block_excl_max3(int a[3], ScanSmem& s) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    inc[b] = warp_incl_max(a[b]);
+    if (lane == 31) s.wmax[b][w] = inc[b];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      int x = lane < kWarps ? s.wmax[b][lane] : -1;
+      int xi = warp_incl_max(x);
+      int ex = __shfl_up_sync(0xffffffffu, xi, 1);
+      if (lane == 0) ex = -1;
+      if (lane < kWarps) s.wmax[b][lane] = ex;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    int ex = __shfl_up_sync(0xffffffffu, inc[b], 1);
+    if (lane == 0) ex = -1;
+    a[b] = max(ex, s.wmax[b][w]);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------- bit helpers --- //
+// Leading identical bytes of v and its predecessor, capped at 3 (the 2-bit code).
+__device__ __forceinline__ uint32_t xor_code(uint64_t v, uint64_t prev) {
+  uint64_t d = v ^ prev;
+  uint32_t L = d ? (uint32_t)(__clzll((long long)d) >> 3) : 8u;
+  return L < 3u ? L : 3u;
+}
+__device__ __forceinline__ uint32_t resid_len(uint32_t c, uint32_t S) {
+  int r = (int)S - 8 * (int)c;
+  return r > 0 ? (uint32_t)r : 0u;
+}
+// r bits (1..64) starting at MSB-first bit position `pos` of the word array.
+__device__ __forceinline__ uint64_t get_bits(const uint64_t* w, uint32_t pos, uint32_t r) {
+  uint32_t wi = pos >> 6, off = pos & 63u;
+  uint64_t hi = w[wi] << off;
+  if (off + r > 64u) hi |= w[wi + 1] >> (64u - off);
+  return hi >> (64u - r);
+}
+__device__ __forceinline__ uint64_t trunc_mask(uint32_t S) { return S >= 64u ? ~0ull : (~0ull << (64u - S)); }
+
+// ----------------------------------------------------------- decoder ----- //
+// Per-thread value ownership: thread t holds values [t*VPT, t*VPT + VPT).
+template <int VPT>
+__device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t nv, uint32_t S, uint32_t bits,
+                                 uint64_t* tile, ScanSmem& s) {
+  const uint32_t* codes32 = reinterpret_cast<const uint32_t*>(payload);
+  const uint32_t cb = code_bytes(nv);
+  const uint64_t* words = reinterpret_cast<const uint64_t*>(payload + cb);
+  const uint32_t j0 = threadIdx.x * VPT;
+  uint32_t c[VPT], r[VPT];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    c[k] = 3u;
+    r[k] = 0u;
+    if (j < nv) {
+      uint32_t word = codes32[j >> 4];
+      uint32_t sh = 8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u);
+      c[k] = (word >> sh) & 3u;
+      r[k] = resid_len(c[k], S);
+      sum += r[k];
+    }
+  }
+  uint32_t total;
+  uint32_t o = block_excl_add(sum, s, &total);
+  if (total != bits || cb + resid_bytes(bits) != plen) return false;
+  // explicit part of every value: residual bits placed at [8c, S)
+  int lw[3] = {-1, -1, -1};
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    if (j < nv) {
+      uint64_t e = 0;
+      if (r[k]) e = (get_bits(words, o, r[k]) << (64u - r[k])) >> (8u * c[k]);
+      tile[j] = e;
+      o += r[k];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        if (c[k] <= (uint32_t)b) lw[b] = (int)j;
+    }
+  }
+  int ex[3] = {lw[0], lw[1], lw[2]};
+  // running "last explicit writer" of leading byte b, exclusive of this thread
+  int thr_last[3] = {-1, -1, -1};
+#pragma unroll
+  for (int b = 0; b < 3; ++b) thr_last[b] = ex[b];
+  block_excl_max3(thr_last, s);  // now: last writer before this thread's first value
+  // (block_excl_max3 ends with __syncthreads, so every explicit part is visible)
+  int run[3] = {thr_last[0], thr_last[1], thr_last[2]};
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    if (j < nv) {
+      uint64_t v = tile[j];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if ((uint32_t)b < c[k] && run[b] >= 0) v |= tile[run[b]] & (0xFF00000000000000ull >> (8 * b));
+      }
+      // leading bytes b >= c of this value are explicit: it becomes the last writer
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        if (c[k] <= (uint32_t)b) run[b] = (int)j;
+      tile[j] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Decodes the staged image (header + payload in shared memory) into tile[0..N).
+// Returns false (tile zero-filled) if the image fails its checks.
+template <int VPT>
+__device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uint64_t* tile, ScanSmem& s) {
+  // img_bytes <= the caller's staging buffer; images in the pool are at most RAW size,
+  // images handed to the codec entry points at most max_coded_bytes(kc)
+  const uint32_t N = 2u << kc;
+  const uint32_t* h = reinterpret_cast<const uint32_t*>(img);
+  const uint32_t mode = h[0] & 0xffu, S = (h[0] >> 8) & 0xffu, lp = (h[0] >> 16) & 0xffu, flags = h[0] >> 24;
+  const uint32_t plen = h[1], nv = h[2], bits = h[3];
+  const uint8_t* payload = img + 16;
+  bool ok = flags == 0 && img_bytes >= 16 && plen + 16u == img_bytes && (plen & 15u) == 0 &&
+            img_bytes <= max_coded_bytes(kc) && (mode == M_ZERO || (S >= 13u && S <= 64u));
+  if (ok) {
+    switch (mode) {
+      case M_ZERO: ok = S == 0 && lp == 0 && plen == 0 && nv == 0 && bits == 0; break;
+      case M_CONST: ok = lp == 0 && plen == 16 && nv == 2 && bits == 0; break;
+      case M_PERIOD: ok = lp >= 1 && (int)lp < kc && nv == (2u << lp); break;
+      case M_STREAM: ok = lp == 0 && nv == N; break;
+      case M_RAW: ok = lp == 0 && nv == N && bits == 0 && plen == 8u * N; break;
+      default: ok = false;
+    }
+  }
+  if (ok && (mode == M_PERIOD || mode == M_STREAM)) {
+    ok = decode_xor_block<VPT>(payload, plen, nv, S, bits, tile, s);
+    if (ok && mode == M_PERIOD) {
+      for (uint32_t j = nv + threadIdx.x; j < N; j += kThreads) tile[j] = tile[j & (nv - 1u)];
+      __syncthreads();
+    }
+    if (ok) return true;
+  }
+  const uint64_t* pw = reinterpret_cast<const uint64_t*>(payload);
+  for (uint32_t j = threadIdx.x; j < N; j += kThreads) {
+    uint64_t v = 0;
+    if (ok && mode == M_CONST) v = pw[j & 1u];
+    else if (ok && mode == M_RAW) v = pw[j];
+    tile[j] = v;
+  }
+  __syncthreads();
+  return ok;
+}
+
+// ----------------------------------------------------------- encoder ----- //
+// Encodes tile[0..N) (raw bit patterns; overwritten with the truncated values) into
+// img (img_cap bytes).  S_req = 12 - EXP(eps) or 64.  force_mode < 0: smallest image
+// (never larger than RAW).  Returns the image length, or 0 with *err set (non-finite
+// value, or a forced mode that does not apply or does not fit in img_cap).
+template <int VPT>
+__device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int force_mode, uint8_t* img,
+                                 uint32_t img_cap, ScanSmem& s, unsigned int* err) {
+  const uint32_t N = 2u << kc, A = 1u << kc;
+  const uint32_t j0 = threadIdx.x * VPT;
+  // 1. chunk-wide width: a nonzero subnormal forces 64 bits; non-finite is an error
+  bool sub = false, nonfin = false;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    if (j < N) {
+      uint64_t v = tile[j];
+      uint32_t e = (uint32_t)(v >> 52) & 0x7ffu;
+      nonfin |= e == 0x7ffu;
+      sub |= (e == 0u) && ((v << 12) != 0ull);
+    }
+  }
+  const int anynf = __syncthreads_or(nonfin);
+  const int anysub = __syncthreads_or(sub);
+  if (anynf) {
+    if (threadIdx.x == 0) atomicOr(err, (unsigned)E_NONFINITE);
+    return 0;
+  }
+  const uint32_t S = anysub ? 64u : S_req;
+  const uint64_t mask = trunc_mask(S);
+  // 2. truncate (and store -0 as +0)
+  uint64_t t[VPT];
+  bool nz = false;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    t[k] = 0;
+    if (j < N) {
+      uint64_t v = tile[j] & mask;
+      if (v == 0x8000000000000000ull) v = 0;
+      t[k] = v;
+      tile[j] = v;
+      nz |= v != 0;
+    }
+  }
+  __syncthreads();
+  // 3. codes and residual lengths
+  uint32_t c[VPT], r[VPT], sum = 0;
+  uint64_t prev = (j0 > 0 && j0 <= N) ? tile[j0 - 1] : 0ull;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    c[k] = 3u;
+    r[k] = 0u;
+    if (j < N) {
+      c[k] = xor_code(t[k], prev);
+      r[k] = resid_len(c[k], S);
+      sum += r[k];
+      prev = t[k];
+    }
+  }
+  // 4. ZERO and CONST tests
+  const uint64_t a0 = tile[0], a1 = tile[1];
+  bool cst = true;
+  for (uint32_t i = threadIdx.x; i < A; i += kThreads) cst &= (tile[2 * i] == a0) && (tile[2 * i + 1] == a1);
+  const int allzero = !__syncthreads_or(nz);
+  const int allconst = __syncthreads_and(cst);
+  // 5. offsets of the residual stream
+  uint32_t total;
+  const uint32_t o0 = block_excl_add(sum, s, &total);
+  // 6. smallest power-of-two period P (amplitudes) with 2 <= P < 2^kc
+  int period = -1;
+  if (kc >= 2) {
+    int p = kc - 1;
+    for (; p >= 1; --p) {
+      const uint32_t P = 1u << p;
+      bool ok = true;
+      for (uint32_t i = threadIdx.x; i < A; i += kThreads)
+        if (i & P) ok &= (tile[2 * i] == tile[2 * (i ^ P)]) && (tile[2 * i + 1] == tile[2 * (i ^ P) + 1]);
+      if (!__syncthreads_and(ok)) break;
+    }
+    if (p < kc - 1) period = p + 1;  // every bit from p+1 up to kc-1 left the chunk unchanged
+  }
+  // residual bits of the first 2P values
+  if (threadIdx.x == 0) s.bits_period = 0;
+  __syncthreads();
+  if (period > 0) {
+    const uint32_t nvp = 2u << period;
+    uint32_t o = o0;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (j0 + k == nvp) s.bits_period = o;
+      o += r[k];
+    }
+    __syncthreads();
+  }
+  const uint32_t bits_p = s.bits_period;
+  // 7. sizes and the choice
+  uint32_t size[M_NMODES];
+  size[M_ZERO] = allzero ? 16u : 0u;
+  size[M_CONST] = allconst ? 32u : 0u;
+  size[M_PERIOD] = period > 0 ? 16u + code_bytes(2u << period) + resid_bytes(bits_p) : 0u;
+  size[M_STREAM] = 16u + code_bytes(N) + resid_bytes(total);
+  size[M_RAW] = 16u + 8u * N;
+  uint32_t mode = 0, best = 0;
+  if (force_mode >= 0) {
+    if (force_mode >= (int)M_NMODES || size[force_mode] == 0 || size[force_mode] > img_cap) {
+      if (threadIdx.x == 0) atomicOr(err, (unsigned)E_MODE);
+      return 0;
+    }
+    mode = (uint32_t)force_mode;
+    best = size[mode];
+  } else {
+    best = 0xffffffffu;
+#pragma unroll
+    for (uint32_t m = 0; m < M_NMODES; ++m)
+      if (size[m] != 0 && size[m] < best) { best = size[m]; mode = m; }
+    if (best > img_cap) {  // cannot happen: RAW always fits a buffer of max_image_bytes
+      if (threadIdx.x == 0) atomicOr(err, (unsigned)E_MODE);
+      return 0;
+    }
+  }
+  // 8. write the image
+  uint32_t nv = 0, rbits = 0;
+  if (mode == M_CONST) nv = 2;
+  if (mode == M_PERIOD) { nv = 2u << period; rbits = bits_p; }
+  if (mode == M_STREAM) { nv = N; rbits = total; }
+  if (mode == M_RAW) nv = N;
+  uint64_t* pay64 = reinterpret_cast<uint64_t*>(img + 16);
+  const uint32_t plen = best - 16u;
+  for (uint32_t q = threadIdx.x; q < plen / 8u; q += kThreads) pay64[q] = 0ull;
+  if (threadIdx.x == 0) {
+    uint32_t* h = reinterpret_cast<uint32_t*>(img);
+    h[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | ((mode == M_PERIOD ? (uint32_t)period : 0u) << 16);
+    h[1] = plen;
+    h[2] = nv;
+    h[3] = rbits;
+  }
+  __syncthreads();
+  if (mode == M_CONST) {
+    if (threadIdx.x < 2) pay64[threadIdx.x] = tile[threadIdx.x];
+  } else if (mode == M_RAW) {
+    for (uint32_t j = threadIdx.x; j < N; j += kThreads) pay64[j] = tile[j];
+  } else if (mode == M_PERIOD || mode == M_STREAM) {
+    uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
+    uint64_t* words = reinterpret_cast<uint64_t*>(img + 16 + code_bytes(nv));
+    uint32_t cw = 0, cw_idx = 0xffffffffu;
+    uint64_t acc = 0;
+    uint32_t acc_w = 0xffffffffu;
+    uint32_t o = o0;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const uint32_t j = j0 + k;
+      if (j < nv) {
+        const uint32_t widx = j >> 4;
+        if (widx != cw_idx) {
+          if (cw_idx != 0xffffffffu && cw) atomicOr(&codes32[cw_idx], cw);
+          cw = 0;
+          cw_idx = widx;
+        }
+        cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
+        const uint32_t rr = r[k];
+        if (rr) {
+          const uint64_t val = (t[k] << (8u * c[k])) >> (64u - rr);
+          const uint32_t w = o >> 6, off = o & 63u;
+          if (w != acc_w) {
+            if (acc_w != 0xffffffffu && acc) atomicOr((unsigned long long*)&words[acc_w], (unsigned long long)acc);
+            acc = 0;
+            acc_w = w;
+          }
+          if (off + rr <= 64u) {
+            acc |= val << (64u - off - rr);
+          } else {
+            acc |= val >> (off + rr - 64u);
+            if (acc) atomicOr((unsigned long long*)&words[acc_w], (unsigned long long)acc);
+            acc_w = w + 1;
+            acc = val << (128u - off - rr);
+          }
+          o += rr;
+        }
+      }
+    }
+    if (cw_idx != 0xffffffffu && cw) atomicOr(&codes32[cw_idx], cw);
+    if (acc_w != 0xffffffffu && acc) atomicOr((unsigned long long*)&words[acc_w], (unsigned long long)acc);
+  }
+  __syncthreads();
+  return best;
+}
+
+// -------------------------------------------------------- gate arithmetic -- //
+// Coefficients of the four output components, four terms each, in a fixed order:
+//   a'r = u00r ar - u00i ai + u01r br - u01i bi      a'i = u00r ai + u00i ar + u01r bi + u01i br
+//   b'r = u10r ar - u10i ai + u11r br - u11i bi      b'i = u10r ai + u10i ar + u11r bi + u11i br
+// A term whose coefficient is exactly zero is left out; the first kept term is one
+// rounded product and every later term one fused multiply-add.  With no term the
+// result is +0.  A first-term coefficient of +-1 is an exact copy / sign flip,
+// which is what the rounded product gives.
+struct GateCoef {
+  double c[16];
+};
+
+__device__ __forceinline__ double row4(const double* c, double x0, double x1, double x2, double x3) {
+  const double xs[4] = {x0, x1, x2, x3};
+  double acc = 0.0;
+  bool have = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double ck = c[k];
+    if (ck != 0.0) {
+      if (!have) {
+        if (ck == 1.0) acc = xs[k];
+        else if (ck == -1.0) acc = __longlong_as_double(__double_as_longlong(xs[k]) ^ (long long)0x8000000000000000ull);
+        else acc = __dmul_rn(ck, xs[k]);
+        have = true;
+      } else {
+        acc = __fma_rn(ck, xs[k], acc);
+      }
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void apply_pair(const GateCoef& g, double2& a, double2& b) {
+  const double ar = a.x, ai = a.y, br = b.x, bi = b.y;
+  double2 na, nb;
+  na.x = row4(g.c + 0, ar, ai, br, bi);
+  na.y = row4(g.c + 4, ai, ar, bi, br);
+  nb.x = row4(g.c + 8, ar, ai, br, bi);
+  nb.y = row4(g.c + 12, ai, ar, bi, br);
+  a = na;
+  b = nb;
+}
+
+// --------------------------------------------------------------- pool ---- //
+__device__ __forceinline__ uint32_t* dir_entry(const Pool& P, unsigned long long chunk) {
+  return P.dir + chunk * (unsigned long long)P.dir_words;
+}
+
+// Stages chunk's image into smem (all threads).  Returns the image length.
+__device__ __forceinline__ uint32_t load_image_block(const Pool& P, unsigned long long chunk, uint8_t* smem_img,
+                                                     uint32_t* smem_pages, uint32_t cap) {
+  const uint32_t* e = dir_entry(P, chunk);
+  const uint32_t bytes = e[0], np = e[1];
+  if (bytes > cap) return bytes;  // caller reports corruption
+  uint4* dst = reinterpret_cast<uint4*>(smem_img);
+  const uint32_t units = bytes >> 4;
+  if (np == 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(e + 4);
+    for (uint32_t u = threadIdx.x; u < units; u += kThreads) dst[u] = src[u];
+  } else {
+    for (uint32_t q = threadIdx.x; q < np; q += kThreads) smem_pages[q] = e[4 + q];
+    __syncthreads();
+    constexpr uint32_t upp = kPage / 16;
+    for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
+      const uint32_t pid = smem_pages[u / upp];
+      const uint4* src = reinterpret_cast<const uint4*>(P.pages + (unsigned long long)pid * kPage);
+      dst[u] = __ldcs(src + (u % upp));
+    }
+  }
+  __syncthreads();
+  return bytes;
+}
+
+struct CtaCache {
+  uint32_t* ids;  // global, kCacheCap entries of this CTA
+  uint32_t n;     // kept in shared memory by thread 0
+};
+
+// Thread 0 only: returns the chunk's old pages to this CTA's cache (overflow to the
+// global freed list, merged into the stack after the gate).
+__device__ __forceinline__ void free_pages_t0(const Pool& P, CtaCache& cc, const uint32_t* smem_pages, uint32_t np) {
+  for (uint32_t q = 0; q < np; ++q) {
+    if (cc.n < (uint32_t)kCacheCap) {
+      cc.ids[cc.n++] = smem_pages[q];
+    } else {
+      unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->nfreed), 1ull);
+      P.freed[pos] = smem_pages[q];
+    }
+  }
+}
+
+// Thread 0 only: takes np pages (cache first, then the global stack).  False: pool dry.
+__device__ __forceinline__ bool alloc_pages_t0(const Pool& P, CtaCache& cc, uint32_t* out, uint32_t np) {
+  uint32_t q = 0;
+  while (q < np && cc.n > 0) out[q++] = cc.ids[--cc.n];
+  if (q < np) {
+    const long long need = (long long)(np - q);
+    const long long old = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top),
+                                               (unsigned long long)(-need));
+    if (old - need < 0) return false;
+    for (long long k = 0; k < need; ++k) out[q++] = P.stack[old - 1 - k];
+  }
+  return true;
+}
+
+// Writes the image in smem to the chunk (inline in the directory when it fits,
+// else to freshly allocated pages) and updates the directory entry.  All threads.
+// smem_pages must hold the page ids (thread 0 allocated them).
+__device__ __forceinline__ void store_image_block(const Pool& P, unsigned long long chunk, const uint8_t* smem_img,
+                                                  uint32_t bytes, const uint32_t* smem_pages, uint32_t np) {
+  uint32_t* e = dir_entry(P, chunk);
+  const uint4* src = reinterpret_cast<const uint4*>(smem_img);
+  const uint32_t units = bytes >> 4;
+  if (np == 0) {
+    uint4* dst = reinterpret_cast<uint4*>(e + 4);
+    for (uint32_t u = threadIdx.x; u < units; u += kThreads) dst[u] = src[u];
+  } else {
+    constexpr uint32_t upp = kPage / 16;
+    for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
+      uint4* dst = reinterpret_cast<uint4*>(P.pages + (unsigned long long)smem_pages[u / upp] * kPage);
+      __stcs(dst + (u % upp), src[u]);
+    }
+    for (uint32_t q = threadIdx.x; q < np; q += kThreads) e[4 + q] = smem_pages[q];
+  }
+  if (threadIdx.x == 0) {
+    e[0] = bytes;
+    e[1] = np;
+  }
+}
+
+__host__ __device__ __forceinline__ uint32_t pages_for(uint32_t bytes, int kc) {
+  return bytes <= inline_cap(kc) ? 0u : (bytes + kPage - 1) / kPage;
+}
+
+// Scatter the bits of j into the positions that are set in `free_mask` (low first).
+__device__ __forceinline__ unsigned long long deposit_bits(unsigned long long j, unsigned long long free_mask) {
+  unsigned long long out = 0;
+  while (free_mask) {
+    const unsigned long long low = free_mask & (~free_mask + 1ull);
+    if (j & 1ull) out |= low;
+    j >>= 1;
+    free_mask ^= low;
+  }
+  return out;
+}
+
+}  // namespace qc

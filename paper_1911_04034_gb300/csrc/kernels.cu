@@ -1,0 +1,607 @@
+// kernels.cu -- CUDA kernels of libqcsim (sm_103a).
+//
+// k_gate   the fused persistent kernel of the hot path: for each work item (two
+//          chunks) it stages the compressed images in shared memory, decodes them,
+//          applies the gate to every amplitude pair (Section 3.1, Eq. matrix1/2) and
+//          re-encodes them with the hybrid codec (Section 4.2, Solution C) under the
+//          bound chosen by the controller (Section 3.7), then commits the new images
+//          to the page pool.  Decoded amplitudes never leave shared memory.
+// k_post   after each gate: returns freed pages to the stack, adds the gate's byte
+//          change to E, and records the controller's level and fidelity bounds.
+// others   initialisation, codec entry points, readout and the uncompressed path.
+#include "launch.h"
+
+namespace qc {
+
+int vpt_for(int kc) {
+  const int N = 2 << kc;
+  return N <= kThreads ? 1 : N / kThreads;
+}
+__host__ __device__ __forceinline__ uint32_t imgcap(int kc) { return round16(max_image_bytes(kc)); }
+// staging buffer of the codec entry points: any forced image fits
+__host__ __device__ __forceinline__ uint32_t codedcap(int kc) { return round16(max_coded_bytes(kc)); }
+__host__ __device__ __forceinline__ uint32_t pagelist_words(int kc) { return (max_pages(kc) + 3u) & ~3u; }
+
+size_t gate_smem_bytes(int kc) {
+  const size_t N = size_t(2) << kc;
+  return 2 * N * 8 + 2 * size_t(imgcap(kc)) + 2 * 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
+}
+size_t codec_smem_bytes(int kc) {
+  const size_t N = size_t(2) << kc;
+  return N * 8 + size_t(codedcap(kc)) + 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
+}
+
+// ------------------------------------------------------------- the gate -- //
+template <int VPT>
+__global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int kc = L.P.kc;
+  const uint32_t N = 2u << kc, A = 1u << kc;
+  const uint32_t cap = imgcap(kc);
+  uint64_t* tile0 = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* tile1 = tile0 + N;
+  uint8_t* img0 = reinterpret_cast<uint8_t*>(tile1 + N);
+  uint8_t* img1 = img0 + cap;
+  uint32_t* pages0 = reinterpret_cast<uint32_t*>(img1 + cap);
+  uint32_t* pages1 = pages0 + pagelist_words(kc);
+  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages1 + pagelist_words(kc));
+  __shared__ int s_oom;
+  __shared__ uint32_t s_np[2];
+
+  const Pool& P = L.P;
+  DevCtl* ctl = P.ctl;
+  // Section 3.7: the bound for this gate, from E after the previous gate.  Every CTA
+  // evaluates the same rule on the same values (k_post alone writes them).
+  const int lvl = next_level(L.ctl, ctl->E, ctl->level);
+  const uint32_t S = (uint32_t)level_bits(L.ctl, lvl);
+
+  CtaCache cc;
+  cc.ids = P.cache + (size_t)blockIdx.x * kCacheCap;
+  cc.n = 0;
+  if (threadIdx.x == 0) cc.n = P.cache_n[blockIdx.x];
+  long long dE = 0;
+  unsigned long long rd = 0, wr = 0;
+
+  for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x) {
+    // one barrier that also broadcasts thread 0's view of the error word
+    if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned int*)&ctl->err) != 0u)) break;
+    unsigned long long c0, c1;
+    bool has1;
+    if (L.pair) {
+      c0 = deposit_bits(item, L.free_mask) | L.hi_vals;
+      c1 = c0 | L.pair_bit;
+      has1 = true;
+    } else {
+      const unsigned long long k0 = 2ull * item;
+      c0 = deposit_bits(k0, L.free_mask) | L.hi_vals;
+      has1 = k0 + 1 < L.nact;
+      c1 = has1 ? (deposit_bits(k0 + 1, L.free_mask) | L.hi_vals) : 0ull;
+    }
+    const uint32_t* e0 = dir_entry(P, c0);
+    const uint32_t* e1 = dir_entry(P, c1);
+    const uint32_t np0 = e0[1], np1 = has1 ? e1[1] : 0u;
+    const uint32_t b0 = e0[0], b1 = has1 ? e1[0] : 0u;
+    if (b0 > cap || b1 > cap || np0 > max_pages(kc) || np1 > max_pages(kc)) {
+      if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
+      break;
+    }
+    // An all-zero chunk maps to an all-zero chunk under any gate (signed zeros are
+    // stored as +0), and its image does not depend on the bound: skip it.
+    const bool z0 = np0 == 0 && b0 == 16u && e0[4] == 0u;
+    const bool z1 = !has1 || (np1 == 0 && b1 == 16u && e1[4] == 0u);
+    rd += b0 + b1;
+    if (z0 && z1) continue;
+
+    load_image_block(P, c0, img0, pages0, cap);
+    if (has1) load_image_block(P, c1, img1, pages1, cap);
+    if (threadIdx.x == 0) {
+      free_pages_t0(P, cc, pages0, np0);
+      if (has1) free_pages_t0(P, cc, pages1, np1);
+    }
+    const bool ok0 = decode_block<VPT>(img0, b0, kc, tile0, s);
+    const bool ok1 = has1 ? decode_block<VPT>(img1, b1, kc, tile1, s) : true;
+    if (!ok0 || !ok1) {
+      if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
+      break;
+    }
+    // apply the gate to every amplitude pair whose in-chunk control bits match
+    double2* t0 = reinterpret_cast<double2*>(tile0);
+    double2* t1 = reinterpret_cast<double2*>(tile1);
+    if (L.pair) {
+      for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+        if ((i & L.lo_mask) != L.lo_vals) continue;
+        double2 a = t0[i], b = t1[i];
+        apply_pair(L.g, a, b);
+        t0[i] = a;
+        t1[i] = b;
+      }
+    } else {
+      const uint32_t tb = 1u << L.target, lowm = tb - 1u;
+      const uint32_t tot = has1 ? A : A / 2u;  // pairs over both tiles
+      for (uint32_t q = threadIdx.x; q < tot; q += kThreads) {
+        const uint32_t p = q & (A / 2u - 1u);
+        double2* tt = (q < A / 2u) ? t0 : t1;
+        const uint32_t i0 = ((p & ~lowm) << 1) | (p & lowm);
+        if ((i0 & L.lo_mask) != L.lo_vals) continue;
+        double2 a = tt[i0], b = tt[i0 | tb];
+        apply_pair(L.g, a, b);
+        tt[i0] = a;
+        tt[i0 | tb] = b;
+      }
+    }
+    __syncthreads();
+    const uint32_t n0 = encode_block<VPT>(tile0, kc, S, -1, img0, cap, s, &ctl->err);
+    const uint32_t n1 = has1 ? encode_block<VPT>(tile1, kc, S, -1, img1, cap, s, &ctl->err) : 1u;
+    if (n0 == 0u || n1 == 0u) break;
+    if (threadIdx.x == 0) {
+      s_np[0] = pages_for(n0, kc);
+      s_np[1] = has1 ? pages_for(n1, kc) : 0u;
+      bool ok = alloc_pages_t0(P, cc, pages0, s_np[0]);
+      if (ok && has1) ok = alloc_pages_t0(P, cc, pages1, s_np[1]);
+      if (!ok) atomicOr(&ctl->err, (unsigned)E_OOM);
+      s_oom = !ok;
+    }
+    __syncthreads();
+    if (s_oom) break;
+    store_image_block(P, c0, img0, n0, pages0, s_np[0]);
+    if (has1) store_image_block(P, c1, img1, n1, pages1, s_np[1]);
+    dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
+    wr += n0 + (has1 ? n1 : 0u);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.cache_n[blockIdx.x] = cc.n;
+    if (dE) atomicAdd(&ctl->dE, (unsigned long long)dE);
+    if (rd) atomicAdd(&ctl->bytes_in, rd);
+    if (wr) atomicAdd(&ctl->bytes_out, wr);
+  }
+}
+
+// After a gate: free pages back to the stack, then the controller bookkeeping.
+__global__ void __launch_bounds__(1024) k_post(const Pool P, const CtlParams cp, int grid_ctas) {
+  DevCtl* ctl = P.ctl;
+  __shared__ unsigned long long s_top;
+  if (threadIdx.x == 0) s_top = (unsigned long long)ctl->top;
+  __syncthreads();
+  const unsigned long long slots = (unsigned long long)grid_ctas * kCacheCap;
+  for (unsigned long long q = threadIdx.x; q < slots; q += blockDim.x) {
+    const unsigned long long b = q / kCacheCap, i = q % kCacheCap;
+    if (i < P.cache_n[b]) {
+      const unsigned long long pos = atomicAdd(&s_top, 1ull);
+      P.stack[pos] = P.cache[q];
+    }
+  }
+  const unsigned long long nf = ctl->nfreed;
+  for (unsigned long long i = threadIdx.x; i < nf; i += blockDim.x) {
+    const unsigned long long pos = atomicAdd(&s_top, 1ull);
+    P.stack[pos] = P.freed[i];
+  }
+  __syncthreads();
+  for (unsigned long long b = threadIdx.x; b < (unsigned long long)grid_ctas; b += blockDim.x) P.cache_n[b] = 0;
+  if (threadIdx.x == 0) {
+    ctl->top = (long long)s_top;
+    ctl->nfreed = 0;
+    const int lvl = next_level(cp, ctl->E, ctl->level);
+    const int S = level_bits(cp, lvl);
+    if (lvl > 0 && ctl->switch_gate < 0) ctl->switch_gate = (long long)ctl->gates;
+    if (S < 64) {
+      ctl->lb_sum += cp.delta[lvl - 1];
+      ctl->lb_prod *= (1.0 - cp.delta[lvl - 1]);
+    }
+    ctl->level = lvl;
+    ctl->S_last = S;
+    ctl->E += ctl->dE;
+    ctl->dE = 0;
+    if (ctl->E > ctl->Emax) ctl->Emax = ctl->E;
+    ctl->gates += 1;
+    const unsigned long long in_use = P.npages - s_top;
+    if (in_use > ctl->peak_pages) ctl->peak_pages = in_use;
+  }
+}
+
+// ------------------------------------------------------------ initialise -- //
+__global__ void k_pool_init(const Pool P, unsigned long long nchunks) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P.npages; i += stride)
+    P.stack[i] = (uint32_t)i;
+  // every chunk starts as a ZERO image held inline: header only, all fields 0
+  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nchunks; c += stride) {
+    uint32_t* e = dir_entry(P, c);
+    e[0] = 16u;
+    e[1] = 0u;
+    e[2] = e[3] = 0u;
+    e[4] = e[5] = e[6] = e[7] = 0u;
+  }
+}
+
+// Chunk 0 holds amplitude 1 at index 0 (the state |0...0>), encoded losslessly.
+template <int VPT>
+__global__ void __launch_bounds__(kThreads) k_init_chunk0(const Pool P, unsigned long long nchunks) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int kc = P.kc;
+  const uint32_t N = 2u << kc, cap = codedcap(kc);
+  uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
+  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  __shared__ uint32_t s_np;
+  __shared__ int s_ok;
+  for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[j] = j == 0 ? 0x3FF0000000000000ull : 0ull;
+  __syncthreads();
+  const uint32_t n0 = encode_block<VPT>(tile, kc, 64u, -1, img, imgcap(kc), s, &P.ctl->err);
+  if (threadIdx.x == 0) {
+    s_np = pages_for(n0, kc);
+    CtaCache cc;
+    cc.ids = nullptr;
+    cc.n = 0;
+    s_ok = n0 != 0u && alloc_pages_t0(P, cc, pages, s_np);
+    if (!s_ok) atomicOr(&P.ctl->err, (unsigned)E_OOM);
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  store_image_block(P, 0ull, img, n0, pages, s_np);
+  if (threadIdx.x == 0) {
+    P.ctl->E = 16ull * (nchunks - 1ull) + n0;
+    P.ctl->Emax = P.ctl->E;
+    P.ctl->peak_pages = P.npages - (unsigned long long)P.ctl->top;
+  }
+}
+
+// -------------------------------------------------------- codec entries -- //
+template <int VPT>
+__global__ void __launch_bounds__(kThreads)
+    k_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force, uint8_t* out,
+                   unsigned long long stride, uint32_t* lens, unsigned int* err) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t N = 2u << kc, cap = codedcap(kc);
+  uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
+  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in) + c * N;
+    for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[j] = src[j];
+    __syncthreads();
+    const uint32_t n = encode_block<VPT>(tile, kc, S, force, img, cap, s, err);
+    uint4* dst = reinterpret_cast<uint4*>(out + c * stride);
+    const uint4* sv = reinterpret_cast<const uint4*>(img);
+    for (uint32_t u = threadIdx.x; u < n / 16u; u += kThreads) dst[u] = sv[u];
+    if (threadIdx.x == 0) lens[c] = n;
+    __syncthreads();
+  }
+}
+
+template <int VPT>
+__global__ void __launch_bounds__(kThreads)
+    k_codec_decode(const uint8_t* in, unsigned long long stride, const uint32_t* lens, unsigned long long nchunks,
+                   int kc, double* out, unsigned int* err) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t N = 2u << kc, cap = codedcap(kc);
+  uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
+  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint32_t len = lens[c];
+    const bool fits = len <= cap && (len & 15u) == 0u && len >= 16u;
+    if (fits) {
+      const uint4* src = reinterpret_cast<const uint4*>(in + c * stride);
+      uint4* d = reinterpret_cast<uint4*>(img);
+      for (uint32_t u = threadIdx.x; u < len / 16u; u += kThreads) d[u] = src[u];
+    } else if (threadIdx.x == 0) {
+      reinterpret_cast<uint32_t*>(img)[0] = 0xffu;  // fails the header checks
+    }
+    __syncthreads();
+    const bool ok = decode_block<VPT>(img, fits ? len : 16u, kc, tile, s);
+    if (!ok && threadIdx.x == 0) atomicOr(err, (unsigned)E_CORRUPT);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(out) + c * N;
+    for (uint32_t j = threadIdx.x; j < N; j += kThreads) dst[j] = tile[j];
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------- readout -- //
+// Decodes the chunks overlapping [first_amp, first_amp + count) into out.
+template <int VPT>
+__global__ void __launch_bounds__(kThreads)
+    k_decode_range(const Pool P, unsigned long long first_amp, unsigned long long count, double* out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int kc = P.kc;
+  const uint32_t N = 2u << kc, A = 1u << kc, cap = imgcap(kc);
+  uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
+  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  const unsigned long long cfirst = first_amp >> kc, clast = (first_amp + count - 1ull) >> kc;
+  for (unsigned long long c = cfirst + blockIdx.x; c <= clast; c += gridDim.x) {
+    const uint32_t* e = dir_entry(P, c);
+    const uint32_t b = e[0];
+    if (b > cap || e[1] > max_pages(kc)) {
+      if (threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+      return;
+    }
+    load_image_block(P, c, img, pages, cap);
+    if (!decode_block<VPT>(img, b, kc, tile, s) && threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+    const unsigned long long base = c << kc;
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(out);
+    for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+      const unsigned long long a = base + i;
+      if (a >= first_amp && a < first_amp + count) {
+        dst[2 * (a - first_amp)] = tile[2 * i];
+        dst[2 * (a - first_amp) + 1] = tile[2 * i + 1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Per chunk: sum over its amplitudes of fma(re, re, im*im) (measurement), or the
+// partial inner product with a reference state and the norm (fidelity).
+template <int VPT, bool DOT>
+__global__ void __launch_bounds__(kThreads)
+    k_chunk_reduce(const Pool P, unsigned long long cfirst, unsigned long long nchunks, const double* ref, double* out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int kc = P.kc;
+  const uint32_t N = 2u << kc, A = 1u << kc, cap = imgcap(kc);
+  uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
+  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  __shared__ double red[3][kThreads];
+  for (unsigned long long cl = blockIdx.x; cl < nchunks; cl += gridDim.x) {
+    const unsigned long long c = cfirst + cl;
+    const uint32_t* e = dir_entry(P, c);
+    const uint32_t b = e[0];
+    if (b > cap || e[1] > max_pages(kc)) {
+      if (threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+      return;
+    }
+    load_image_block(P, c, img, pages, cap);
+    if (!decode_block<VPT>(img, b, kc, tile, s) && threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+    const double* v = reinterpret_cast<const double*>(tile);
+    double x = 0.0, y = 0.0, z = 0.0;
+    for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+      const double pr = v[2 * i], pi = v[2 * i + 1];
+      z += __fma_rn(pr, pr, __dmul_rn(pi, pi));
+      if (DOT) {
+        const double rr = ref[(cl << kc) * 2 + 2 * i], ri = ref[(cl << kc) * 2 + 2 * i + 1];
+        x += rr * pr + ri * pi;
+        y += rr * pi - ri * pr;
+      }
+    }
+    red[0][threadIdx.x] = x;
+    red[1][threadIdx.x] = y;
+    red[2][threadIdx.x] = z;
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) {
+        red[0][threadIdx.x] += red[0][threadIdx.x + h];
+        red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        red[2][threadIdx.x] += red[2][threadIdx.x + h];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (DOT) {
+        out[3 * cl] = red[0][0];
+        out[3 * cl + 1] = red[1][0];
+        out[3 * cl + 2] = red[2][0];
+      } else {
+        out[cl] = red[2][0];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_mode_counts(const Pool P, unsigned long long nchunks, unsigned long long* counts) {
+  __shared__ unsigned long long sc[8];
+  if (threadIdx.x < 8) sc[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nchunks; c += stride) {
+    const uint32_t* e = dir_entry(P, c);
+    uint32_t h = e[4];
+    if (e[1] != 0u) h = *reinterpret_cast<const uint32_t*>(P.pages + (unsigned long long)e[4] * kPage);
+    atomicAdd(&sc[h & 7u], 1ull);
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+}
+
+__global__ void k_copy_image(const Pool P, unsigned long long chunk, uint8_t* out) {
+  const uint32_t* e = dir_entry(P, chunk);
+  const uint32_t b = e[0], np = e[1];
+  if (b > max_image_bytes(P.kc) || np > max_pages(P.kc)) return;
+  for (uint32_t u = threadIdx.x; u < b / 16u; u += blockDim.x) {
+    uint4 v;
+    if (np == 0) v = reinterpret_cast<const uint4*>(e + 4)[u];
+    else v = reinterpret_cast<const uint4*>(P.pages + (unsigned long long)e[4 + u / (kPage / 16)] * kPage)[u % (kPage / 16)];
+    reinterpret_cast<uint4*>(out)[u] = v;
+  }
+}
+
+// ------------------------------------------------------ uncompressed path -- //
+__global__ void k_sv_init(double2* psi, unsigned long long amps) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < amps; i += stride)
+    psi[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void __launch_bounds__(256) k_sv_gate(double2* psi, unsigned long long npairs, const GateCoef g, int target,
+                                                 unsigned long long cmask, unsigned long long cvals) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long tb = 1ull << target, lowm = tb - 1ull;
+  for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < npairs; p += stride) {
+    const unsigned long long i0 = ((p & ~lowm) << 1) | (p & lowm);
+    if ((i0 & cmask) != cvals) continue;
+    double2 a = psi[i0], b = psi[i0 | tb];
+    apply_pair(g, a, b);
+    psi[i0] = a;
+    psi[i0 | tb] = b;
+  }
+}
+
+// ------------------------------------------------------------- launchers -- //
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+#define QC_VPT_DISPATCH(kc, ...)                          \
+  switch (vpt_for(kc)) {                                  \
+    case 1: { constexpr int V = 1; __VA_ARGS__; } break;  \
+    case 2: { constexpr int V = 2; __VA_ARGS__; } break;  \
+    case 4: { constexpr int V = 4; __VA_ARGS__; } break;  \
+    case 8: { constexpr int V = 8; __VA_ARGS__; } break;  \
+    case 16: { constexpr int V = 16; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;                \
+  }
+
+int gate_ctas_per_sm(int kc) {
+  int n = 0;
+  const size_t smem = gate_smem_bytes(kc);
+  cudaError_t e = cudaSuccess;
+  switch (vpt_for(kc)) {
+    case 1: prep(k_gate<1>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gate<1>, kThreads, smem); break;
+    case 2: prep(k_gate<2>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gate<2>, kThreads, smem); break;
+    case 4: prep(k_gate<4>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gate<4>, kThreads, smem); break;
+    case 8: prep(k_gate<8>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gate<8>, kThreads, smem); break;
+    case 16: prep(k_gate<16>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gate<16>, kThreads, smem); break;
+  }
+  if (e != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+cudaError_t launch_gate(const GateLaunch& L, int grid, cudaStream_t st) {
+  const size_t smem = gate_smem_bytes(L.P.kc);
+  QC_VPT_DISPATCH(L.P.kc, {
+    cudaError_t e = prep(k_gate<V>, smem);
+    if (e != cudaSuccess) return e;
+    k_gate<V><<<grid, kThreads, smem, st>>>(L);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_post(const Pool& P, const CtlParams& cp, int grid_ctas, cudaStream_t st) {
+  k_post<<<1, 1024, 0, st>>>(P, cp, grid_ctas);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pool_init(const Pool& P, unsigned long long nchunks, cudaStream_t st) {
+  k_pool_init<<<num_sms() * 4, 256, 0, st>>>(P, nchunks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_chunk0(const Pool& P, unsigned long long nchunks, cudaStream_t st) {
+  const size_t smem = codec_smem_bytes(P.kc);
+  QC_VPT_DISPATCH(P.kc, {
+    cudaError_t e = prep(k_init_chunk0<V>, smem);
+    if (e != cudaSuccess) return e;
+    k_init_chunk0<V><<<1, kThreads, smem, st>>>(P, nchunks);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force,
+                                uint8_t* out, unsigned long long stride, uint32_t* lens, unsigned int* err,
+                                cudaStream_t st) {
+  const size_t smem = codec_smem_bytes(kc);
+  const unsigned long long g = nchunks < (unsigned long long)num_sms() * 8 ? nchunks : (unsigned long long)num_sms() * 8;
+  QC_VPT_DISPATCH(kc, {
+    cudaError_t e = prep(k_codec_encode<V>, smem);
+    if (e != cudaSuccess) return e;
+    k_codec_encode<V><<<(unsigned)g, kThreads, smem, st>>>(in, nchunks, kc, S, force, out, stride, lens, err);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codec_decode(const uint8_t* in, unsigned long long stride, const uint32_t* lens,
+                                unsigned long long nchunks, int kc, double* out, unsigned int* err, cudaStream_t st) {
+  const size_t smem = codec_smem_bytes(kc);
+  const unsigned long long g = nchunks < (unsigned long long)num_sms() * 8 ? nchunks : (unsigned long long)num_sms() * 8;
+  QC_VPT_DISPATCH(kc, {
+    cudaError_t e = prep(k_codec_decode<V>, smem);
+    if (e != cudaSuccess) return e;
+    k_codec_decode<V><<<(unsigned)g, kThreads, smem, st>>>(in, stride, lens, nchunks, kc, out, err);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_range(const Pool& P, unsigned long long first_amp, unsigned long long count, double* out,
+                                cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const size_t smem = codec_smem_bytes(P.kc);
+  const unsigned long long nch = ((first_amp + count - 1ull) >> P.kc) - (first_amp >> P.kc) + 1ull;
+  const unsigned long long g = nch < (unsigned long long)num_sms() * 8 ? nch : (unsigned long long)num_sms() * 8;
+  QC_VPT_DISPATCH(P.kc, {
+    cudaError_t e = prep(k_decode_range<V>, smem);
+    if (e != cudaSuccess) return e;
+    k_decode_range<V><<<(unsigned)g, kThreads, smem, st>>>(P, first_amp, count, out);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_norms(const Pool& P, unsigned long long cfirst, unsigned long long nchunks, double* out,
+                              cudaStream_t st) {
+  const size_t smem = codec_smem_bytes(P.kc);
+  const unsigned long long g = nchunks < (unsigned long long)num_sms() * 8 ? nchunks : (unsigned long long)num_sms() * 8;
+  QC_VPT_DISPATCH(P.kc, {
+    cudaError_t e = prep(k_chunk_reduce<V, false>, smem);
+    if (e != cudaSuccess) return e;
+    k_chunk_reduce<V, false><<<(unsigned)g, kThreads, smem, st>>>(P, cfirst, nchunks, nullptr, out);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_dots(const Pool& P, unsigned long long cfirst, unsigned long long nchunks, const double* ref,
+                             double* out, cudaStream_t st) {
+  const size_t smem = codec_smem_bytes(P.kc);
+  const unsigned long long g = nchunks < (unsigned long long)num_sms() * 8 ? nchunks : (unsigned long long)num_sms() * 8;
+  QC_VPT_DISPATCH(P.kc, {
+    cudaError_t e = prep(k_chunk_reduce<V, true>, smem);
+    if (e != cudaSuccess) return e;
+    k_chunk_reduce<V, true><<<(unsigned)g, kThreads, smem, st>>>(P, cfirst, nchunks, ref, out);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mode_counts(const Pool& P, unsigned long long nchunks, unsigned long long* counts,
+                               cudaStream_t st) {
+  const unsigned long long blocks = (nchunks + 255ull) / 256ull;
+  const unsigned g = (unsigned)(blocks < (unsigned long long)num_sms() * 8 ? blocks : (unsigned long long)num_sms() * 8);
+  k_mode_counts<<<g, 256, 0, st>>>(P, nchunks, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_image(const Pool& P, unsigned long long chunk, uint8_t* out, cudaStream_t st) {
+  k_copy_image<<<1, 256, 0, st>>>(P, chunk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sv_init(double* psi, unsigned long long amps, cudaStream_t st) {
+  k_sv_init<<<num_sms() * 8, 256, 0, st>>>(reinterpret_cast<double2*>(psi), amps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sv_gate(double* psi, int n, const GateCoef& g, int target, unsigned long long cmask,
+                           unsigned long long cvals, cudaStream_t st) {
+  const unsigned long long npairs = 1ull << (n - 1);
+  const unsigned long long want = (npairs + 255ull) / 256ull;
+  const unsigned grid = (unsigned)(want < (unsigned long long)num_sms() * 16 ? want : (unsigned long long)num_sms() * 16);
+  k_sv_gate<<<grid, 256, 0, st>>>(reinterpret_cast<double2*>(psi), npairs, g, target, cmask, cvals);
+  return cudaGetLastError();
+}
+
+}  // namespace qc

@@ -1,0 +1,53 @@
+// launch.h -- host-side launch wrappers of the kernels in kernels.cu (internal).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace qc {
+
+// One gate on the compressed state.
+struct GateLaunch {
+  Pool P;
+  CtlParams ctl;
+  GateCoef g;
+  unsigned long long items;      // work items (chunk pairs)
+  unsigned long long nact;       // active chunks (in-chunk gates pair them up)
+  unsigned long long free_mask;  // chunk-index bits enumerated by the item counter
+  unsigned long long hi_vals;    // control values on chunk-index bits
+  unsigned long long pair_bit;   // chunk-index bit of the target (cross-chunk gates), else 0
+  uint32_t lo_mask, lo_vals;     // controls inside a chunk
+  int target;                    // target bit (in-chunk gates)
+  int pair;                      // 1: target >= chunk_log2
+};
+
+int vpt_for(int kc);
+size_t gate_smem_bytes(int kc);
+size_t codec_smem_bytes(int kc);
+int gate_ctas_per_sm(int kc);
+
+cudaError_t launch_gate(const GateLaunch& L, int grid, cudaStream_t st);
+cudaError_t launch_post(const Pool& P, const CtlParams& cp, int grid_ctas, cudaStream_t st);
+cudaError_t launch_pool_init(const Pool& P, unsigned long long nchunks, cudaStream_t st);
+cudaError_t launch_init_chunk0(const Pool& P, unsigned long long nchunks, cudaStream_t st);
+cudaError_t launch_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force,
+                                uint8_t* out, unsigned long long stride, uint32_t* lens, unsigned int* err,
+                                cudaStream_t st);
+cudaError_t launch_codec_decode(const uint8_t* in, unsigned long long stride, const uint32_t* lens,
+                                unsigned long long nchunks, int kc, double* out, unsigned int* err, cudaStream_t st);
+cudaError_t launch_decode_range(const Pool& P, unsigned long long first_amp, unsigned long long count, double* out,
+                                cudaStream_t st);
+cudaError_t launch_chunk_norms(const Pool& P, unsigned long long cfirst, unsigned long long nchunks, double* out,
+                              cudaStream_t st);
+cudaError_t launch_chunk_dots(const Pool& P, unsigned long long cfirst, unsigned long long nchunks, const double* ref,
+                             double* out, cudaStream_t st);
+cudaError_t launch_mode_counts(const Pool& P, unsigned long long nchunks, unsigned long long* counts,
+                               cudaStream_t st);
+cudaError_t launch_copy_image(const Pool& P, unsigned long long chunk, uint8_t* out, cudaStream_t st);
+
+cudaError_t launch_sv_init(double* psi, unsigned long long amps, cudaStream_t st);
+cudaError_t launch_sv_gate(double* psi, int n, const GateCoef& g, int target, unsigned long long cmask,
+                           unsigned long long cvals, cudaStream_t st);
+
+}  // namespace qc

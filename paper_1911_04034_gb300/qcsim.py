@@ -1,0 +1,319 @@
+"""ctypes binding of libqcsim (include/qcsim.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels.  There is no CPU
+fallback: if libqcsim.so cannot be loaded this module raises.  Device buffers may be
+torch CUDA tensors (their data_ptr() is passed through); host buffers are numpy
+arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_CORRUPT, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "SIM_OK", -1: "SIM_ERR_INVALID", -2: "SIM_ERR_OOM", -3: "SIM_ERR_CUDA", -4: "SIM_ERR_CORRUPT",
+                -5: "SIM_ERR_TIMEOUT", -6: "SIM_ERR_STATE"}
+
+# sim_gate: int32 target, int32 kind, uint64 ctrl_mask, uint64 ctrl_vals, double u[8]
+SIM_GATE = np.dtype([("target", "<i4"), ("kind", "<i4"), ("ctrl_mask", "<u8"), ("ctrl_vals", "<u8"),
+                     ("u", "<f8", (8,))])
+assert SIM_GATE.itemsize == 88
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, call: str, msg: str):
+        super().__init__(f"{call}: {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("gates", C.c_uint64), ("encoded_bytes", C.c_uint64), ("max_encoded_bytes", C.c_uint64),
+        ("raw_bytes", C.c_uint64), ("inflight_bytes", C.c_uint64), ("chunks_by_mode", C.c_uint64 * 8),
+        ("pool_bytes", C.c_uint64), ("pages_in_use_bytes", C.c_uint64), ("peak_pages_bytes", C.c_uint64),
+        ("device_bytes", C.c_uint64), ("amp_updates", C.c_uint64),
+        ("ratio", C.c_double), ("min_ratio", C.c_double), ("eps_current", C.c_double),
+        ("fidelity_lb_sum", C.c_double), ("fidelity_lb_prod", C.c_double), ("eps_switch_gate", C.c_int64),
+        ("sig_bits_current", C.c_int32), ("level", C.c_int32), ("chunk_log2", C.c_int32), ("block_log2", C.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["chunks_by_mode"] = list(self.chunks_by_mode)
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Loads libqcsim.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libqcsim.so is missing; the CUDA library must be built (nvcc, sm_103a)")
+        L = C.CDLL(path)
+        vp, u64, i32, dbl, sz = C.c_void_p, C.c_uint64, C.c_int, C.c_double, C.c_size_t
+        pp = C.POINTER(C.c_void_p)
+        sig = {
+            "sim_create": [i32, i32, dbl, pp],
+            "sim_create_ex": [i32, i32, i32, dbl, u64, dbl, i32, u64, pp],
+            "sim_destroy": [vp],
+            "sim_set_stream": [vp, vp],
+            "sim_apply_gate": [vp, vp],
+            "sim_apply_circuit": [vp, vp, sz],
+            "sim_sync": [vp],
+            "sim_amplitudes": [vp, u64, u64, vp, i32],
+            "sim_measure": [vp, u64, C.POINTER(C.c_uint64), C.POINTER(C.c_double)],
+            "sim_fidelity": [vp, vp, i32, C.POINTER(C.c_double), vp, vp],
+            "sim_stats": [vp, C.POINTER(Stats)],
+            "sim_chunk_image": [vp, u64, vp, sz, C.POINTER(C.c_size_t)],
+            "sim_layout": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+            "sim_codec_encode": [vp, u64, i32, dbl, i32, vp, u64, vp, i32],
+            "sim_codec_decode": [vp, u64, vp, u64, i32, vp, i32],
+            "sim_set_timing": [vp, i32],
+            "sim_timing": [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                           C.POINTER(C.c_uint64)],
+            "sim_sv_create": [i32, pp],
+            "sim_sv_destroy": [vp],
+            "sim_sv_set_stream": [vp, vp],
+            "sim_sv_apply_circuit": [vp, vp, sz],
+            "sim_sv_amplitudes": [vp, u64, u64, vp, i32],
+            "sim_sv_data": [vp, C.POINTER(C.c_void_p)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.sim_last_error.restype = C.c_char_p
+        L.sim_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, call: str) -> None:
+    if rc != OK:
+        raise SimError(rc, call, lib().sim_last_error().decode(errors="replace"))
+
+
+def gates_array(gates) -> np.ndarray:
+    """Copies gate records (fields target, kind, ctrl_mask, ctrl_vals, u) into the
+    sim_gate layout."""
+    src = np.atleast_1d(np.asarray(gates))
+    out = np.zeros(src.shape[0], dtype=SIM_GATE)
+    for f in SIM_GATE.names:
+        out[f] = src[f]
+    return out
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or a torch tensor."""
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x.ctypes.data)
+
+
+def _is_device(x) -> bool:
+    return bool(getattr(x, "is_cuda", False))
+
+
+class Sim:
+    """A compressed n-qubit state on the GPU (sim_t)."""
+
+    def __init__(self, n_qubits: int, block_log2: int, err_bound: float, chunk_log2: int | None = None,
+                 budget: int | None = None, tau: float = 0.9, ladder: int = 0, pool_bytes: int = 0, stream=None):
+        h = C.c_void_p()
+        if chunk_log2 is None and budget is None and tau == 0.9 and ladder == 0 and not pool_bytes:
+            _check(lib().sim_create(n_qubits, block_log2, float(err_bound), C.byref(h)), "sim_create")
+        else:
+            kc = min(10, block_log2) if chunk_log2 is None else chunk_log2
+            if budget is None:
+                budget = (16 << n_qubits) + 16 * (1 << max(0, n_qubits - kc)) + 4096
+            _check(lib().sim_create_ex(n_qubits, block_log2, kc, float(err_bound), int(budget), float(tau),
+                                       int(ladder), int(pool_bytes), C.byref(h)), "sim_create_ex")
+        self._h = h
+        self.n = n_qubits
+        nc, kc_, b_ = C.c_uint64(), C.c_int(), C.c_int()
+        _check(lib().sim_layout(self._h, C.byref(nc), C.byref(kc_), C.byref(b_)), "sim_layout")
+        self.n_chunks, self.chunk_log2, self.block_log2 = int(nc.value), int(kc_.value), int(b_.value)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib().sim_destroy(self._h), "sim_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib().sim_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream) -> None:
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(lib().sim_set_stream(self._h, C.c_void_p(int(handle))), "sim_set_stream")
+
+    def apply_gate(self, gate) -> None:
+        g = gates_array(gate)
+        _check(lib().sim_apply_gate(self._h, C.c_void_p(_ptr(g))), "sim_apply_gate")
+
+    def apply_circuit(self, gates) -> None:
+        g = gates_array(gates)
+        _check(lib().sim_apply_circuit(self._h, C.c_void_p(_ptr(g)), g.shape[0]), "sim_apply_circuit")
+
+    def sync(self) -> None:
+        _check(lib().sim_sync(self._h), "sim_sync")
+
+    def amplitudes(self, first: int = 0, count: int | None = None, out=None):
+        """Decoded amplitudes as complex128 (numpy), or into `out` (numpy complex128 or
+        a torch CUDA tensor of 2*count float64)."""
+        if count is None:
+            count = (1 << self.n) - first
+        if out is None:
+            out = np.zeros(count, dtype=np.complex128)
+        _check(lib().sim_amplitudes(self._h, first, count, C.c_void_p(_ptr(out)), int(_is_device(out))),
+               "sim_amplitudes")
+        return out
+
+    def measure(self, seed: int) -> tuple[int, float]:
+        o, p = C.c_uint64(), C.c_double()
+        _check(lib().sim_measure(self._h, C.c_uint64(seed), C.byref(o), C.byref(p)), "sim_measure")
+        return int(o.value), float(p.value)
+
+    def fidelity(self, ref) -> dict:
+        """F = |<ref|psi>| against a full reference state (numpy complex128, or a torch
+        CUDA tensor)."""
+        if not _is_device(ref):
+            ref = np.ascontiguousarray(ref, dtype=np.complex128)
+        F = C.c_double()
+        ri = np.zeros(2)
+        nn = np.zeros(1)
+        _check(lib().sim_fidelity(self._h, C.c_void_p(_ptr(ref)), int(_is_device(ref)), C.byref(F),
+                                  C.c_void_p(_ptr(ri)), C.c_void_p(_ptr(nn))), "sim_fidelity")
+        return {"F": float(F.value), "overlap": complex(ri[0], ri[1]), "norm2": float(nn[0])}
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().sim_stats(self._h, C.byref(st)), "sim_stats")
+        return st.as_dict()
+
+    def set_timing(self, on: bool) -> None:
+        _check(lib().sim_set_timing(self._h, int(bool(on))), "sim_set_timing")
+
+    def timing(self) -> dict:
+        """Gate-kernel time (CUDA events), launches and image bytes read/written since
+        the last call (or since timing was switched on)."""
+        ms, n, rd, wr = C.c_double(), C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().sim_timing(self._h, C.byref(ms), C.byref(n), C.byref(rd), C.byref(wr)), "sim_timing")
+        return {"gate_kernel_ms": float(ms.value), "launches": int(n.value), "bytes_read": int(rd.value),
+                "bytes_written": int(wr.value)}
+
+    def chunk_image(self, c: int) -> bytes:
+        cap = 16 + (16 << self.chunk_log2) + 64
+        buf = np.zeros(cap, dtype=np.uint8)
+        ln = C.c_size_t()
+        _check(lib().sim_chunk_image(self._h, c, C.c_void_p(_ptr(buf)), cap, C.byref(ln)), "sim_chunk_image")
+        return buf[: ln.value].tobytes()
+
+
+def codec_stride(chunk_log2: int) -> int:
+    need = 16 + (16 << chunk_log2) + (1 << chunk_log2) // 2 + 32
+    return (need + 15) // 16 * 16
+
+
+def codec_encode(values, chunk_log2: int, eps: float, force_mode: int = -1):
+    """Encodes chunks with the device encoder.  values: numpy complex128 of
+    n_chunks * 2^chunk_log2 amplitudes (host) or a torch CUDA float64 tensor.
+    Returns (images as a list of bytes, lengths) for host input; for device input
+    returns (image buffer tensor, lengths tensor, stride)."""
+    stride = codec_stride(chunk_log2)
+    if _is_device(values):
+        import torch
+
+        n = values.numel() // (2 << chunk_log2)
+        out = torch.zeros(n * stride, dtype=torch.uint8, device=values.device)
+        lens = torch.zeros(n, dtype=torch.int32, device=values.device)
+        _check(lib().sim_codec_encode(C.c_void_p(_ptr(values)), n, chunk_log2, float(eps), force_mode,
+                                      C.c_void_p(_ptr(out)), stride, C.c_void_p(_ptr(lens)), 1), "sim_codec_encode")
+        return out, lens, stride
+    x = np.ascontiguousarray(values, dtype=np.complex128)
+    n = x.size >> chunk_log2
+    assert n << chunk_log2 == x.size
+    out = np.zeros(n * stride, dtype=np.uint8)
+    lens = np.zeros(n, dtype=np.uint32)
+    _check(lib().sim_codec_encode(C.c_void_p(_ptr(x)), n, chunk_log2, float(eps), force_mode, C.c_void_p(_ptr(out)),
+                                  stride, C.c_void_p(_ptr(lens)), 0), "sim_codec_encode")
+    return [out[k * stride: k * stride + int(lens[k])].tobytes() for k in range(n)], lens
+
+
+def codec_decode(images: list[bytes], chunk_log2: int) -> np.ndarray:
+    """Decodes host images with the device decoder; returns complex128 amplitudes."""
+    n = len(images)
+    stride = max([codec_stride(chunk_log2)] + [(len(b) + 15) // 16 * 16 for b in images])
+    buf = np.zeros(max(1, n) * stride, dtype=np.uint8)
+    lens = np.zeros(max(1, n), dtype=np.uint32)
+    for k, b in enumerate(images):
+        buf[k * stride: k * stride + len(b)] = np.frombuffer(b, dtype=np.uint8)
+        lens[k] = len(b)
+    out = np.zeros(n << chunk_log2, dtype=np.complex128)
+    _check(lib().sim_codec_decode(C.c_void_p(_ptr(buf)), stride, C.c_void_p(_ptr(lens)), n, chunk_log2,
+                                  C.c_void_p(_ptr(out)), 0), "sim_codec_decode")
+    return out
+
+
+class StateVector:
+    """Uncompressed complex128 state vector on the GPU (sim_sv_t)."""
+
+    def __init__(self, n_qubits: int, stream=None):
+        h = C.c_void_p()
+        _check(lib().sim_sv_create(n_qubits, C.byref(h)), "sim_sv_create")
+        self._h = h
+        self.n = n_qubits
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            _check(lib().sim_sv_set_stream(self._h, C.c_void_p(int(handle))), "sim_sv_set_stream")
+
+    def close(self):
+        if self._h:
+            _check(lib().sim_sv_destroy(self._h), "sim_sv_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib().sim_sv_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def apply_circuit(self, gates) -> None:
+        g = gates_array(gates)
+        _check(lib().sim_sv_apply_circuit(self._h, C.c_void_p(_ptr(g)), g.shape[0]), "sim_sv_apply_circuit")
+
+    def amplitudes(self, first: int = 0, count: int | None = None, out=None):
+        if count is None:
+            count = (1 << self.n) - first
+        if out is None:
+            out = np.zeros(count, dtype=np.complex128)
+        _check(lib().sim_sv_amplitudes(self._h, first, count, C.c_void_p(_ptr(out)), int(_is_device(out))),
+               "sim_sv_amplitudes")
+        return out
+
+    def data_ptr(self) -> int:
+        p = C.c_void_p()
+        _check(lib().sim_sv_data(self._h, C.byref(p)), "sim_sv_data")
+        return int(p.value)
