@@ -42,7 +42,7 @@ from paper_1911_04034_gb300 import circuits as Cc  # noqa: E402
 
 METRIC = "compressed-state amplitude updates/s"
 UNIT = "amp-updates/s"
-ROWS, COLS, BLOCK_LOG2, CHUNK_LOG2, SEED = 5, 6, 20, 10, 2024
+ROWS, COLS, BLOCK_LOG2, CHUNK_LOG2, SEED = 5, 6, 20, 10, 2024  # defaults; --rows/--cols override
 
 # dram__bytes_read.sum + dram__bytes_write.sum per k_gate launch from the last ncu
 # capture, with the hash of the kernel sources it was taken on (None = no capture).
@@ -211,14 +211,11 @@ def run_gpu(args) -> dict | None:
         sv.apply_circuit(applied)
         sv_s = time.perf_counter() - t0
         sv_rate = len(applied) * float(1 << n) / sv_s
-        ref = torch.empty(2 << n, dtype=torch.float64, device="cuda")
-        ref_ptr = sv.data_ptr()
-        # the state vector's own device buffer serves as the reference
-        f = qcsim.lib().sim_fidelity(sim._h, qcsim.C.c_void_p(ref_ptr), 1, qcsim.C.byref(F := qcsim.C.c_double()),
-                                     None, None)
-        qcsim._check(f, "sim_fidelity")
+        # the state vector's own device buffer is the reference of sim_fidelity
+        F = qcsim.C.c_double()
+        qcsim._check(qcsim.lib().sim_fidelity(sim._h, qcsim.C.c_void_p(sv.data_ptr()), 1, qcsim.C.byref(F), None, None),
+                     "sim_fidelity")
         fid = float(F.value)
-        del ref
         sv.close()
     ms_max = ms
     upd_total = updates
@@ -252,7 +249,7 @@ def run_gpu(args) -> dict | None:
         "dtype": "f64",
         "data": "synthetic",
         "config": {
-            "workload": f"random circuit {ROWS}x{COLS} grid, 30 qubits, layers {1 + args.warmup}-{args.warmup + args.steps} "
+            "workload": f"random circuit {ROWS}x{COLS} grid, {n} qubits, layers {1 + args.warmup}-{args.warmup + args.steps} "
                         f"timed; eps {args.eps}; blocks 2^{BLOCK_LOG2}, chunks 2^{kc}",
             "n_qubits": n, "block_log2": BLOCK_LOG2, "chunk_log2": kc, "eps": args.eps,
             "budget_bytes": raw // 4, "pool_bytes": raw + raw // 8, "gates_timed": int(sum(len(x) for x in timed)),
@@ -301,7 +298,7 @@ def cpu_sample(eps: float, n: int = 20, warm_layers: int = 3, timed_layers: int 
         m = len(Cc.grid_edges(rows, cols, n, layer % 4)) + n
         out.append(gates[pos:pos + m])
         pos += m
-    cs = O.CSim(n, BLOCK_LOG2, CHUNK_LOG2, eps, (16 << n) // 4)
+    cs = O.CSim(n, n - 10, CHUNK_LOG2, eps, (16 << n) // 4)  # 2^10 blocks, as at 30 qubits
     for L in out[: 1 + warm_layers]:
         cs.apply(L)
     t0 = time.perf_counter()
@@ -335,7 +332,7 @@ def run_reference(args) -> dict | None:
         m = len(Cc.grid_edges(rows, cols, n, layer % 4)) + n
         L.append(gates[pos:pos + m])
         pos += m
-    cs = O.CSim(n, BLOCK_LOG2, CHUNK_LOG2, args.eps, (16 << n) // 4)
+    cs = O.CSim(n, n - 10, CHUNK_LOG2, args.eps, (16 << n) // 4)  # 2^10 blocks, as at 30 qubits
     for x in L[: 1 + args.warmup]:
         cs.apply(x)
     t0 = time.perf_counter()
@@ -364,7 +361,12 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--no-sv", action="store_true", help="skip the uncompressed comparator and fidelity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
+    ap.add_argument("--cols", type=int, default=6)
     args = ap.parse_args()
+    global ROWS, COLS, BLOCK_LOG2
+    ROWS, COLS = args.rows, args.cols
+    BLOCK_LOG2 = min(20, ROWS * COLS - 10)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
