@@ -169,7 +169,7 @@ def run_gpu(args) -> dict | None:
     # timed region (device time, CUDA events on the simulator's stream)
     timed = layers[1 + args.warmup: 1 + args.warmup + args.steps]
     clocks = Clocks(local)
-    sim.set_timing(True)
+    sim.set_timing(2 if args.phases else 1)
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -277,6 +277,9 @@ def run_gpu(args) -> dict | None:
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else None,
         },
         "gpu_launches": 2 * tm["launches"],
+        "phase_share": ({k: round(v / max(1, sum(st1["phase_cycles"])), 4) for k, v in
+                         zip(("stage", "decode", "apply", "encode", "commit", "const"), st1["phase_cycles"])}
+                        if args.phases else None),
         "clocks": clk,
         "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // max(1, len(e2e_layers)),
                 "d2h_bytes_per_step": d2h // max(1, len(e2e_layers))},
@@ -361,6 +364,7 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--no-sv", action="store_true", help="skip the uncompressed comparator and fidelity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phases", action="store_true", help="also count SM cycles per phase of the fused kernel")
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)
     args = ap.parse_args()

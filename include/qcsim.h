@@ -89,6 +89,8 @@ typedef struct sim_stats_t {
   int32_t sig_bits_current;   /* S of the last gate (64 = lossless) */
   int32_t level;              /* position on the bound ladder, 0 = lossless */
   int32_t chunk_log2, block_log2;
+  uint64_t phase_cycles[6];   /* with sim_set_timing(sim, 2): SM cycles of the fused kernel's CTAs in
+                                 stage / decode / apply / encode / commit / constant fast paths */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
@@ -156,7 +158,8 @@ sim_status sim_chunk_image(sim_t* sim, uint64_t c, uint8_t* out, size_t cap, siz
 /* Number of chunks and chunk_log2 of the handle. */
 sim_status sim_layout(sim_t* sim, uint64_t* n_chunks, int* chunk_log2, int* block_log2);
 
-/* Timing of the fused gate kernel: with timing on, every gate-kernel launch is
+/* Timing of the fused gate kernel: with timing on (on = 1; on = 2 also counts the
+ * SM cycles of each phase of the kernel, see sim_stats_t), every gate-kernel launch is
  * bracketed by CUDA events on the handle's stream.  sim_timing synchronises and
  * returns, since timing was switched on or last read: the summed kernel time in ms,
  * the number of gate-kernel launches, and the chunk-image bytes those launches read

@@ -83,12 +83,28 @@ bool gate_ok(const sim_gate* g, int n, std::string* why) {
 
 GateCoef coef_of(const sim_gate* g) {
   const double* u = g->u;
+  // four rows (a'r, a'i, b'r, b'i), four terms each: coefficient and operand
+  // (0 ar, 1 ai, 2 br, 3 bi) in the order of the sums of Eq. matrix1
+  const double cf[4][4] = {{u[0], -u[1], u[2], -u[3]},
+                           {u[0], u[1], u[2], u[3]},
+                           {u[4], -u[5], u[6], -u[7]},
+                           {u[4], u[5], u[6], u[7]}};
+  const uint8_t ops[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {0, 1, 2, 3}, {1, 0, 3, 2}};
   GateCoef c;
-  const double v[16] = {u[0], -u[1], u[2], -u[3],  // a'r: ar ai br bi
-                        u[0], u[1],  u[2], u[3],   // a'i: ai ar bi br
-                        u[4], -u[5], u[6], -u[7],  // b'r: ar ai br bi
-                        u[4], u[5],  u[6], u[7]};  // b'i: ai ar bi br
-  for (int k = 0; k < 16; ++k) c.c[k] = v[k];
+  std::memset(&c, 0, sizeof(c));
+  for (int r = 0; r < 4; ++r) {
+    int k = 0;
+    for (int t = 0; t < 4; ++t) {
+      if (cf[r][t] == 0.0) continue;  // an exactly-zero coefficient drops its term
+      c.c[4 * r + k] = cf[r][t];
+      c.op[4 * r + k] = ops[r][t];
+      ++k;
+    }
+    c.cnt[r] = (uint8_t)k;
+    c.first[r] = 0;
+    if (k > 0 && c.c[4 * r] == 1.0) c.first[r] = 1;
+    if (k > 0 && c.c[4 * r] == -1.0) c.first[r] = 2;
+  }
   return c;
 }
 
@@ -121,6 +137,7 @@ struct sim {
   double level_eps[8] = {0};
   // gate-kernel timing
   bool timing = false;
+  bool phases = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   size_t ev_next = 0;
@@ -333,6 +350,7 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
   L.lo_mask = (uint32_t)(g->ctrl_mask & (A - 1ull));
   L.lo_vals = (uint32_t)(g->ctrl_vals & (A - 1ull));
   L.target = t;
+  L.prof = s->phases ? 1 : 0;
   if (t >= kc) {
     L.pair = 1;
     L.pair_bit = 1ull << (t - kc);
@@ -406,6 +424,7 @@ sim_status sim_set_timing(sim_t* s, int on) {
   if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
   CK(cudaStreamSynchronize(s->st), "sync");
   s->timing = on != 0;
+  s->phases = on >= 2;
   s->ev_pending.clear();
   s->ev_next = 0;
   return read_traffic(s, &s->t_bytes_in0, &s->t_bytes_out0);
@@ -575,6 +594,7 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->level = h.level;
   o->chunk_log2 = s->kc;
   o->block_log2 = s->b;
+  for (int k = 0; k < 6; ++k) o->phase_cycles[k] = h.phase_cycles[k];
   if (h.err) return s->check_device();
   return SIM_OK;
 }

@@ -64,6 +64,7 @@ struct DevCtl {
   unsigned int pad;
   unsigned long long bytes_in;  // image bytes the gate kernels read (cumulative)
   unsigned long long bytes_out; // image bytes the gate kernels wrote (cumulative)
+  unsigned long long phase_cycles[6];  // SM cycles of CTA thread 0 per phase when profiling
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -197,8 +198,53 @@ __device__ __forceinline__ uint64_t get_bits(const uint64_t* w, uint32_t pos, ui
 }
 __device__ __forceinline__ uint64_t trunc_mask(uint32_t S) { return S >= 64u ? ~0ull : (~0ull << (64u - S)); }
 
+// ------------------------------------------------------------ tile layout -- //
+// A decoded chunk lives in shared memory as 2^kc amplitudes of 16 bytes with one
+// unused 16-byte slot after every 8 amplitudes.  Threads own contiguous runs of
+// values (what the prefix scans need); the padding spreads those runs over all
+// banks, so every 16-byte access of a warp is conflict-free.
+__host__ __device__ __forceinline__ uint32_t tile_amp(uint32_t a) { return a + (a >> 3); }
+__host__ __device__ __forceinline__ uint32_t tile_val(uint32_t j) { return 2u * tile_amp(j >> 1) + (j & 1u); }
+__host__ __device__ __forceinline__ uint32_t tile_words(int kc) {
+  const uint32_t A = 1u << kc;
+  return 2u * (A + (A >> 3));
+}
+
+// Thread t owns values [t*VPT, t*VPT + VPT) (whole amplitudes when VPT >= 2).
+template <int VPT>
+__device__ __forceinline__ void load_vals(const uint64_t* tile, uint32_t j0, uint32_t N, uint64_t v[VPT]) {
+  if (VPT >= 2) {
+    const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
+#pragma unroll
+    for (int m = 0; m < VPT / 2; ++m) {
+      const uint32_t a = (j0 >> 1) + m;
+      if (2u * a < N) {
+        const ulonglong2 q = t2[tile_amp(a)];
+        v[2 * m] = q.x;
+        v[2 * m + 1] = q.y;
+      } else {
+        v[2 * m] = v[2 * m + 1] = 0ull;
+      }
+    }
+  } else {
+    v[0] = j0 < N ? tile[tile_val(j0)] : 0ull;
+  }
+}
+template <int VPT>
+__device__ __forceinline__ void store_vals(uint64_t* tile, uint32_t j0, uint32_t N, const uint64_t v[VPT]) {
+  if (VPT >= 2) {
+    ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tile);
+#pragma unroll
+    for (int m = 0; m < VPT / 2; ++m) {
+      const uint32_t a = (j0 >> 1) + m;
+      if (2u * a < N) t2[tile_amp(a)] = make_ulonglong2(v[2 * m], v[2 * m + 1]);
+    }
+  } else {
+    if (j0 < N) tile[tile_val(j0)] = v[0];
+  }
+}
+
 // ----------------------------------------------------------- decoder ----- //
-// Per-thread value ownership: thread t holds values [t*VPT, t*VPT + VPT).
 template <int VPT>
 __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t nv, uint32_t S, uint32_t bits,
                                  uint64_t* tile, ScanSmem& s) {
@@ -214,8 +260,8 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
     c[k] = 3u;
     r[k] = 0u;
     if (j < nv) {
-      uint32_t word = codes32[j >> 4];
-      uint32_t sh = 8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u);
+      const uint32_t word = codes32[j >> 4];
+      const uint32_t sh = 8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u);
       c[k] = (word >> sh) & 3u;
       r[k] = resid_len(c[k], S);
       sum += r[k];
@@ -225,49 +271,49 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
   uint32_t o = block_excl_add(sum, s, &total);
   if (total != bits || cb + resid_bytes(bits) != plen) return false;
   // explicit part of every value: residual bits placed at [8c, S)
+  uint64_t e[VPT];
   int lw[3] = {-1, -1, -1};
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
     const uint32_t j = j0 + k;
+    e[k] = 0ull;
     if (j < nv) {
-      uint64_t e = 0;
-      if (r[k]) e = (get_bits(words, o, r[k]) << (64u - r[k])) >> (8u * c[k]);
-      tile[j] = e;
+      if (r[k]) e[k] = (get_bits(words, o, r[k]) << (64u - r[k])) >> (8u * c[k]);
       o += r[k];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
         if (c[k] <= (uint32_t)b) lw[b] = (int)j;
     }
   }
-  int ex[3] = {lw[0], lw[1], lw[2]};
-  // running "last explicit writer" of leading byte b, exclusive of this thread
-  int thr_last[3] = {-1, -1, -1};
+  store_vals<VPT>(tile, j0, nv, e);
+  // last explicit writer of leading byte b before this thread's first value
+  block_excl_max3(lw, s);  // ends with a barrier: every explicit part is visible
+  // byte b of a value with code c > b repeats byte b of the last value that wrote it
+  // explicitly (code <= b); before the first value it is 0
+  uint64_t lastb[3];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) thr_last[b] = ex[b];
-  block_excl_max3(thr_last, s);  // now: last writer before this thread's first value
-  // (block_excl_max3 ends with __syncthreads, so every explicit part is visible)
-  int run[3] = {thr_last[0], thr_last[1], thr_last[2]};
+  for (int b = 0; b < 3; ++b)
+    lastb[b] = lw[b] >= 0 ? (tile[tile_val((uint32_t)lw[b])] & (0xFF00000000000000ull >> (8 * b))) : 0ull;
+  __syncthreads();  // every thread has read the explicit parts it needs
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    if (j < nv) {
-      uint64_t v = tile[j];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if ((uint32_t)b < c[k] && run[b] >= 0) v |= tile[run[b]] & (0xFF00000000000000ull >> (8 * b));
-      }
-      // leading bytes b >= c of this value are explicit: it becomes the last writer
+    if (j0 + k < nv) {
+      uint64_t v = e[k];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
-        if (c[k] <= (uint32_t)b) run[b] = (int)j;
-      tile[j] = v;
+        if ((uint32_t)b < c[k]) v |= lastb[b];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        if (c[k] <= (uint32_t)b) lastb[b] = v & (0xFF00000000000000ull >> (8 * b));
+      e[k] = v;
     }
   }
+  store_vals<VPT>(tile, j0, nv, e);
   __syncthreads();
   return true;
 }
 
-// Decodes the staged image (header + payload in shared memory) into tile[0..N).
+// Decodes the staged image (header + payload in shared memory) into the tile.
 // Returns false (tile zero-filled) if the image fails its checks.
 template <int VPT>
 __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uint64_t* tile, ScanSmem& s) {
@@ -293,24 +339,27 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
   if (ok && (mode == M_PERIOD || mode == M_STREAM)) {
     ok = decode_xor_block<VPT>(payload, plen, nv, S, bits, tile, s);
     if (ok && mode == M_PERIOD) {
-      for (uint32_t j = nv + threadIdx.x; j < N; j += kThreads) tile[j] = tile[j & (nv - 1u)];
+      ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tile);
+      const uint32_t P = nv >> 1;  // period in amplitudes
+      for (uint32_t a = P + threadIdx.x; a < (N >> 1); a += kThreads) t2[tile_amp(a)] = t2[tile_amp(a & (P - 1u))];
       __syncthreads();
     }
     if (ok) return true;
   }
   const uint64_t* pw = reinterpret_cast<const uint64_t*>(payload);
-  for (uint32_t j = threadIdx.x; j < N; j += kThreads) {
-    uint64_t v = 0;
-    if (ok && mode == M_CONST) v = pw[j & 1u];
-    else if (ok && mode == M_RAW) v = pw[j];
-    tile[j] = v;
+  ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tile);
+  for (uint32_t a = threadIdx.x; a < (N >> 1); a += kThreads) {
+    ulonglong2 q = make_ulonglong2(0ull, 0ull);
+    if (ok && mode == M_CONST) q = make_ulonglong2(pw[0], pw[1]);
+    else if (ok && mode == M_RAW) q = make_ulonglong2(pw[2 * a], pw[2 * a + 1]);
+    t2[tile_amp(a)] = q;
   }
   __syncthreads();
   return ok;
 }
 
 // ----------------------------------------------------------- encoder ----- //
-// Encodes tile[0..N) (raw bit patterns; overwritten with the truncated values) into
+// Encodes the tile (raw bit patterns; overwritten with the truncated values) into
 // img (img_cap bytes).  S_req = 12 - EXP(eps) or 64.  force_mode < 0: smallest image
 // (never larger than RAW).  Returns the image length, or 0 with *err set (non-finite
 // value, or a forced mode that does not apply or does not fit in img_cap).
@@ -319,16 +368,17 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
                                  uint32_t img_cap, ScanSmem& s, unsigned int* err) {
   const uint32_t N = 2u << kc, A = 1u << kc;
   const uint32_t j0 = threadIdx.x * VPT;
+  const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
   // 1. chunk-wide width: a nonzero subnormal forces 64 bits; non-finite is an error
+  uint64_t t[VPT];
+  load_vals<VPT>(tile, j0, N, t);
   bool sub = false, nonfin = false;
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    if (j < N) {
-      uint64_t v = tile[j];
-      uint32_t e = (uint32_t)(v >> 52) & 0x7ffu;
+    if (j0 + k < N) {
+      const uint32_t e = (uint32_t)(t[k] >> 52) & 0x7ffu;
       nonfin |= e == 0x7ffu;
-      sub |= (e == 0u) && ((v << 12) != 0ull);
+      sub |= (e == 0u) && ((t[k] << 12) != 0ull);
     }
   }
   const int anynf = __syncthreads_or(nonfin);
@@ -340,30 +390,24 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   const uint32_t S = anysub ? 64u : S_req;
   const uint64_t mask = trunc_mask(S);
   // 2. truncate (and store -0 as +0)
-  uint64_t t[VPT];
   bool nz = false;
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    t[k] = 0;
-    if (j < N) {
-      uint64_t v = tile[j] & mask;
-      if (v == 0x8000000000000000ull) v = 0;
-      t[k] = v;
-      tile[j] = v;
-      nz |= v != 0;
-    }
+    uint64_t v = t[k] & mask;
+    if (v == 0x8000000000000000ull) v = 0;
+    t[k] = (j0 + k < N) ? v : 0ull;
+    nz |= t[k] != 0ull;
   }
+  store_vals<VPT>(tile, j0, N, t);
   __syncthreads();
-  // 3. codes and residual lengths
+  // 3. codes and residual lengths (predecessor of value 0 is 0)
   uint32_t c[VPT], r[VPT], sum = 0;
-  uint64_t prev = (j0 > 0 && j0 <= N) ? tile[j0 - 1] : 0ull;
+  uint64_t prev = (j0 > 0 && j0 <= N) ? tile[tile_val(j0 - 1)] : 0ull;
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
     c[k] = 3u;
     r[k] = 0u;
-    if (j < N) {
+    if (j0 + k < N) {
       c[k] = xor_code(t[k], prev);
       r[k] = resid_len(c[k], S);
       sum += r[k];
@@ -371,26 +415,34 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
     }
   }
   // 4. ZERO and CONST tests
-  const uint64_t a0 = tile[0], a1 = tile[1];
+  const ulonglong2 a0 = t2[tile_amp(0)];
   bool cst = true;
-  for (uint32_t i = threadIdx.x; i < A; i += kThreads) cst &= (tile[2 * i] == a0) && (tile[2 * i + 1] == a1);
+  for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+    const ulonglong2 q = t2[tile_amp(i)];
+    cst &= (q.x == a0.x) && (q.y == a0.y);
+  }
   const int allzero = !__syncthreads_or(nz);
   const int allconst = __syncthreads_and(cst);
   // 5. offsets of the residual stream
   uint32_t total;
   const uint32_t o0 = block_excl_add(sum, s, &total);
-  // 6. smallest power-of-two period P (amplitudes) with 2 <= P < 2^kc
+  // 6. smallest power-of-two period P (amplitudes) with 2 <= P < 2^kc: the chunk is
+  //    P-periodic iff flipping any amplitude-index bit >= log2 P leaves it unchanged
   int period = -1;
   if (kc >= 2) {
     int p = kc - 1;
     for (; p >= 1; --p) {
       const uint32_t P = 1u << p;
       bool ok = true;
-      for (uint32_t i = threadIdx.x; i < A; i += kThreads)
-        if (i & P) ok &= (tile[2 * i] == tile[2 * (i ^ P)]) && (tile[2 * i + 1] == tile[2 * (i ^ P) + 1]);
+      for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+        if (i & P) {
+          const ulonglong2 q = t2[tile_amp(i)], w = t2[tile_amp(i ^ P)];
+          ok &= (q.x == w.x) && (q.y == w.y);
+        }
+      }
       if (!__syncthreads_and(ok)) break;
     }
-    if (p < kc - 1) period = p + 1;  // every bit from p+1 up to kc-1 left the chunk unchanged
+    if (p < kc - 1) period = p + 1;
   }
   // residual bits of the first 2P values
   if (threadIdx.x == 0) s.bits_period = 0;
@@ -439,7 +491,8 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   if (mode == M_RAW) nv = N;
   uint64_t* pay64 = reinterpret_cast<uint64_t*>(img + 16);
   const uint32_t plen = best - 16u;
-  for (uint32_t q = threadIdx.x; q < plen / 8u; q += kThreads) pay64[q] = 0ull;
+  if (mode == M_PERIOD || mode == M_STREAM)
+    for (uint32_t q = threadIdx.x; q < plen / 8u; q += kThreads) pay64[q] = 0ull;
   if (threadIdx.x == 0) {
     uint32_t* h = reinterpret_cast<uint32_t*>(img);
     h[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | ((mode == M_PERIOD ? (uint32_t)period : 0u) << 16);
@@ -449,9 +502,13 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   }
   __syncthreads();
   if (mode == M_CONST) {
-    if (threadIdx.x < 2) pay64[threadIdx.x] = tile[threadIdx.x];
+    if (threadIdx.x == 0) {
+      pay64[0] = a0.x;
+      pay64[1] = a0.y;
+    }
   } else if (mode == M_RAW) {
-    for (uint32_t j = threadIdx.x; j < N; j += kThreads) pay64[j] = tile[j];
+    ulonglong2* p2 = reinterpret_cast<ulonglong2*>(pay64);
+    for (uint32_t a = threadIdx.x; a < A; a += kThreads) p2[a] = t2[tile_amp(a)];
   } else if (mode == M_PERIOD || mode == M_STREAM) {
     uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
     uint64_t* words = reinterpret_cast<uint64_t*>(img + 16 + code_bytes(nv));
@@ -499,47 +556,73 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
 }
 
 // -------------------------------------------------------- gate arithmetic -- //
-// Coefficients of the four output components, four terms each, in a fixed order:
+// Each output component is a sum of four products with (ar, ai, br, bi):
 //   a'r = u00r ar - u00i ai + u01r br - u01i bi      a'i = u00r ai + u00i ar + u01r bi + u01i br
 //   b'r = u10r ar - u10i ai + u11r br - u11i bi      b'i = u10r ai + u10i ar + u11r bi + u11i br
-// A term whose coefficient is exactly zero is left out; the first kept term is one
-// rounded product and every later term one fused multiply-add.  With no term the
-// result is +0.  A first-term coefficient of +-1 is an exact copy / sign flip,
-// which is what the rounded product gives.
+// taken in the order written.  A term whose coefficient is exactly zero is left out;
+// the first kept term is one rounded product and every later term one fused
+// multiply-add; with no term the result is +0.  The host lists the kept terms of
+// each row (coefficient and operand) and marks a first coefficient of +1 / -1, whose
+// product is an exact copy / sign flip and needs no FP64 instruction.
 struct GateCoef {
-  double c[16];
+  double c[16];      // row r: c[4r .. 4r + cnt[r]) in execution order
+  uint8_t op[16];    // operand of each term: 0 ar, 1 ai, 2 br, 3 bi
+  uint8_t cnt[4];    // kept terms per row
+  uint8_t first[4];  // first term: 0 product, 1 copy, 2 sign flip
 };
 
-__device__ __forceinline__ double row4(const double* c, double x0, double x1, double x2, double x3) {
-  const double xs[4] = {x0, x1, x2, x3};
-  double acc = 0.0;
-  bool have = false;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double ck = c[k];
-    if (ck != 0.0) {
-      if (!have) {
-        if (ck == 1.0) acc = xs[k];
-        else if (ck == -1.0) acc = __longlong_as_double(__double_as_longlong(xs[k]) ^ (long long)0x8000000000000000ull);
-        else acc = __dmul_rn(ck, xs[k]);
-        have = true;
-      } else {
-        acc = __fma_rn(ck, xs[k], acc);
-      }
-    }
-  }
+__device__ __forceinline__ double pick4(const double x[4], uint32_t i) {
+  return i == 0 ? x[0] : (i == 1 ? x[1] : (i == 2 ? x[2] : x[3]));
+}
+__device__ __forceinline__ double flip_sign(double v) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double row_eval(const GateCoef& g, int r, const double x[4]) {
+  const uint32_t n = g.cnt[r];
+  if (n == 0) return 0.0;
+  const double v0 = pick4(x, g.op[4 * r]);
+  double acc;
+  if (g.first[r] == 0) acc = __dmul_rn(g.c[4 * r], v0);
+  else acc = g.first[r] == 1 ? v0 : flip_sign(v0);
+  if (n > 1) acc = __fma_rn(g.c[4 * r + 1], pick4(x, g.op[4 * r + 1]), acc);
+  if (n > 2) acc = __fma_rn(g.c[4 * r + 2], pick4(x, g.op[4 * r + 2]), acc);
+  if (n > 3) acc = __fma_rn(g.c[4 * r + 3], pick4(x, g.op[4 * r + 3]), acc);
   return acc;
 }
 
 __device__ __forceinline__ void apply_pair(const GateCoef& g, double2& a, double2& b) {
-  const double ar = a.x, ai = a.y, br = b.x, bi = b.y;
-  double2 na, nb;
-  na.x = row4(g.c + 0, ar, ai, br, bi);
-  na.y = row4(g.c + 4, ai, ar, bi, br);
-  nb.x = row4(g.c + 8, ar, ai, br, bi);
-  nb.y = row4(g.c + 12, ai, ar, bi, br);
-  a = na;
-  b = nb;
+  const double x[4] = {a.x, a.y, b.x, b.y};
+  a.x = row_eval(g, 0, x);
+  a.y = row_eval(g, 1, x);
+  b.x = row_eval(g, 2, x);
+  b.y = row_eval(g, 3, x);
+}
+
+// Image of a chunk whose amplitudes all equal (v0, v1): what encode_block writes
+// for a constant tile (the subnormal rule, truncation, -0 -> +0, then ZERO if both
+// values are +0, else CONST).  h receives 8 words (16-byte header + 16-byte payload
+// as u32); returns the image length, 0 for a non-finite value.
+__device__ __forceinline__ uint32_t const_image(uint64_t v0, uint64_t v1, uint32_t S_req, uint32_t h[8]) {
+  const uint32_t e0 = (uint32_t)(v0 >> 52) & 0x7ffu, e1 = (uint32_t)(v1 >> 52) & 0x7ffu;
+  if (e0 == 0x7ffu || e1 == 0x7ffu) return 0;
+  const bool sub = (e0 == 0u && (v0 << 12) != 0ull) || (e1 == 0u && (v1 << 12) != 0ull);
+  const uint32_t S = sub ? 64u : S_req;
+  const uint64_t m = trunc_mask(S);
+  uint64_t t0 = v0 & m, t1 = v1 & m;
+  if (t0 == 0x8000000000000000ull) t0 = 0;
+  if (t1 == 0x8000000000000000ull) t1 = 0;
+  for (int k = 0; k < 8; ++k) h[k] = 0u;
+  if (t0 == 0ull && t1 == 0ull) return 16u;
+  h[0] = M_CONST | (S << 8);
+  h[1] = 16u;
+  h[2] = 2u;
+  h[3] = 0u;
+  h[4] = (uint32_t)t0;
+  h[5] = (uint32_t)(t0 >> 32);
+  h[6] = (uint32_t)t1;
+  h[7] = (uint32_t)(t1 >> 32);
+  return 32u;
 }
 
 // --------------------------------------------------------------- pool ---- //

@@ -23,24 +23,23 @@ __host__ __device__ __forceinline__ uint32_t codedcap(int kc) { return round16(m
 __host__ __device__ __forceinline__ uint32_t pagelist_words(int kc) { return (max_pages(kc) + 3u) & ~3u; }
 
 size_t gate_smem_bytes(int kc) {
-  const size_t N = size_t(2) << kc;
-  return 2 * N * 8 + 2 * size_t(imgcap(kc)) + 2 * 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
+  return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgcap(kc)) + 2 * 4 * size_t(pagelist_words(kc)) +
+         round16(sizeof(ScanSmem));
 }
 size_t codec_smem_bytes(int kc) {
-  const size_t N = size_t(2) << kc;
-  return N * 8 + size_t(codedcap(kc)) + 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
+  return size_t(tile_words(kc)) * 8 + size_t(codedcap(kc)) + 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
 }
 
 // ------------------------------------------------------------- the gate -- //
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
+__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3) k_gate(const GateLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int kc = L.P.kc;
-  const uint32_t N = 2u << kc, A = 1u << kc;
+  const uint32_t A = 1u << kc;
   const uint32_t cap = imgcap(kc);
   uint64_t* tile0 = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* tile1 = tile0 + N;
-  uint8_t* img0 = reinterpret_cast<uint8_t*>(tile1 + N);
+  uint64_t* tile1 = tile0 + tile_words(kc);
+  uint8_t* img0 = reinterpret_cast<uint8_t*>(tile1 + tile_words(kc));
   uint8_t* img1 = img0 + cap;
   uint32_t* pages0 = reinterpret_cast<uint32_t*>(img1 + cap);
   uint32_t* pages1 = pages0 + pagelist_words(kc);
@@ -61,6 +60,19 @@ __global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
   if (threadIdx.x == 0) cc.n = P.cache_n[blockIdx.x];
   long long dE = 0;
   unsigned long long rd = 0, wr = 0;
+  // phases: 0 stage images, 1 decode, 2 apply, 3 encode, 4 commit, 5 constant fast
+  // paths; [6] holds the last clock (kept in shared memory, thread 0 only)
+  __shared__ long long s_ph[7];
+  if (L.prof && threadIdx.x == 0) {
+    for (int k = 0; k < 6; ++k) s_ph[k] = 0;
+    s_ph[6] = clock64();
+  }
+#define QC_PHASE(k)                   \
+  if (L.prof && threadIdx.x == 0) {   \
+    const long long now_ = clock64(); \
+    s_ph[k] += now_ - s_ph[6];        \
+    s_ph[6] = now_;                   \
+  }
 
   for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x) {
     // one barrier that also broadcasts thread 0's view of the error word
@@ -90,7 +102,44 @@ __global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
     const bool z0 = np0 == 0 && b0 == 16u && e0[4] == 0u;
     const bool z1 = !has1 || (np1 == 0 && b1 == 16u && e1[4] == 0u);
     rd += b0 + b1;
-    if (z0 && z1) continue;
+    if (z0 && z1) {
+      QC_PHASE(5);
+      continue;
+    }
+    // Two constant chunks (ZERO or CONST images, held inline) under a cross-chunk gate
+    // with no in-chunk controls: every pair sees the same inputs, so one pair gives
+    // both output chunks, which are constant again.
+    if (L.pair && L.lo_mask == 0u && inline_cap(kc) >= 32u && np0 == 0u && np1 == 0u &&
+        (z0 || (e0[4] & 0xffu) == M_CONST) &&
+        (z1 || (e1[4] & 0xffu) == M_CONST)) {
+      if (threadIdx.x == 0) {
+        double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+        if (!z0) a = make_double2(__longlong_as_double(((const long long*)(e0 + 8))[0]),
+                                  __longlong_as_double(((const long long*)(e0 + 8))[1]));
+        if (!z1) b = make_double2(__longlong_as_double(((const long long*)(e1 + 8))[0]),
+                                  __longlong_as_double(((const long long*)(e1 + 8))[1]));
+        apply_pair(L.g, a, b);
+        uint32_t h0[8], h1[8];
+        const uint32_t n0 = const_image((uint64_t)__double_as_longlong(a.x), (uint64_t)__double_as_longlong(a.y), S, h0);
+        const uint32_t n1 = const_image((uint64_t)__double_as_longlong(b.x), (uint64_t)__double_as_longlong(b.y), S, h1);
+        if (n0 == 0u || n1 == 0u) {
+          atomicOr(&ctl->err, (unsigned)E_NONFINITE);
+        } else {
+          uint32_t* w0 = dir_entry(P, c0);
+          uint32_t* w1 = dir_entry(P, c1);
+          for (int k = 0; k < 8; ++k) {
+            w0[4 + k] = h0[k];
+            w1[4 + k] = h1[k];
+          }
+          w0[0] = n0;
+          w1[0] = n1;
+          dE += (long long)n0 + (long long)n1 - (long long)b0 - (long long)b1;
+          wr += n0 + n1;
+        }
+      }
+      QC_PHASE(5);
+      continue;
+    }
 
     load_image_block(P, c0, img0, pages0, cap);
     if (has1) load_image_block(P, c1, img1, pages1, cap);
@@ -98,8 +147,10 @@ __global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
       free_pages_t0(P, cc, pages0, np0);
       if (has1) free_pages_t0(P, cc, pages1, np1);
     }
+    QC_PHASE(0);
     const bool ok0 = decode_block<VPT>(img0, b0, kc, tile0, s);
     const bool ok1 = has1 ? decode_block<VPT>(img1, b1, kc, tile1, s) : true;
+    QC_PHASE(1);
     if (!ok0 || !ok1) {
       if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
       break;
@@ -110,10 +161,11 @@ __global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
     if (L.pair) {
       for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
         if ((i & L.lo_mask) != L.lo_vals) continue;
-        double2 a = t0[i], b = t1[i];
+        const uint32_t pi = tile_amp(i);
+        double2 a = t0[pi], b = t1[pi];
         apply_pair(L.g, a, b);
-        t0[i] = a;
-        t1[i] = b;
+        t0[pi] = a;
+        t1[pi] = b;
       }
     } else {
       const uint32_t tb = 1u << L.target, lowm = tb - 1u;
@@ -123,15 +175,18 @@ __global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
         double2* tt = (q < A / 2u) ? t0 : t1;
         const uint32_t i0 = ((p & ~lowm) << 1) | (p & lowm);
         if ((i0 & L.lo_mask) != L.lo_vals) continue;
-        double2 a = tt[i0], b = tt[i0 | tb];
+        const uint32_t p0 = tile_amp(i0), p1 = tile_amp(i0 | tb);
+        double2 a = tt[p0], b = tt[p1];
         apply_pair(L.g, a, b);
-        tt[i0] = a;
-        tt[i0 | tb] = b;
+        tt[p0] = a;
+        tt[p1] = b;
       }
     }
     __syncthreads();
+    QC_PHASE(2);
     const uint32_t n0 = encode_block<VPT>(tile0, kc, S, -1, img0, cap, s, &ctl->err);
     const uint32_t n1 = has1 ? encode_block<VPT>(tile1, kc, S, -1, img1, cap, s, &ctl->err) : 1u;
+    QC_PHASE(3);
     if (n0 == 0u || n1 == 0u) break;
     if (threadIdx.x == 0) {
       s_np[0] = pages_for(n0, kc);
@@ -148,8 +203,13 @@ __global__ void __launch_bounds__(kThreads) k_gate(const GateLaunch L) {
     dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
     wr += n0 + (has1 ? n1 : 0u);
     __syncthreads();
+    QC_PHASE(4);
   }
+#undef QC_PHASE
   if (threadIdx.x == 0) {
+    if (L.prof)
+      for (int k = 0; k < 6; ++k)
+        if (s_ph[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)s_ph[k]);
     P.cache_n[blockIdx.x] = cc.n;
     if (dE) atomicAdd(&ctl->dE, (unsigned long long)dE);
     if (rd) atomicAdd(&ctl->bytes_in, rd);
@@ -221,12 +281,12 @@ __global__ void __launch_bounds__(kThreads) k_init_chunk0(const Pool P, unsigned
   const int kc = P.kc;
   const uint32_t N = 2u << kc, cap = codedcap(kc);
   uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
-  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
   __shared__ uint32_t s_np;
   __shared__ int s_ok;
-  for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[j] = j == 0 ? 0x3FF0000000000000ull : 0ull;
+  for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[tile_val(j)] = j == 0 ? 0x3FF0000000000000ull : 0ull;
   __syncthreads();
   const uint32_t n0 = encode_block<VPT>(tile, kc, 64u, -1, img, imgcap(kc), s, &P.ctl->err);
   if (threadIdx.x == 0) {
@@ -255,12 +315,12 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t N = 2u << kc, cap = codedcap(kc);
   uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
-  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
   for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in) + c * N;
-    for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[j] = src[j];
+    for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[tile_val(j)] = src[j];
     __syncthreads();
     const uint32_t n = encode_block<VPT>(tile, kc, S, force, img, cap, s, err);
     uint4* dst = reinterpret_cast<uint4*>(out + c * stride);
@@ -278,7 +338,7 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t N = 2u << kc, cap = codedcap(kc);
   uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
-  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
   for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -295,7 +355,7 @@ __global__ void __launch_bounds__(kThreads)
     const bool ok = decode_block<VPT>(img, fits ? len : 16u, kc, tile, s);
     if (!ok && threadIdx.x == 0) atomicOr(err, (unsigned)E_CORRUPT);
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(out) + c * N;
-    for (uint32_t j = threadIdx.x; j < N; j += kThreads) dst[j] = tile[j];
+    for (uint32_t j = threadIdx.x; j < N; j += kThreads) dst[j] = tile[tile_val(j)];
     __syncthreads();
   }
 }
@@ -307,9 +367,9 @@ __global__ void __launch_bounds__(kThreads)
     k_decode_range(const Pool P, unsigned long long first_amp, unsigned long long count, double* out) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int kc = P.kc;
-  const uint32_t N = 2u << kc, A = 1u << kc, cap = imgcap(kc);
+  const uint32_t A = 1u << kc, cap = imgcap(kc);
   uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
-  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
   const unsigned long long cfirst = first_amp >> kc, clast = (first_amp + count - 1ull) >> kc;
@@ -327,8 +387,8 @@ __global__ void __launch_bounds__(kThreads)
     for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
       const unsigned long long a = base + i;
       if (a >= first_amp && a < first_amp + count) {
-        dst[2 * (a - first_amp)] = tile[2 * i];
-        dst[2 * (a - first_amp) + 1] = tile[2 * i + 1];
+        dst[2 * (a - first_amp)] = tile[tile_val(2 * i)];
+        dst[2 * (a - first_amp) + 1] = tile[tile_val(2 * i + 1)];
       }
     }
     __syncthreads();
@@ -342,9 +402,9 @@ __global__ void __launch_bounds__(kThreads)
     k_chunk_reduce(const Pool P, unsigned long long cfirst, unsigned long long nchunks, const double* ref, double* out) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int kc = P.kc;
-  const uint32_t N = 2u << kc, A = 1u << kc, cap = imgcap(kc);
+  const uint32_t A = 1u << kc, cap = imgcap(kc);
   uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
-  uint8_t* img = reinterpret_cast<uint8_t*>(tile + N);
+  uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
   __shared__ double red[3][kThreads];
@@ -361,7 +421,7 @@ __global__ void __launch_bounds__(kThreads)
     const double* v = reinterpret_cast<const double*>(tile);
     double x = 0.0, y = 0.0, z = 0.0;
     for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
-      const double pr = v[2 * i], pi = v[2 * i + 1];
+      const double pr = v[tile_val(2 * i)], pi = v[tile_val(2 * i + 1)];
       z += __fma_rn(pr, pr, __dmul_rn(pi, pi));
       if (DOT) {
         const double rr = ref[(cl << kc) * 2 + 2 * i], ri = ref[(cl << kc) * 2 + 2 * i + 1];

@@ -20,6 +20,7 @@ struct GateLaunch {
   uint32_t lo_mask, lo_vals;     // controls inside a chunk
   int target;                    // target bit (in-chunk gates)
   int pair;                      // 1: target >= chunk_log2
+  int prof;                      // 1: accumulate per-phase SM cycles
 };
 
 int vpt_for(int kc);

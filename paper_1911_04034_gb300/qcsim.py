@@ -39,11 +39,13 @@ class Stats(C.Structure):
         ("ratio", C.c_double), ("min_ratio", C.c_double), ("eps_current", C.c_double),
         ("fidelity_lb_sum", C.c_double), ("fidelity_lb_prod", C.c_double), ("eps_switch_gate", C.c_int64),
         ("sig_bits_current", C.c_int32), ("level", C.c_int32), ("chunk_log2", C.c_int32), ("block_log2", C.c_int32),
+        ("phase_cycles", C.c_uint64 * 6),
     ]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["chunks_by_mode"] = list(self.chunks_by_mode)
+        d["phase_cycles"] = list(self.phase_cycles)
         return d
 
 
@@ -211,8 +213,9 @@ class Sim:
         _check(lib().sim_stats(self._h, C.byref(st)), "sim_stats")
         return st.as_dict()
 
-    def set_timing(self, on: bool) -> None:
-        _check(lib().sim_set_timing(self._h, int(bool(on))), "sim_set_timing")
+    def set_timing(self, on) -> None:
+        """0 off, 1 gate-kernel events, 2 events and per-phase SM cycles."""
+        _check(lib().sim_set_timing(self._h, int(on)), "sim_set_timing")
 
     def timing(self) -> dict:
         """Gate-kernel time (CUDA events), launches and image bytes read/written since
