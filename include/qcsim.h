@@ -196,6 +196,26 @@ sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2,
 sim_status sim_codec_decode(const uint8_t* in, uint64_t in_stride, const uint32_t* in_len, uint64_t n_chunks,
                             int chunk_log2, double* out, int on_device);
 
+/* The encoder of sim_codec_encode for callers that must not allocate device memory
+ * (the paper has no counterpart; this is a deployment variant).  In, out and out_len
+ * are host pointers with the meaning of sim_codec_encode.  Where sim_codec_encode
+ * obtains its staging buffer with cudaMalloc on every call, this call stages through
+ * one fixed device array of 8 MiB that the library declares (held by every GPU that
+ * loads the library until the process exits), so it never calls cudaMalloc, cudaFree
+ * or an allocating library routine.  That suits processes whose device memory is
+ * already owned by another allocator or bounded by a fixed budget.
+ *  - A request whose inputs, images and lengths need more than the array returns
+ *    SIM_ERR_INVALID ("request larger than the 8 MiB scratch"): n_chunks *
+ *    (16 * 2^chunk_log2 + out_stride) + 4 * n_chunks + 768 bytes must fit in 8 MiB.
+ *  - The first call on each device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - All calls on a device share the array: calls that overlap on the same device
+ *    (other host threads or streams) race and must be serialised by the caller.
+ *    Each call resets the parts it uses, so results never depend on earlier calls.
+ *  - Works on the legacy default stream and returns when the images are on the host. */
+sim_status sim_codec_encode_noalloc(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
+                                    uint8_t* out, uint64_t out_stride, uint32_t* out_len);
+
 /* ---------------------------------------------------------------------------------
  * Uncompressed complex128 state vector on the same GPU (the comparator of the
  * compressed path; same gate arithmetic).  16 * 2^n bytes of device memory.

@@ -119,6 +119,8 @@ int device_sms() {
 
 }  // namespace
 
+void qc::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct sim {
   int n = 0, b = 0, kc = 0, ladder = 0;
   double eps_max = 0.0, tau = 0.9;

@@ -23,6 +23,9 @@ struct GateLaunch {
   int prof;                      // 1: accumulate per-phase SM cycles
 };
 
+// Records the message sim_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 int vpt_for(int kc);
 size_t gate_smem_bytes(int kc);
 size_t codec_smem_bytes(int kc);

@@ -78,6 +78,7 @@ def lib():
             "sim_layout": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.POINTER(C.c_int)],
             "sim_codec_encode": [vp, u64, i32, dbl, i32, vp, u64, vp, i32],
             "sim_codec_decode": [vp, u64, vp, u64, i32, vp, i32],
+            "sim_codec_encode_noalloc": [vp, u64, i32, dbl, i32, vp, u64, vp],
             "sim_set_timing": [vp, i32],
             "sim_timing": [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                            C.POINTER(C.c_uint64)],
@@ -261,6 +262,21 @@ def codec_encode(values, chunk_log2: int, eps: float, force_mode: int = -1):
     _check(lib().sim_codec_encode(C.c_void_p(_ptr(x)), n, chunk_log2, float(eps), force_mode, C.c_void_p(_ptr(out)),
                                   stride, C.c_void_p(_ptr(lens)), 0), "sim_codec_encode")
     return [out[k * stride: k * stride + int(lens[k])].tobytes() for k in range(n)], lens
+
+
+def codec_encode_noalloc(values, chunk_log2: int, eps: float, force_mode: int = -1):
+    """Like codec_encode for host arrays, through sim_codec_encode_noalloc: the
+    library stages the call in its fixed device array instead of allocating."""
+    stride = codec_stride(chunk_log2)
+    x = np.ascontiguousarray(values, dtype=np.complex128)
+    n = x.size >> chunk_log2
+    assert n << chunk_log2 == x.size
+    out = np.zeros(max(1, n) * stride, dtype=np.uint8)
+    lens = np.zeros(max(1, n), dtype=np.uint32)
+    _check(lib().sim_codec_encode_noalloc(C.c_void_p(_ptr(x)), n, chunk_log2, float(eps), force_mode,
+                                          C.c_void_p(_ptr(out)), stride, C.c_void_p(_ptr(lens))),
+           "sim_codec_encode_noalloc")
+    return [out[k * stride: k * stride + int(lens[k])].tobytes() for k in range(n)], lens[:n]
 
 
 def codec_decode(images: list[bytes], chunk_log2: int) -> np.ndarray:
