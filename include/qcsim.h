@@ -130,6 +130,30 @@ sim_status sim_apply_gate(sim_t* sim, const sim_gate* gate);
  * returns any device-side error. */
 sim_status sim_apply_circuit(sim_t* sim, const sim_gate* gates, size_t n_gates);
 
+/* Batched form: runs `count` circuits, circuits[k] (n_gates[k] gates) on handle
+ * sims[k], together.  Gate step t applies gate t of every circuit that has one with a
+ * single fused-kernel launch covering the work items of all of them (and one
+ * bookkeeping launch); with use_graph != 0 the whole launch sequence is captured once
+ * into a CUDA graph and replayed.  Each handle keeps its own pool, controller and
+ * statistics, and ends in exactly the state sim_apply_circuit would give it.  The
+ * handles must be distinct and share chunk_log2; launches go to sims[0]'s stream.
+ * All gates are validated first.  Synchronises; returns the first device error. */
+sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const* circuits, const size_t* n_gates,
+                           int use_graph);
+
+/* Chunk-size autotuner: for each candidate chunk_log2, creates a handle (budget raw/4,
+ * pool raw + 1/8), applies the first half of the probe circuit, then times the fused
+ * kernel over the second half; *best receives the candidate with the most amplitude
+ * updates per second of kernel time, rates[i] (if not NULL) each candidate's rate. */
+sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,
+                              const int* candidates, int n_candidates, int* best, double* rates);
+
+/* Chunk modes the encoder chooses from for later gates (bit m = mode m).  The default
+ * 0x1F is Solution C (Section 4.2) with its Zstd stand-in modes ZERO..RAW; 0x3F adds
+ * SPLIT, Solution D (the real parts, then the imaginary parts, XOR-coded).  The set
+ * must contain 0x1F. */
+sim_status sim_set_modes(sim_t* sim, uint32_t modes);
+
 /* Waits for queued work and returns the device error state. */
 sim_status sim_sync(sim_t* sim);
 
@@ -177,7 +201,7 @@ const char* sim_last_error(void);
  * 16-byte header [mode, S, log2 P, 0, payload bytes u32, coded values u32,
  * residual bits u32] then the payload (a multiple of 16 bytes); modes 0 ZERO,
  * 1 CONST, 2 PERIOD, 3 STREAM, 4 RAW (Section 4.2 Solution C for the coded streams;
- * the modes stand in for its Zstd stage).  The encoder truncates with
+ * the modes stand in for its Zstd stage), 5 SPLIT (Solution D).  The encoder truncates with
  * S = 12 - EXP(eps) bits (eps = 0: 64 bits), forced to 64 for a chunk holding a
  * nonzero subnormal, and keeps the smallest image (ties: lower mode); force_mode
  * >= 0 selects a mode instead (SIM_ERR_INVALID if it does not apply).
@@ -189,6 +213,11 @@ const char* sim_last_error(void);
  * pointers are device pointers; else host pointers. */
 sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
                             uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device);
+
+/* sim_codec_encode with the automatic choice restricted to the mode set `modes`
+ * (see sim_set_modes). */
+sim_status sim_codec_encode_ex(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
+                               uint32_t modes, uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device);
 
 /* Decodes n_chunks images (image k at in + k * in_stride, length in_len[k]) into
  * out = n_chunks * 2^(chunk_log2+1) doubles.  SIM_ERR_CORRUPT if any image fails

@@ -29,8 +29,9 @@ _lock = threading.Lock()
 _lib = None
 
 OK, ERR_INVALID, ERR_OOM, ERR_CORRUPT, ERR_STATE = 0, -1, -2, -4, -6
-MODE_ZERO, MODE_CONST, MODE_PERIOD, MODE_STREAM, MODE_RAW = 0, 1, 2, 3, 4
-MODE_NAMES = ("ZERO", "CONST", "PERIOD", "STREAM", "RAW")
+MODE_ZERO, MODE_CONST, MODE_PERIOD, MODE_STREAM, MODE_RAW, MODE_SPLIT = 0, 1, 2, 3, 4, 5
+MODE_NAMES = ("ZERO", "CONST", "PERIOD", "STREAM", "RAW", "SPLIT")
+DEFAULT_MODES = 0x1F  # Solution C; SPLIT (Solution D) only when asked for
 
 
 class OracleError(RuntimeError):
@@ -95,6 +96,8 @@ def lib():
             "orc_chunk_sig_bits": (C.c_int, [u64p, C.c_size_t, C.c_int]),
             "orc_mode_sizes": (C.c_int, [u64p, C.c_int, C.c_int, u64p]),
             "orc_encode_chunk": (C.c_long, [u64p, C.c_int, C.c_int, C.c_int, u8p, C.c_size_t]),
+            "orc_encode_chunk_mask": (C.c_long, [u64p, C.c_int, C.c_int, C.c_int, C.c_uint, u8p, C.c_size_t]),
+            "orc_csim_set_modes": (C.c_int, [C.c_void_p, C.c_uint]),
             "orc_decode_chunk": (C.c_int, [u8p, C.c_size_t, C.c_int, u64p]),
             "orc_gate_check": (C.c_int, [C.POINTER(_Gate), C.c_int]),
             "orc_sv_init": (None, [dp, C.c_int]),
@@ -175,13 +178,13 @@ def _as_bits(values) -> np.ndarray:
     return np.ascontiguousarray(v, dtype=np.uint64)
 
 
-def encode_chunk(values, kc: int, S: int, force_mode: int = -1) -> bytes:
+def encode_chunk(values, kc: int, S: int, force_mode: int = -1, modes: int = DEFAULT_MODES) -> bytes:
     """values: 2^kc complex128 amplitudes (or 2^(kc+1) float64 / uint64 patterns)."""
     x = _as_bits(values)
     assert x.size == 2 << kc, (x.size, kc)
     cap = 16 + 8 * x.size + x.size // 4 + 64  # forced STREAM can exceed RAW
     out = np.zeros(cap, dtype=np.uint8)
-    L = lib().orc_encode_chunk(_ptr(x, C.c_uint64), kc, S, force_mode, _ptr(out, C.c_uint8), cap)
+    L = lib().orc_encode_chunk_mask(_ptr(x, C.c_uint64), kc, S, force_mode, modes, _ptr(out, C.c_uint8), cap)
     if L < 0:
         raise OracleError(int(L), "encode_chunk")
     return out[:L].tobytes()
@@ -203,7 +206,7 @@ def mode_sizes(values, kc: int, S: int) -> list[int]:
     rc = lib().orc_mode_sizes(_ptr(x, C.c_uint64), kc, S, _ptr(sizes, C.c_uint64))
     if rc:
         raise OracleError(rc, "mode_sizes")
-    return [int(s) for s in sizes[:5]]
+    return [int(s) for s in sizes[:6]]
 
 
 # ---------------------------------------------------------- state vector --- #
@@ -265,7 +268,7 @@ class CSim:
     work item, and the error-bound controller run before every gate."""
 
     def __init__(self, n: int, block_log2: int, chunk_log2: int, eps_max: float, budget: int, tau: float = 0.9,
-                 ladder: int = LADDER_JUMP):
+                 ladder: int = LADDER_JUMP, modes: int = DEFAULT_MODES):
         self._h = lib().orc_csim_create(n, block_log2, chunk_log2, float(eps_max), int(budget), float(tau),
                                         int(ladder))
         if not self._h:
@@ -273,6 +276,10 @@ class CSim:
         self.n = n
         self.kc = int(lib().orc_csim_chunk_log2(self._h))
         self.b = int(lib().orc_csim_block_log2(self._h))
+        if modes != DEFAULT_MODES:
+            rc = lib().orc_csim_set_modes(self._h, modes)
+            if rc:
+                raise OracleError(rc, "csim_set_modes")
         self.nchunks = int(lib().orc_csim_nchunks(self._h))
 
     def close(self):

@@ -40,7 +40,9 @@
 #define ORC_MODE_PERIOD 2
 #define ORC_MODE_STREAM 3
 #define ORC_MODE_RAW 4
-#define ORC_NMODES 5
+#define ORC_MODE_SPLIT 5
+#define ORC_NMODES 6
+#define ORC_DEFAULT_MODES 0x1F /* Solution C: ZERO..RAW; SPLIT (Solution D) on request */
 
 /* Planted-mistake switch used only by the mutation tests: each nonzero value
  * introduces one plausible bug so the tests can show that some pin catches it. */
@@ -157,6 +159,8 @@ static uint64_t bw_get(const uint64_t* w, uint64_t pos, int r) {
  *            i >= P; payload = XOR coding of the first 2P values.
  *   STREAM : XOR coding of all N values.
  *   RAW    : the N truncated values verbatim.
+ *   SPLIT  : Solution D (Section 4.2): the real parts of all amplitudes, then the
+ *            imaginary parts, XOR-coded like STREAM (enabled by a mode mask).
  * XOR coding layout: the 2-bit codes, four per byte with the first code in the top
  * two bits, padded to 16 bytes; then the residual bit stream in 64-bit
  * little-endian words, first bit = bit 63 of word 0, padded to 16 bytes.
@@ -262,6 +266,15 @@ static int find_period(const uint64_t* t, int kc) {
   return -1;
 }
 
+/* Solution D order: u[k] = re of amplitude k for k < 2^kc, then the imaginary parts. */
+static void split_order(const uint64_t* t, int kc, uint64_t* u) {
+  size_t A = (size_t)1 << kc;
+  for (size_t k = 0; k < A; ++k) {
+    u[k] = t[2 * k];
+    u[A + k] = t[2 * k + 1];
+  }
+}
+
 /* Size in bytes of the image in mode m, or 0 if m does not apply. */
 static size_t mode_size(int m, const uint64_t* t, int kc, int S, int period) {
   size_t N = (size_t)2 << kc;
@@ -281,6 +294,13 @@ static size_t mode_size(int m, const uint64_t* t, int kc, int S, int period) {
       return 16 + codes_area(N) + resid_area(xor_bits(t, N, S));
     case ORC_MODE_RAW:
       return 16 + 8 * N;
+    case ORC_MODE_SPLIT: {
+      uint64_t* u = (uint64_t*)malloc(N * 8);
+      split_order(t, kc, u);
+      size_t sz = 16 + codes_area(N) + resid_area(xor_bits(u, N, S));
+      free(u);
+      return sz;
+    }
   }
   return 0;
 }
@@ -294,14 +314,17 @@ int orc_mode_sizes(const uint64_t* x, int kc, int S_req, uint64_t* sizes_out) {
   uint64_t* t = (uint64_t*)malloc(N * 8);
   for (size_t j = 0; j < N; ++j) t[j] = orc_truncate(x[j], S);
   int period = find_period(t, kc);
-  for (int m = 0; m < ORC_NMODES; ++m) sizes_out[m] = mode_size(m, t, kc, S, period);
+  for (int m = 0; m < ORC_NMODES; ++m) sizes_out[m] = mode_size(m, t, kc, S, period);  /* 6 entries */
   free(t);
   return ORC_OK;
 }
 
 /* Encode one chunk (raw bit patterns x[0..N)) with requested bits S_req.
- * force_mode < 0 selects the smallest image.  Returns the image length or an error. */
-long orc_encode_chunk(const uint64_t* x, int kc, int S_req, int force_mode, uint8_t* out, size_t cap) {
+ * force_mode >= 0 selects that mode; otherwise the smallest image among the modes
+ * whose bit is set in mode_mask (ties: lower mode number).  Returns the image length
+ * or an error. */
+long orc_encode_chunk_mask(const uint64_t* x, int kc, int S_req, int force_mode, unsigned mode_mask, uint8_t* out,
+                           size_t cap) {
   if (kc < 0 || kc > 20) return ORC_ERR_INVALID;
   if (S_req < 13 || S_req > 64) return ORC_ERR_INVALID;
   size_t N = (size_t)2 << kc;
@@ -319,9 +342,11 @@ long orc_encode_chunk(const uint64_t* x, int kc, int S_req, int force_mode, uint
     if (best == 0) { free(t); return ORC_ERR_INVALID; }
   } else {
     for (int m = 0; m < ORC_NMODES; ++m) {
-      size_t s = mode_size(m, t, kc, S, period);
-      if (s != 0 && (mode < 0 || s < best)) { best = s; mode = m; }
+      if (!((mode_mask >> m) & 1u)) continue;
+      size_t sz = mode_size(m, t, kc, S, period);
+      if (sz != 0 && (mode < 0 || sz < best)) { best = sz; mode = m; }
     }
+    if (mode < 0) { free(t); return ORC_ERR_INVALID; }
   }
   if (best > cap) { free(t); return ORC_ERR_INVALID; }
   memset(out, 0, best);
@@ -349,12 +374,25 @@ long orc_encode_chunk(const uint64_t* x, int kc, int S_req, int force_mode, uint
       nv = (uint32_t)N;
       for (size_t j = 0; j < N; ++j) put_u64(p + 8 * j, t[j]);
       break;
+    case ORC_MODE_SPLIT: {
+      uint64_t* u = (uint64_t*)malloc(N * 8);
+      split_order(t, kc, u);
+      nv = (uint32_t)N;
+      bits = xor_bits(u, N, S);
+      xor_write(u, N, S, p, bits);
+      free(u);
+      break;
+    }
   }
   put_u32(out + 4, (uint32_t)(best - 16));
   put_u32(out + 8, nv);
   put_u32(out + 12, (uint32_t)bits);
   free(t);
   return (long)best;
+}
+
+long orc_encode_chunk(const uint64_t* x, int kc, int S_req, int force_mode, uint8_t* out, size_t cap) {
+  return orc_encode_chunk_mask(x, kc, S_req, force_mode, ORC_DEFAULT_MODES, out, cap);
 }
 
 /* Decode an image into N raw bit patterns. */
@@ -389,6 +427,19 @@ int orc_decode_chunk(const uint8_t* img, size_t len, int kc, uint64_t* out) {
       if (lp != 0 || nv != N || bits != 0 || plen != 8 * N) return ORC_ERR_CORRUPT;
       for (size_t j = 0; j < N; ++j) out[j] = get_u64(p + 8 * j);
       return ORC_OK;
+    case ORC_MODE_SPLIT: {
+      if (lp != 0 || nv != N) return ORC_ERR_CORRUPT;
+      uint64_t* u = (uint64_t*)malloc(N * 8);
+      int rc = xor_read(p, plen, nv, S, bits, u);
+      size_t A = N / 2;
+      if (!rc)
+        for (size_t k = 0; k < A; ++k) {
+          out[2 * k] = u[k];
+          out[2 * k + 1] = u[A + k];
+        }
+      free(u);
+      return rc;
+    }
   }
   return ORC_ERR_CORRUPT;
 }
@@ -552,6 +603,7 @@ typedef struct {
 
 typedef struct {
   int n, b, kc, ladder, S_cur, level, nlevels;
+  unsigned modes;
   double levels[8];
   double eps_max, tau;
   uint64_t budget, thresh, inflight, nchunks, E, Emax, gates;
@@ -567,7 +619,7 @@ void orc_csim_destroy(orc_csim* s);
 static int csim_store(orc_csim* s, uint64_t c, const uint64_t* vals) {
   size_t cap = 16 + 8 * ((size_t)2 << s->kc);
   uint8_t* buf = (uint8_t*)malloc(cap);
-  long L = orc_encode_chunk(vals, s->kc, s->S_cur, -1, buf, cap);
+  long L = orc_encode_chunk_mask(vals, s->kc, s->S_cur, -1, s->modes, buf, cap);
   if (L < 0) { free(buf); return (int)L; }
   uint8_t* fit = (uint8_t*)realloc(buf, (size_t)L);
   if (fit) buf = fit;
@@ -597,6 +649,7 @@ orc_csim* orc_csim_create(int n, int block_log2, int chunk_log2, double eps_max,
   /* Eq. totalnbBytes with r = 1: two decompressed blocks are in flight. */
   s->inflight = (uint64_t)2 << (s->b + 4);
   s->ladder = ladder;
+  s->modes = ORC_DEFAULT_MODES;
   s->S_cur = 64;
   s->switch_gate = -1;
   s->lb_sum = 0.0;
@@ -761,5 +814,12 @@ void orc_csim_stats(const orc_csim* s, orc_stats* st) {
 }
 
 uint64_t orc_csim_nchunks(const orc_csim* s) { return s->nchunks; }
+
+/* Mode set the encoder chooses from for later gates (bit m = mode m). */
+int orc_csim_set_modes(orc_csim* s, unsigned mask) {
+  if ((mask & 0x1Fu) != 0x1Fu || (mask >> ORC_NMODES)) return ORC_ERR_INVALID;
+  s->modes = mask;
+  return ORC_OK;
+}
 int orc_csim_chunk_log2(const orc_csim* s) { return s->kc; }
 int orc_csim_block_log2(const orc_csim* s) { return s->b; }

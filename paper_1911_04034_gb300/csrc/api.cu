@@ -140,6 +140,7 @@ struct sim {
   // gate-kernel timing
   bool timing = false;
   bool phases = false;
+  uint32_t modes = qc::kDefaultModes;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   size_t ev_next = 0;
@@ -339,7 +340,8 @@ sim_status sim_set_stream(sim_t* s, void* stream) {
   return SIM_OK;
 }
 
-static sim_status enqueue_gate(sim* s, const sim_gate* g) {
+// Work description of one gate (Section 3.3 segments, see the top of this file).
+static GateLaunch make_launch(sim* s, const sim_gate* g) {
   const int kc = s->kc, t = g->target;
   const uint64_t A = 1ull << kc;
   GateLaunch L{};
@@ -353,6 +355,7 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
   L.lo_vals = (uint32_t)(g->ctrl_vals & (A - 1ull));
   L.target = t;
   L.prof = s->phases ? 1 : 0;
+  L.modes = s->modes;
   if (t >= kc) {
     L.pair = 1;
     L.pair_bit = 1ull << (t - kc);
@@ -366,6 +369,11 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
     L.nact = 1ull << popcount64(L.free_mask);
     L.items = (L.nact + 1ull) / 2ull;
   }
+  return L;
+}
+
+static sim_status enqueue_gate(sim* s, const sim_gate* g) {
+  const GateLaunch L = make_launch(s, g);
   const int grid = (uint64_t)s->grid < L.items ? s->grid : (int)L.items;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (s->timing) {
@@ -384,7 +392,7 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
     s->ev_pending.emplace_back(e0, e1);
   }
   CK(qc::launch_post(s->P, s->cp, s->grid, s->st), "post kernel launch");
-  s->amp_updates += L.nact * A;
+  s->amp_updates += L.nact << s->kc;
   return SIM_OK;
 }
 
@@ -451,6 +459,14 @@ sim_status sim_timing(sim_t* s, double* ms, uint64_t* launches, uint64_t* bytes_
   s->t_bytes_out0 = out;
   s->ev_pending.clear();
   s->ev_next = 0;
+  return SIM_OK;
+}
+
+sim_status sim_set_modes(sim_t* s, uint32_t modes) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  if ((modes & qc::kDefaultModes) != qc::kDefaultModes || (modes >> qc::M_NMODES))
+    return fail(SIM_ERR_INVALID, "the mode set must contain ZERO..RAW (0x1F) and only known modes");
+  s->modes = modes;
   return SIM_OK;
 }
 
@@ -618,9 +634,141 @@ sim_status sim_chunk_image(sim_t* s, uint64_t c, uint8_t* out, size_t cap, size_
   return SIM_OK;
 }
 
+// ------------------------------------------------------------ batch ------ //
+sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const* circuits, const size_t* n_gates,
+                           int use_graph) {
+  if (!sims || !circuits || !n_gates || count < 1) return fail(SIM_ERR_INVALID, "bad batch arguments");
+  const int kc = sims[0] ? sims[0]->kc : -1;
+  size_t steps = 0;
+  std::string why;
+  for (int k = 0; k < count; ++k) {
+    sim* s = sims[k];
+    if (!s) return fail(SIM_ERR_INVALID, "NULL handle in the batch");
+    if (s->kc != kc) return fail(SIM_ERR_INVALID, "all handles of a batch must share chunk_log2");
+    if (sim_status r = s->guard()) return r;
+    for (int j = 0; j < k; ++j)
+      if (sims[j] == s) return fail(SIM_ERR_INVALID, "a handle appears twice in the batch");
+    if (n_gates[k] && !circuits[k]) return fail(SIM_ERR_INVALID, "NULL circuit in the batch");
+    for (size_t i = 0; i < n_gates[k]; ++i)
+      if (!gate_ok(circuits[k] + i, s->n, &why)) return fail(SIM_ERR_INVALID, "circuit %d gate %zu: %s", k, i, why.c_str());
+    if (n_gates[k] > steps) steps = n_gates[k];
+  }
+  if (steps == 0) return SIM_OK;
+  // step t holds gate t of every circuit that has one; its jobs' items are numbered
+  // consecutively
+  std::vector<qc::BatchJob> jobs;
+  std::vector<size_t> off(steps + 1, 0);
+  std::vector<unsigned long long> total(steps, 0);
+  int grid = sims[0]->grid;
+  for (int k = 1; k < count; ++k) grid = sims[k]->grid < grid ? sims[k]->grid : grid;
+  for (size_t t = 0; t < steps; ++t) {
+    off[t] = jobs.size();
+    unsigned long long begin = 0;
+    for (int k = 0; k < count; ++k) {
+      if (t >= n_gates[k]) continue;
+      qc::BatchJob j;
+      j.L = make_launch(sims[k], circuits[k] + t);
+      j.begin = begin;
+      begin += j.L.items;
+      jobs.push_back(j);
+    }
+    total[t] = begin;
+  }
+  off[steps] = jobs.size();
+  cudaStream_t st = sims[0]->st;
+  qc::BatchJob* d_jobs = nullptr;
+  CK(cudaMalloc(&d_jobs, jobs.size() * sizeof(qc::BatchJob)), "batch job list");
+  cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(qc::BatchJob), cudaMemcpyHostToDevice, st);
+  // A graph is captured on a private stream (the legacy default stream cannot be
+  // captured), ordered after the work already queued on the handles' stream.
+  cudaStream_t cs = st;
+  cudaEvent_t ready = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && use_graph) {
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  }
+  for (size_t t = 0; t < steps && e == cudaSuccess; ++t) {
+    const int n = (int)(off[t + 1] - off[t]);
+    const int g = (unsigned long long)grid < total[t] ? grid : (int)total[t];
+    e = qc::launch_gate_batch(d_jobs + off[t], n, total[t], kc, g, cs);
+    if (e == cudaSuccess) e = qc::launch_post_batch(d_jobs + off[t], n, grid, cs);
+  }
+  if (use_graph && cs != st) {
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (ready) cudaEventDestroy(ready);
+  if (cs != st) cudaStreamDestroy(cs);
+  cudaFree(d_jobs);
+  if (e != cudaSuccess) {
+    for (int k = 0; k < count; ++k) sims[k]->poisoned = SIM_ERR_CUDA;
+    return cuda_fail(e, "batched launch");
+  }
+  for (int k = 0; k < count; ++k) {
+    const uint64_t A = 1ull << sims[k]->kc;
+    for (size_t i = 0; i < n_gates[k]; ++i) sims[k]->amp_updates += make_launch(sims[k], circuits[k] + i).nact * A;
+  }
+  sim_status worst = SIM_OK;
+  for (int k = 0; k < count; ++k) {
+    sim_status r = sims[k]->check_device();
+    if (r != SIM_OK && worst == SIM_OK) worst = r;
+  }
+  return worst;
+}
+
+sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,
+                              const int* candidates, int n_candidates, int* best, double* rates) {
+  if (!probe || !candidates || !best || n_candidates < 1 || n_probe < 2)
+    return fail(SIM_ERR_INVALID, "bad autotune arguments");
+  const uint64_t raw = 16ull << n_qubits;
+  double best_rate = -1.0;
+  *best = candidates[0];
+  for (int i = 0; i < n_candidates; ++i) {
+    sim_t* s = nullptr;
+    sim_status r = sim_create_ex(n_qubits, block_log2, candidates[i], err_bound, raw / 4 ? raw / 4 : 1, 0.9, 0,
+                                 raw + raw / 8 + (64ull << 20), &s);
+    if (r != SIM_OK) return r;
+    const size_t half = n_probe / 2;
+    r = sim_apply_circuit(s, probe, half);
+    if (r == SIM_OK) r = sim_set_timing(s, 1);
+    const uint64_t before = s->amp_updates;
+    if (r == SIM_OK) r = sim_apply_circuit(s, probe + half, n_probe - half);
+    double ms = 0.0;
+    if (r == SIM_OK) r = sim_timing(s, &ms, nullptr, nullptr, nullptr);
+    const double rate = (r == SIM_OK && ms > 0.0) ? (double)(s->amp_updates - before) / (ms * 1e-3) : 0.0;
+    sim_destroy(s);
+    if (r != SIM_OK) return r;
+    if (rates) rates[i] = rate;
+    if (rate > best_rate) {
+      best_rate = rate;
+      *best = candidates[i];
+    }
+  }
+  return SIM_OK;
+}
+
 // ------------------------------------------------------------ codec ------ //
 sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
                             uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device) {
+  return sim_codec_encode_ex(in, n_chunks, chunk_log2, eps, force_mode, qc::kDefaultModes, out, out_stride, out_len,
+                             on_device);
+}
+
+sim_status sim_codec_encode_ex(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
+                               uint32_t modes, uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device) {
+  if ((modes & qc::kDefaultModes) != qc::kDefaultModes || (modes >> qc::M_NMODES))
+    return fail(SIM_ERR_INVALID, "the mode set must contain ZERO..RAW (0x1F) and only known modes");
   if (!in || !out || !out_len) return fail(SIM_ERR_INVALID, "NULL argument");
   if (chunk_log2 < 0 || chunk_log2 > qc::kMaxKC) return fail(SIM_ERR_INVALID, "chunk_log2 must be in [0, 11]");
   const int S = sig_bits_of(eps);
@@ -646,8 +794,8 @@ sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2,
     cudaMemcpy((void*)din, in, in_bytes, cudaMemcpyHostToDevice);
   }
   cudaMemset(derr, 0, sizeof(unsigned int));
-  cudaError_t e = qc::launch_codec_encode(din, n_chunks, chunk_log2, (uint32_t)S, force_mode, dout, out_stride, dlen,
-                                          derr, 0);
+  cudaError_t e = qc::launch_codec_encode(din, n_chunks, chunk_log2, (uint32_t)S, force_mode, modes, dout, out_stride,
+                                          dlen, derr, 0);
   unsigned int herr = 0;
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost);

@@ -23,7 +23,9 @@ constexpr int kPage = 512;
 constexpr int kCacheCap = 128;
 constexpr int kMaxKC = 11;
 
-enum : uint32_t { M_ZERO = 0, M_CONST = 1, M_PERIOD = 2, M_STREAM = 3, M_RAW = 4, M_NMODES = 5 };
+enum : uint32_t { M_ZERO = 0, M_CONST = 1, M_PERIOD = 2, M_STREAM = 3, M_RAW = 4, M_SPLIT = 5, M_NMODES = 6 };
+// Solution C's modes; SPLIT (Solution D, re parts then im parts) only on request
+constexpr uint32_t kDefaultModes = 0x1Fu;
 
 enum : uint32_t { E_OK = 0, E_OOM = 1, E_CORRUPT = 2, E_NONFINITE = 4, E_MODE = 8 };
 
@@ -120,62 +122,105 @@ __device__ __forceinline__ int warp_incl_max(int v) {
   return v;
 }
 
+// Warp totals of the block scans, double-buffered: each scan uses buffer pp and flips
+// pp, so two consecutive scans never share a buffer and one barrier per scan is
+// enough (the other scan's barrier separates a buffer's readers from its next writer).
 struct ScanSmem {
-  uint32_t wsum[kWarps];
-  int wmax[3][kWarps];
-  uint32_t total;
+  uint32_t wsum2[2][kWarps];
+  uint32_t wsum[2][kWarps];
+  uint32_t wor[2][kWarps];
+  uint32_t wand[2][kWarps];
+  int wmax[2][3][kWarps];
   uint32_t bits_period;
-  int flag;
-  int period;
+  uint32_t pad[3];
 };
 
-// Exclusive prefix sum over the CTA; *total receives the sum.
-__device__ __forceinline__ uint32_t block_excl_add(uint32_t v, ScanSmem& s, uint32_t* total) {
+// Exclusive prefix sum over the CTA with one barrier; also ORs `fo` and ANDs `fa`
+// over the CTA.  All threads must call it.
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t fo, uint32_t fa, ScanSmem& s, int& pp,
+                                               uint32_t* total, uint32_t* all_or, uint32_t* all_and) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t inc = warp_incl_add(v);
-  if (lane == 31) s.wsum[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t x = lane < kWarps ? s.wsum[lane] : 0u;
-    uint32_t xi = warp_incl_add(x);
-    if (lane < kWarps) s.wsum[lane] = xi - x;
-    if (lane == kWarps - 1) s.total = xi;
+  const uint32_t inc = warp_incl_add(v);
+  const uint32_t wo = __reduce_or_sync(0xffffffffu, fo);
+  const uint32_t wa = __reduce_and_sync(0xffffffffu, fa);
+  if (lane == 31) {
+    s.wsum[pp][w] = inc;
+    s.wor[pp][w] = wo;
+    s.wand[pp][w] = wa;
   }
   __syncthreads();
-  uint32_t r = s.wsum[w] + inc - v;
-  *total = s.total;
-  __syncthreads();
-  return r;
+  uint32_t base = 0, tot = 0, o = 0, a = 0xffffffffu;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) {
+    const uint32_t x = s.wsum[pp][i];
+    base += i < w ? x : 0u;
+    tot += x;
+    o |= s.wor[pp][i];
+    a &= s.wand[pp][i];
+  }
+  pp ^= 1;
+  *total = tot;
+  *all_or = o;
+  *all_and = a;
+  return base + inc - v;
 }
 
-// Exclusive max-scan of three ints over the CTA (identity -1).
-__device__ __forceinline__ void block_excl_max3(int a[3], ScanSmem& s) {
+// Two exclusive prefix sums at once (same barrier), plus OR/AND flags.
+__device__ __forceinline__ void block_scan2(uint32_t v, uint32_t v2, uint32_t fo, uint32_t fa, ScanSmem& s, int& pp,
+                                            uint32_t* ex, uint32_t* ex2, uint32_t* total, uint32_t* total2,
+                                            uint32_t* all_or, uint32_t* all_and) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_add(v);
+  const uint32_t inc2 = warp_incl_add(v2);
+  const uint32_t wo = __reduce_or_sync(0xffffffffu, fo);
+  const uint32_t wa = __reduce_and_sync(0xffffffffu, fa);
+  if (lane == 31) {
+    s.wsum[pp][w] = inc;
+    s.wsum2[pp][w] = inc2;
+    s.wor[pp][w] = wo;
+    s.wand[pp][w] = wa;
+  }
+  __syncthreads();
+  uint32_t base = 0, tot = 0, base2 = 0, tot2 = 0, o = 0, a = 0xffffffffu;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) {
+    const uint32_t x = s.wsum[pp][i], x2 = s.wsum2[pp][i];
+    base += i < w ? x : 0u;
+    base2 += i < w ? x2 : 0u;
+    tot += x;
+    tot2 += x2;
+    o |= s.wor[pp][i];
+    a &= s.wand[pp][i];
+  }
+  pp ^= 1;
+  *ex = base + inc - v;
+  *ex2 = base2 + inc2 - v2;
+  *total = tot;
+  *total2 = tot2;
+  *all_or = o;
+  *all_and = a;
+}
+
+// Exclusive max-scan of three ints over the CTA (identity -1), one barrier.
+__device__ __forceinline__ void block_excl_max3(int a[3], ScanSmem& s, int& pp) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int inc[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     inc[b] = warp_incl_max(a[b]);
-    if (lane == 31) s.wmax[b][w] = inc[b];
-  }
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      int x = lane < kWarps ? s.wmax[b][lane] : -1;
-      int xi = warp_incl_max(x);
-      int ex = __shfl_up_sync(0xffffffffu, xi, 1);
-      if (lane == 0) ex = -1;
-      if (lane < kWarps) s.wmax[b][lane] = ex;
-    }
+    if (lane == 31) s.wmax[pp][b][w] = inc[b];
   }
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     int ex = __shfl_up_sync(0xffffffffu, inc[b], 1);
     if (lane == 0) ex = -1;
-    a[b] = max(ex, s.wmax[b][w]);
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i)
+      if (i < w) ex = max(ex, s.wmax[pp][b][i]);
+    a[b] = ex;
   }
-  __syncthreads();
+  pp ^= 1;
 }
 
 // ---------------------------------------------------------- bit helpers --- //
@@ -197,6 +242,16 @@ __device__ __forceinline__ uint64_t get_bits(const uint64_t* w, uint32_t pos, ui
   return hi >> (64u - r);
 }
 __device__ __forceinline__ uint64_t trunc_mask(uint32_t S) { return S >= 64u ? ~0ull : (~0ull << (64u - S)); }
+
+// The residual stream is a sequence of 64-bit little-endian words read most
+// significant bit first; as 32-bit units in stream order, unit q is memory word q ^ 1.
+// 64 stream bits starting at bit position o (needs 8 readable bytes past the stream).
+__device__ __forceinline__ void stream_window(const uint32_t* m32, uint32_t o, uint32_t& hi, uint32_t& lo) {
+  const uint32_t q = o >> 5, sh = o & 31u;
+  const uint32_t x0 = m32[q ^ 1u], x1 = m32[(q + 1u) ^ 1u], x2 = m32[(q + 2u) ^ 1u];
+  hi = __funnelshift_l(x1, x0, sh);
+  lo = __funnelshift_l(x2, x1, sh);
+}
 
 // ------------------------------------------------------------ tile layout -- //
 // A decoded chunk lives in shared memory as 2^kc amplitudes of 16 bytes with one
@@ -245,13 +300,23 @@ __device__ __forceinline__ void store_vals(uint64_t* tile, uint32_t j0, uint32_t
 }
 
 // ----------------------------------------------------------- decoder ----- //
-template <int VPT>
+// Position in the chunk of the k-th coded value: k itself, or for SPLIT (Solution D)
+// the real parts of all amplitudes first, then the imaginary parts.
+template <bool SPLIT>
+__device__ __forceinline__ uint32_t coded_pos(uint32_t k, uint32_t A) {
+  return SPLIT ? (k < A ? 2u * k : 2u * (k - A) + 1u) : k;
+}
+
+template <int VPT, bool SPLIT>
 __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t nv, uint32_t S, uint32_t bits,
-                                 uint64_t* tile, ScanSmem& s) {
+                                 uint64_t* tile, ScanSmem& s, int& pp) {
+  const uint32_t A = nv >> 1;
   const uint32_t* codes32 = reinterpret_cast<const uint32_t*>(payload);
   const uint32_t cb = code_bytes(nv);
-  const uint64_t* words = reinterpret_cast<const uint64_t*>(payload + cb);
+  const uint32_t* m32 = reinterpret_cast<const uint32_t*>(payload + cb);
   const uint32_t j0 = threadIdx.x * VPT;
+  // the 2-bit codes of this thread's values share one 32-bit word (VPT divides 16)
+  const uint32_t cword = j0 < nv ? codes32[j0 >> 4] : 0u;
   uint32_t c[VPT], r[VPT];
   uint32_t sum = 0;
 #pragma unroll
@@ -260,17 +325,17 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
     c[k] = 3u;
     r[k] = 0u;
     if (j < nv) {
-      const uint32_t word = codes32[j >> 4];
-      const uint32_t sh = 8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u);
-      c[k] = (word >> sh) & 3u;
+      c[k] = (cword >> (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u))) & 3u;
       r[k] = resid_len(c[k], S);
       sum += r[k];
     }
   }
-  uint32_t total;
-  uint32_t o = block_excl_add(sum, s, &total);
+  uint32_t total, fo, fa;
+  uint32_t o = block_scan(sum, 0u, 0u, s, pp, &total, &fo, &fa);
   if (total != bits || cb + resid_bytes(bits) != plen) return false;
-  // explicit part of every value: residual bits placed at [8c, S)
+  // explicit part of every value: the residual bits placed at [8c, S)
+  const uint64_t mS = trunc_mask(S);
+  const uint32_t mhi = (uint32_t)(mS >> 32), mlo = (uint32_t)mS;
   uint64_t e[VPT];
   int lw[3] = {-1, -1, -1};
 #pragma unroll
@@ -278,22 +343,34 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
     const uint32_t j = j0 + k;
     e[k] = 0ull;
     if (j < nv) {
-      if (r[k]) e[k] = (get_bits(words, o, r[k]) << (64u - r[k])) >> (8u * c[k]);
+      uint32_t hi, lo;
+      stream_window(m32, o, hi, lo);
+      const uint32_t d = 8u * c[k];
+      const uint32_t lo2 = __funnelshift_r(lo, hi, d), hi2 = hi >> d;
+      e[k] = ((uint64_t)(hi2 & mhi) << 32) | (uint64_t)(lo2 & mlo);
       o += r[k];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
         if (c[k] <= (uint32_t)b) lw[b] = (int)j;
     }
   }
-  store_vals<VPT>(tile, j0, nv, e);
-  // last explicit writer of leading byte b before this thread's first value
-  block_excl_max3(lw, s);  // ends with a barrier: every explicit part is visible
+  if (SPLIT) {
+#pragma unroll
+    for (int k = 0; k < VPT; ++k)
+      if (j0 + k < nv) tile[tile_val(coded_pos<true>(j0 + k, A))] = e[k];
+  } else {
+    store_vals<VPT>(tile, j0, nv, e);
+  }
+  // last explicit writer of leading byte b before this thread's first value (the
+  // scan's barrier also makes every explicit part visible)
+  block_excl_max3(lw, s, pp);
   // byte b of a value with code c > b repeats byte b of the last value that wrote it
   // explicitly (code <= b); before the first value it is 0
   uint64_t lastb[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b)
-    lastb[b] = lw[b] >= 0 ? (tile[tile_val((uint32_t)lw[b])] & (0xFF00000000000000ull >> (8 * b))) : 0ull;
+    lastb[b] = lw[b] >= 0 ? (tile[tile_val(coded_pos<SPLIT>((uint32_t)lw[b], A))] & (0xFF00000000000000ull >> (8 * b)))
+                          : 0ull;
   __syncthreads();  // every thread has read the explicit parts it needs
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
@@ -308,7 +385,13 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
       e[k] = v;
     }
   }
-  store_vals<VPT>(tile, j0, nv, e);
+  if (SPLIT) {
+#pragma unroll
+    for (int k = 0; k < VPT; ++k)
+      if (j0 + k < nv) tile[tile_val(coded_pos<true>(j0 + k, A))] = e[k];
+  } else {
+    store_vals<VPT>(tile, j0, nv, e);
+  }
   __syncthreads();
   return true;
 }
@@ -316,7 +399,7 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
 // Decodes the staged image (header + payload in shared memory) into the tile.
 // Returns false (tile zero-filled) if the image fails its checks.
 template <int VPT>
-__device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uint64_t* tile, ScanSmem& s) {
+__device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uint64_t* tile, ScanSmem& s, int& pp) {
   // img_bytes <= the caller's staging buffer; images in the pool are at most RAW size,
   // images handed to the codec entry points at most max_coded_bytes(kc)
   const uint32_t N = 2u << kc;
@@ -333,11 +416,16 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
       case M_PERIOD: ok = lp >= 1 && (int)lp < kc && nv == (2u << lp); break;
       case M_STREAM: ok = lp == 0 && nv == N; break;
       case M_RAW: ok = lp == 0 && nv == N && bits == 0 && plen == 8u * N; break;
+      case M_SPLIT: ok = lp == 0 && nv == N; break;
       default: ok = false;
     }
   }
+  if (ok && mode == M_SPLIT) {
+    if (decode_xor_block<VPT, true>(payload, plen, nv, S, bits, tile, s, pp)) return true;
+    ok = false;
+  }
   if (ok && (mode == M_PERIOD || mode == M_STREAM)) {
-    ok = decode_xor_block<VPT>(payload, plen, nv, S, bits, tile, s);
+    ok = decode_xor_block<VPT, false>(payload, plen, nv, S, bits, tile, s, pp);
     if (ok && mode == M_PERIOD) {
       ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tile);
       const uint32_t P = nv >> 1;  // period in amplitudes
@@ -359,16 +447,84 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
 }
 
 // ----------------------------------------------------------- encoder ----- //
-// Encodes the tile (raw bit patterns; overwritten with the truncated values) into
-// img (img_cap bytes).  S_req = 12 - EXP(eps) or 64.  force_mode < 0: smallest image
-// (never larger than RAW).  Returns the image length, or 0 with *err set (non-finite
-// value, or a forced mode that does not apply or does not fit in img_cap).
+// Writes the 2-bit codes and the residual stream of coded values [j0, j0 + VPT) of this
+// thread (values >= nv are not coded) into an image whose payload was cleared; o0 is
+// the stream offset of value j0.
 template <int VPT>
-__device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int force_mode, uint8_t* img,
-                                 uint32_t img_cap, ScanSmem& s, unsigned int* err) {
+__device__ __forceinline__ void pack_xor(uint8_t* img, uint32_t nv, uint32_t j0, uint32_t o0, const uint64_t t[VPT],
+                                         const uint32_t c[VPT], const uint32_t r[VPT]) {
+  // codes: one 32-bit word per 16 values
+  uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
+  uint32_t cw = 0;
+  uint32_t oend = o0;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    if (j < nv) {
+      cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
+      oend += r[k];
+    }
+  }
+  if (j0 < nv && cw) atomicOr(&codes32[j0 >> 4], cw);
+  // residual bits: this thread owns stream bits [o0, oend); interior 32-bit units are
+  // written once with plain stores, the two end units (shared with the neighbours)
+  // with atomicOr into the cleared payload
+  if (oend > o0) {
+    uint32_t* m32 = reinterpret_cast<uint32_t*>(img + 16 + code_bytes(nv));
+    const uint32_t qf = o0 >> 5, ql = (oend - 1u) >> 5;
+    uint32_t qb = qf, w0 = 0, w1 = 0, w2 = 0, o = o0;
+#define QC_FLUSH(q, v)                                        \
+do {                                                        \
+  if ((q) <= ql && (v) != 0u) {                             \
+    if ((q) == qf || (q) == ql) atomicOr(&m32[(q) ^ 1u], (v)); \
+    else m32[(q) ^ 1u] = (v);                               \
+  }                                                         \
+} while (0)
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (j0 + k < nv && r[k]) {
+        const uint32_t q = o >> 5, sh = o & 31u;
+        while (qb < q) {
+          QC_FLUSH(qb, w0);
+          w0 = w1;
+          w1 = w2;
+          w2 = 0;
+          ++qb;
+        }
+        const uint32_t d = 8u * c[k];
+        const uint32_t thi = (uint32_t)(t[k] >> 32), tlo = (uint32_t)t[k];
+        const uint32_t xhi = __funnelshift_l(tlo, thi, d), xlo = tlo << d;
+        w0 |= xhi >> sh;
+        w1 |= __funnelshift_r(xlo, xhi, sh);
+        w2 |= __funnelshift_r(0u, xlo, sh);
+        o += r[k];
+      }
+    }
+    QC_FLUSH(qb, w0);
+    QC_FLUSH(qb + 1u, w1);
+    QC_FLUSH(qb + 2u, w2);
+#undef QC_FLUSH
+  }
+}
+
+
+// Encodes the tile (raw bit patterns; overwritten with the truncated values) into
+// img (img_cap bytes, nothing else in it is live).  S_req = 12 - EXP(eps) or 64.
+// force_mode < 0: smallest image (never larger than RAW).  Returns the image length,
+// or 0 with *err set (non-finite value, or a forced mode that does not apply or does
+// not fit in img_cap).
+template <int VPT>
+__device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int force_mode, uint32_t modes, uint8_t* img,
+                                 uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err) {
   const uint32_t N = 2u << kc, A = 1u << kc;
   const uint32_t j0 = threadIdx.x * VPT;
   const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
+  // 0. clear the payload area the packers OR into (the buffer is free here)
+  {
+    const uint32_t span = min(img_cap, max_coded_bytes(kc)) - 16u;
+    uint4* z = reinterpret_cast<uint4*>(img + 16);
+    for (uint32_t u = threadIdx.x; u < span / 16u; u += kThreads) z[u] = make_uint4(0u, 0u, 0u, 0u);
+  }
   // 1. chunk-wide width: a nonzero subnormal forces 64 bits; non-finite is an error
   uint64_t t[VPT];
   load_vals<VPT>(tile, j0, N, t);
@@ -381,11 +537,13 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
       sub |= (e == 0u) && ((t[k] << 12) != 0ull);
     }
   }
-  const int anynf = __syncthreads_or(nonfin);
-  const int anysub = __syncthreads_or(sub);
-  if (anynf) {
-    if (threadIdx.x == 0) atomicOr(err, (unsigned)E_NONFINITE);
-    return 0;
+  bool anysub = false;
+  if (__syncthreads_or(nonfin || sub)) {  // rare: settle which of the two it was
+    if (__syncthreads_or(nonfin)) {
+      if (threadIdx.x == 0) atomicOr(err, (unsigned)E_NONFINITE);
+      return 0;
+    }
+    anysub = true;
   }
   const uint32_t S = anysub ? 64u : S_req;
   const uint64_t mask = trunc_mask(S);
@@ -400,37 +558,52 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   }
   store_vals<VPT>(tile, j0, N, t);
   __syncthreads();
-  // 3. codes and residual lengths (predecessor of value 0 is 0)
+  // 3. codes and residual lengths (predecessor of value 0 is 0); CONST and top-level
+  //    PERIOD tests on this thread's values
   uint32_t c[VPT], r[VPT], sum = 0;
   uint64_t prev = (j0 > 0 && j0 <= N) ? tile[tile_val(j0 - 1)] : 0ull;
+  const uint64_t a0x = tile[tile_val(0)], a0y = tile[tile_val(1)];
+  const uint32_t Ptop = kc >= 2 ? (1u << (kc - 1)) : 0u;
+  bool cst = true, gtop = true;
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
     c[k] = 3u;
     r[k] = 0u;
-    if (j0 + k < N) {
+    if (j < N) {
       c[k] = xor_code(t[k], prev);
       r[k] = resid_len(c[k], S);
       sum += r[k];
       prev = t[k];
+      cst &= t[k] == ((j & 1u) ? a0y : a0x);
+      const uint32_t a = j >> 1;
+      if (a & Ptop) gtop &= t[k] == tile[tile_val(2u * (a ^ Ptop) + (j & 1u))];
     }
   }
-  // 4. ZERO and CONST tests
-  const ulonglong2 a0 = t2[tile_amp(0)];
-  bool cst = true;
-  for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
-    const ulonglong2 q = t2[tile_amp(i)];
-    cst &= (q.x == a0.x) && (q.y == a0.y);
+  // Solution D order (SPLIT): only its residual length is needed unless it wins
+  const bool want_split = force_mode == (int)M_SPLIT || (force_mode < 0 && ((modes >> M_SPLIT) & 1u));
+  uint32_t sum2 = 0;
+  if (want_split) {
+    uint64_t pv = j0 > 0 && j0 <= N ? tile[tile_val(coded_pos<true>(j0 - 1, A))] : 0ull;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (j0 + k < N) {
+        const uint64_t v = tile[tile_val(coded_pos<true>(j0 + k, A))];
+        sum2 += resid_len(xor_code(v, pv), S);
+        pv = v;
+      }
+    }
   }
-  const int allzero = !__syncthreads_or(nz);
-  const int allconst = __syncthreads_and(cst);
-  // 5. offsets of the residual stream
-  uint32_t total;
-  const uint32_t o0 = block_excl_add(sum, s, &total);
-  // 6. smallest power-of-two period P (amplitudes) with 2 <= P < 2^kc: the chunk is
+  uint32_t total, f_or, f_and, o0, o2, total2;
+  block_scan2(sum, sum2, nz ? 1u : 0u, (cst ? 1u : 0u) | (gtop ? 2u : 0u), s, pp, &o0, &o2, &total, &total2, &f_or,
+              &f_and);
+  const bool allzero = (f_or & 1u) == 0u;
+  const bool allconst = (f_and & 1u) != 0u;
+  // 4. smallest power-of-two period P (amplitudes), 2 <= P < 2^kc: the chunk is
   //    P-periodic iff flipping any amplitude-index bit >= log2 P leaves it unchanged
   int period = -1;
-  if (kc >= 2) {
-    int p = kc - 1;
+  if (kc >= 2 && (f_and & 2u) && (!allconst || force_mode == (int)M_PERIOD)) {
+    int p = kc - 2;
     for (; p >= 1; --p) {
       const uint32_t P = 1u << p;
       bool ok = true;
@@ -442,12 +615,13 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
       }
       if (!__syncthreads_and(ok)) break;
     }
-    if (p < kc - 1) period = p + 1;
+    period = p + 1;
   }
-  // residual bits of the first 2P values
-  if (threadIdx.x == 0) s.bits_period = 0;
-  __syncthreads();
+  // residual bits of the first 2P values (rare: only periodic chunks)
+  uint32_t bits_p = 0;
   if (period > 0) {
+    if (threadIdx.x == 0) s.bits_period = 0;
+    __syncthreads();
     const uint32_t nvp = 2u << period;
     uint32_t o = o0;
 #pragma unroll
@@ -456,15 +630,17 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
       o += r[k];
     }
     __syncthreads();
+    bits_p = s.bits_period;
+    __syncthreads();
   }
-  const uint32_t bits_p = s.bits_period;
-  // 7. sizes and the choice
+  // 5. sizes and the choice (every thread computes the same)
   uint32_t size[M_NMODES];
   size[M_ZERO] = allzero ? 16u : 0u;
   size[M_CONST] = allconst ? 32u : 0u;
   size[M_PERIOD] = period > 0 ? 16u + code_bytes(2u << period) + resid_bytes(bits_p) : 0u;
   size[M_STREAM] = 16u + code_bytes(N) + resid_bytes(total);
   size[M_RAW] = 16u + 8u * N;
+  size[M_SPLIT] = want_split ? 16u + code_bytes(N) + resid_bytes(total2) : 0u;
   uint32_t mode = 0, best = 0;
   if (force_mode >= 0) {
     if (force_mode >= (int)M_NMODES || size[force_mode] == 0 || size[force_mode] > img_cap) {
@@ -477,79 +653,54 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
     best = 0xffffffffu;
 #pragma unroll
     for (uint32_t m = 0; m < M_NMODES; ++m)
-      if (size[m] != 0 && size[m] < best) { best = size[m]; mode = m; }
+      if (((modes >> m) & 1u) && size[m] != 0 && size[m] < best) { best = size[m]; mode = m; }
     if (best > img_cap) {  // cannot happen: RAW always fits a buffer of max_image_bytes
       if (threadIdx.x == 0) atomicOr(err, (unsigned)E_MODE);
       return 0;
     }
   }
-  // 8. write the image
+  // 6. write the image
   uint32_t nv = 0, rbits = 0;
   if (mode == M_CONST) nv = 2;
   if (mode == M_PERIOD) { nv = 2u << period; rbits = bits_p; }
   if (mode == M_STREAM) { nv = N; rbits = total; }
   if (mode == M_RAW) nv = N;
-  uint64_t* pay64 = reinterpret_cast<uint64_t*>(img + 16);
-  const uint32_t plen = best - 16u;
-  if (mode == M_PERIOD || mode == M_STREAM)
-    for (uint32_t q = threadIdx.x; q < plen / 8u; q += kThreads) pay64[q] = 0ull;
+  if (mode == M_SPLIT) { nv = N; rbits = total2; }
   if (threadIdx.x == 0) {
     uint32_t* h = reinterpret_cast<uint32_t*>(img);
     h[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | ((mode == M_PERIOD ? (uint32_t)period : 0u) << 16);
-    h[1] = plen;
+    h[1] = best - 16u;
     h[2] = nv;
     h[3] = rbits;
   }
-  __syncthreads();
+  uint64_t* pay64 = reinterpret_cast<uint64_t*>(img + 16);
   if (mode == M_CONST) {
     if (threadIdx.x == 0) {
-      pay64[0] = a0.x;
-      pay64[1] = a0.y;
+      pay64[0] = a0x;
+      pay64[1] = a0y;
     }
   } else if (mode == M_RAW) {
     ulonglong2* p2 = reinterpret_cast<ulonglong2*>(pay64);
     for (uint32_t a = threadIdx.x; a < A; a += kThreads) p2[a] = t2[tile_amp(a)];
-  } else if (mode == M_PERIOD || mode == M_STREAM) {
-    uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
-    uint64_t* words = reinterpret_cast<uint64_t*>(img + 16 + code_bytes(nv));
-    uint32_t cw = 0, cw_idx = 0xffffffffu;
-    uint64_t acc = 0;
-    uint32_t acc_w = 0xffffffffu;
-    uint32_t o = o0;
+  } else if (mode == M_SPLIT) {
+    // recompute the Solution D codes (the scan kept only their total)
+    uint64_t pv = j0 > 0 && j0 <= N ? tile[tile_val(coded_pos<true>(j0 - 1, A))] : 0ull;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
-      const uint32_t j = j0 + k;
-      if (j < nv) {
-        const uint32_t widx = j >> 4;
-        if (widx != cw_idx) {
-          if (cw_idx != 0xffffffffu && cw) atomicOr(&codes32[cw_idx], cw);
-          cw = 0;
-          cw_idx = widx;
-        }
-        cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
-        const uint32_t rr = r[k];
-        if (rr) {
-          const uint64_t val = (t[k] << (8u * c[k])) >> (64u - rr);
-          const uint32_t w = o >> 6, off = o & 63u;
-          if (w != acc_w) {
-            if (acc_w != 0xffffffffu && acc) atomicOr((unsigned long long*)&words[acc_w], (unsigned long long)acc);
-            acc = 0;
-            acc_w = w;
-          }
-          if (off + rr <= 64u) {
-            acc |= val << (64u - off - rr);
-          } else {
-            acc |= val >> (off + rr - 64u);
-            if (acc) atomicOr((unsigned long long*)&words[acc_w], (unsigned long long)acc);
-            acc_w = w + 1;
-            acc = val << (128u - off - rr);
-          }
-          o += rr;
-        }
+      if (j0 + k < N) {
+        t[k] = tile[tile_val(coded_pos<true>(j0 + k, A))];
+        c[k] = xor_code(t[k], pv);
+        r[k] = resid_len(c[k], S);
+        pv = t[k];
+      } else {
+        t[k] = 0ull;
+        c[k] = 3u;
+        r[k] = 0u;
       }
     }
-    if (cw_idx != 0xffffffffu && cw) atomicOr(&codes32[cw_idx], cw);
-    if (acc_w != 0xffffffffu && acc) atomicOr((unsigned long long*)&words[acc_w], (unsigned long long)acc);
+    pack_xor<VPT>(img, nv, j0, o2, t, c, r);
+  } else if (mode == M_PERIOD || mode == M_STREAM) {
+    pack_xor<VPT>(img, nv, j0, o0, t, c, r);
   }
   __syncthreads();
   return best;

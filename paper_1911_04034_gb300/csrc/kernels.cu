@@ -22,8 +22,11 @@ __host__ __device__ __forceinline__ uint32_t imgcap(int kc) { return round16(max
 __host__ __device__ __forceinline__ uint32_t codedcap(int kc) { return round16(max_coded_bytes(kc)); }
 __host__ __device__ __forceinline__ uint32_t pagelist_words(int kc) { return (max_pages(kc) + 3u) & ~3u; }
 
+// Each image buffer keeps 16 spare bytes: the decoder's bit window reads up to 8 bytes
+// past the end of a residual stream.
+__host__ __device__ __forceinline__ uint32_t imgbuf(int kc) { return imgcap(kc) + 16u; }
 size_t gate_smem_bytes(int kc) {
-  return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgcap(kc)) + 2 * 4 * size_t(pagelist_words(kc)) +
+  return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgbuf(kc)) + 2 * size_t(dir_stride(kc)) +
          round16(sizeof(ScanSmem));
 }
 size_t codec_smem_bytes(int kc) {
@@ -31,194 +34,291 @@ size_t codec_smem_bytes(int kc) {
 }
 
 // ------------------------------------------------------------- the gate -- //
-template <int VPT>
-__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3) k_gate(const GateLaunch L) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int kc = L.P.kc;
-  const uint32_t A = 1u << kc;
-  const uint32_t cap = imgcap(kc);
-  uint64_t* tile0 = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* tile1 = tile0 + tile_words(kc);
-  uint8_t* img0 = reinterpret_cast<uint8_t*>(tile1 + tile_words(kc));
-  uint8_t* img1 = img0 + cap;
-  uint32_t* pages0 = reinterpret_cast<uint32_t*>(img1 + cap);
-  uint32_t* pages1 = pages0 + pagelist_words(kc);
-  ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages1 + pagelist_words(kc));
-  __shared__ int s_oom;
-  __shared__ uint32_t s_np[2];
-
-  const Pool& P = L.P;
-  DevCtl* ctl = P.ctl;
-  // Section 3.7: the bound for this gate, from E after the previous gate.  Every CTA
-  // evaluates the same rule on the same values (k_post alone writes them).
-  const int lvl = next_level(L.ctl, ctl->E, ctl->level);
-  const uint32_t S = (uint32_t)level_bits(L.ctl, lvl);
-
+// Shared-memory layout of the fused kernel and the per-CTA state it carries between
+// work items (page cache, byte counters, scan-buffer parity).
+struct GateSmem {
+  uint64_t *tile0, *tile1;
+  uint8_t *img0, *img1;
+  uint32_t *ent0, *ent1;  // copies of the two directory entries (header, page ids or image)
+  ScanSmem* s;
+  long long* ph;          // per-phase cycles, [6] = last clock (profiling)
+  int* oom;
+  uint32_t* np;
+};
+struct GateCta {
   CtaCache cc;
-  cc.ids = P.cache + (size_t)blockIdx.x * kCacheCap;
-  cc.n = 0;
-  if (threadIdx.x == 0) cc.n = P.cache_n[blockIdx.x];
-  long long dE = 0;
-  unsigned long long rd = 0, wr = 0;
-  // phases: 0 stage images, 1 decode, 2 apply, 3 encode, 4 commit, 5 constant fast
-  // paths; [6] holds the last clock (kept in shared memory, thread 0 only)
-  __shared__ long long s_ph[7];
-  if (L.prof && threadIdx.x == 0) {
-    for (int k = 0; k < 6; ++k) s_ph[k] = 0;
-    s_ph[6] = clock64();
-  }
-#define QC_PHASE(k)                   \
-  if (L.prof && threadIdx.x == 0) {   \
-    const long long now_ = clock64(); \
-    s_ph[k] += now_ - s_ph[6];        \
-    s_ph[6] = now_;                   \
-  }
+  long long dE;
+  unsigned long long rd, wr;
+  int pp;
+};
 
-  for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x) {
-    // one barrier that also broadcasts thread 0's view of the error word
-    if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned int*)&ctl->err) != 0u)) break;
-    unsigned long long c0, c1;
-    bool has1;
-    if (L.pair) {
-      c0 = deposit_bits(item, L.free_mask) | L.hi_vals;
-      c1 = c0 | L.pair_bit;
-      has1 = true;
-    } else {
-      const unsigned long long k0 = 2ull * item;
-      c0 = deposit_bits(k0, L.free_mask) | L.hi_vals;
-      has1 = k0 + 1 < L.nact;
-      c1 = has1 ? (deposit_bits(k0 + 1, L.free_mask) | L.hi_vals) : 0ull;
-    }
-    const uint32_t* e0 = dir_entry(P, c0);
-    const uint32_t* e1 = dir_entry(P, c1);
-    const uint32_t np0 = e0[1], np1 = has1 ? e1[1] : 0u;
-    const uint32_t b0 = e0[0], b1 = has1 ? e1[0] : 0u;
-    if (b0 > cap || b1 > cap || np0 > max_pages(kc) || np1 > max_pages(kc)) {
-      if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
-      break;
-    }
-    // An all-zero chunk maps to an all-zero chunk under any gate (signed zeros are
-    // stored as +0), and its image does not depend on the bound: skip it.
-    const bool z0 = np0 == 0 && b0 == 16u && e0[4] == 0u;
-    const bool z1 = !has1 || (np1 == 0 && b1 == 16u && e1[4] == 0u);
-    rd += b0 + b1;
-    if (z0 && z1) {
-      QC_PHASE(5);
-      continue;
-    }
-    // Two constant chunks (ZERO or CONST images, held inline) under a cross-chunk gate
-    // with no in-chunk controls: every pair sees the same inputs, so one pair gives
-    // both output chunks, which are constant again.
-    if (L.pair && L.lo_mask == 0u && inline_cap(kc) >= 32u && np0 == 0u && np1 == 0u &&
-        (z0 || (e0[4] & 0xffu) == M_CONST) &&
-        (z1 || (e1[4] & 0xffu) == M_CONST)) {
-      if (threadIdx.x == 0) {
-        double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
-        if (!z0) a = make_double2(__longlong_as_double(((const long long*)(e0 + 8))[0]),
-                                  __longlong_as_double(((const long long*)(e0 + 8))[1]));
-        if (!z1) b = make_double2(__longlong_as_double(((const long long*)(e1 + 8))[0]),
-                                  __longlong_as_double(((const long long*)(e1 + 8))[1]));
-        apply_pair(L.g, a, b);
-        uint32_t h0[8], h1[8];
-        const uint32_t n0 = const_image((uint64_t)__double_as_longlong(a.x), (uint64_t)__double_as_longlong(a.y), S, h0);
-        const uint32_t n1 = const_image((uint64_t)__double_as_longlong(b.x), (uint64_t)__double_as_longlong(b.y), S, h1);
-        if (n0 == 0u || n1 == 0u) {
-          atomicOr(&ctl->err, (unsigned)E_NONFINITE);
-        } else {
-          uint32_t* w0 = dir_entry(P, c0);
-          uint32_t* w1 = dir_entry(P, c1);
-          for (int k = 0; k < 8; ++k) {
-            w0[4 + k] = h0[k];
-            w1[4 + k] = h1[k];
-          }
-          w0[0] = n0;
-          w1[0] = n1;
-          dE += (long long)n0 + (long long)n1 - (long long)b0 - (long long)b1;
-          wr += n0 + n1;
-        }
-      }
-      QC_PHASE(5);
-      continue;
-    }
+__device__ __forceinline__ GateSmem gate_smem(uint8_t* smem, int kc, uint32_t dir_words, long long* ph, int* oom,
+                                               uint32_t* np) {
+  GateSmem m;
+  m.tile0 = reinterpret_cast<uint64_t*>(smem);
+  m.tile1 = m.tile0 + tile_words(kc);
+  m.img0 = reinterpret_cast<uint8_t*>(m.tile1 + tile_words(kc));
+  m.img1 = m.img0 + imgbuf(kc);
+  m.ent0 = reinterpret_cast<uint32_t*>(m.img1 + imgbuf(kc));
+  m.ent1 = m.ent0 + dir_words;
+  m.s = reinterpret_cast<ScanSmem*>(m.ent1 + dir_words);
+  m.ph = ph;
+  m.oom = oom;
+  m.np = np;
+  return m;
+}
 
-    load_image_block(P, c0, img0, pages0, cap);
-    if (has1) load_image_block(P, c1, img1, pages1, cap);
-    if (threadIdx.x == 0) {
-      free_pages_t0(P, cc, pages0, np0);
-      if (has1) free_pages_t0(P, cc, pages1, np1);
-    }
-    QC_PHASE(0);
-    const bool ok0 = decode_block<VPT>(img0, b0, kc, tile0, s);
-    const bool ok1 = has1 ? decode_block<VPT>(img1, b1, kc, tile1, s) : true;
-    QC_PHASE(1);
-    if (!ok0 || !ok1) {
-      if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
-      break;
-    }
-    // apply the gate to every amplitude pair whose in-chunk control bits match
-    double2* t0 = reinterpret_cast<double2*>(tile0);
-    double2* t1 = reinterpret_cast<double2*>(tile1);
-    if (L.pair) {
-      for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
-        if ((i & L.lo_mask) != L.lo_vals) continue;
-        const uint32_t pi = tile_amp(i);
-        double2 a = t0[pi], b = t1[pi];
-        apply_pair(L.g, a, b);
-        t0[pi] = a;
-        t1[pi] = b;
-      }
-    } else {
-      const uint32_t tb = 1u << L.target, lowm = tb - 1u;
-      const uint32_t tot = has1 ? A : A / 2u;  // pairs over both tiles
-      for (uint32_t q = threadIdx.x; q < tot; q += kThreads) {
-        const uint32_t p = q & (A / 2u - 1u);
-        double2* tt = (q < A / 2u) ? t0 : t1;
-        const uint32_t i0 = ((p & ~lowm) << 1) | (p & lowm);
-        if ((i0 & L.lo_mask) != L.lo_vals) continue;
-        const uint32_t p0 = tile_amp(i0), p1 = tile_amp(i0 | tb);
-        double2 a = tt[p0], b = tt[p1];
-        apply_pair(L.g, a, b);
-        tt[p0] = a;
-        tt[p1] = b;
-      }
-    }
-    __syncthreads();
-    QC_PHASE(2);
-    const uint32_t n0 = encode_block<VPT>(tile0, kc, S, -1, img0, cap, s, &ctl->err);
-    const uint32_t n1 = has1 ? encode_block<VPT>(tile1, kc, S, -1, img1, cap, s, &ctl->err) : 1u;
-    QC_PHASE(3);
-    if (n0 == 0u || n1 == 0u) break;
-    if (threadIdx.x == 0) {
-      s_np[0] = pages_for(n0, kc);
-      s_np[1] = has1 ? pages_for(n1, kc) : 0u;
-      bool ok = alloc_pages_t0(P, cc, pages0, s_np[0]);
-      if (ok && has1) ok = alloc_pages_t0(P, cc, pages1, s_np[1]);
-      if (!ok) atomicOr(&ctl->err, (unsigned)E_OOM);
-      s_oom = !ok;
-    }
-    __syncthreads();
-    if (s_oom) break;
-    store_image_block(P, c0, img0, n0, pages0, s_np[0]);
-    if (has1) store_image_block(P, c1, img1, n1, pages1, s_np[1]);
-    dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
-    wr += n0 + (has1 ? n1 : 0u);
-    __syncthreads();
-    QC_PHASE(4);
-  }
-#undef QC_PHASE
-  if (threadIdx.x == 0) {
-    if (L.prof)
-      for (int k = 0; k < 6; ++k)
-        if (s_ph[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)s_ph[k]);
-    P.cache_n[blockIdx.x] = cc.n;
-    if (dE) atomicAdd(&ctl->dE, (unsigned long long)dE);
-    if (rd) atomicAdd(&ctl->bytes_in, rd);
-    if (wr) atomicAdd(&ctl->bytes_out, wr);
+__device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof, long long* ph) {
+  st.cc.ids = P.cache + (size_t)blockIdx.x * kCacheCap;
+  st.cc.n = 0;
+  if (threadIdx.x == 0) st.cc.n = P.cache_n[blockIdx.x];
+  st.dE = 0;
+  st.rd = st.wr = 0;
+  st.pp = 0;
+  if (prof && threadIdx.x == 0) {
+    for (int k = 0; k < 6; ++k) ph[k] = 0;
+    ph[6] = clock64();
   }
 }
 
+// Thread 0: hands the CTA's page cache and counters back to the simulator.
+__device__ __forceinline__ void cta_end(const GateLaunch& L, GateCta& st, const long long* ph) {
+  if (threadIdx.x != 0) return;
+  DevCtl* ctl = L.P.ctl;
+  if (L.prof)
+    for (int k = 0; k < 6; ++k)
+      if (ph[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)ph[k]);
+  L.P.cache_n[blockIdx.x] = st.cc.n;
+  if (st.dE) atomicAdd(&ctl->dE, (unsigned long long)st.dE);
+  if (st.rd) atomicAdd(&ctl->bytes_in, st.rd);
+  if (st.wr) atomicAdd(&ctl->bytes_out, st.wr);
+}
+
+// Section 3.7: the bound of the running gate, from E after the previous gate.  Every
+// CTA evaluates the same rule on the same values (only the post kernel writes them).
+__device__ __forceinline__ uint32_t gate_bits(const GateLaunch& L) {
+  return (uint32_t)level_bits(L.ctl, next_level(L.ctl, L.P.ctl->E, L.P.ctl->level));
+}
+
+// One work item (two chunks) of a gate: stage, decode, apply, encode, commit.
+// Returns false if the simulator's error word is set (nothing more to do for it).
+template <int VPT>
+__device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long long item, uint32_t S,
+                                          const GateSmem& m, GateCta& st) {
+  const int kc = L.P.kc;
+  const uint32_t A = 1u << kc;
+  const uint32_t cap = imgcap(kc);
+  const Pool& P = L.P;
+  DevCtl* ctl = P.ctl;
+  const uint32_t dw4 = P.dir_words / 4u;  // 16-byte units of a directory entry
+#define QC_PHASE(k)                     \
+  if (L.prof && threadIdx.x == 0) {     \
+    const long long now_ = clock64();   \
+    m.ph[k] += now_ - m.ph[6];          \
+    m.ph[6] = now_;                     \
+  }
+  // one barrier that also broadcasts thread 0's view of the error word
+  if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned int*)&ctl->err) != 0u)) return false;
+  unsigned long long c0, c1;
+  bool has1;
+  if (L.pair) {
+    c0 = deposit_bits(item, L.free_mask) | L.hi_vals;
+    c1 = c0 | L.pair_bit;
+    has1 = true;
+  } else {
+    const unsigned long long k0 = 2ull * item;
+    c0 = deposit_bits(k0, L.free_mask) | L.hi_vals;
+    has1 = k0 + 1 < L.nact;
+    c1 = has1 ? (deposit_bits(k0 + 1, L.free_mask) | L.hi_vals) : 0ull;
+  }
+  // stage 1: both directory entries (warp 0 and warp 1)
+  if (threadIdx.x < 32u) {
+    const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, c0));
+    for (uint32_t i = threadIdx.x; i < dw4; i += 32u) reinterpret_cast<uint4*>(m.ent0)[i] = src[i];
+  } else if (threadIdx.x < 64u && has1) {
+    const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, c1));
+    for (uint32_t i = threadIdx.x - 32u; i < dw4; i += 32u) reinterpret_cast<uint4*>(m.ent1)[i] = src[i];
+  }
+  __syncthreads();
+  const uint32_t np0 = m.ent0[1], np1 = has1 ? m.ent1[1] : 0u;
+  const uint32_t b0 = m.ent0[0], b1 = has1 ? m.ent1[0] : 0u;
+  if (b0 > cap || b1 > cap || np0 > max_pages(kc) || np1 > max_pages(kc) || (np0 == 0u && b0 > inline_cap(kc)) ||
+      (np1 == 0u && b1 > inline_cap(kc)) || (b0 & 15u) || (b1 & 15u)) {
+    if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
+    return false;
+  }
+  // An all-zero chunk maps to an all-zero chunk under any gate (signed zeros are
+  // stored as +0), and its image does not depend on the bound: skip it.
+  const bool z0 = np0 == 0 && b0 == 16u && m.ent0[4] == 0u;
+  const bool z1 = !has1 || (np1 == 0 && b1 == 16u && m.ent1[4] == 0u);
+  st.rd += b0 + b1;
+  if (z0 && z1) {
+    QC_PHASE(5);
+    return true;
+  }
+  // Two constant chunks (ZERO or CONST images, held inline) under a cross-chunk gate
+  // with no in-chunk controls: every pair sees the same inputs, so one pair gives
+  // both output chunks, which are constant again.
+  if (L.pair && L.lo_mask == 0u && inline_cap(kc) >= 32u && np0 == 0u && np1 == 0u &&
+      (z0 || (m.ent0[4] & 0xffu) == M_CONST) && (z1 || (m.ent1[4] & 0xffu) == M_CONST)) {
+    if (threadIdx.x == 0) {
+      double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+      if (!z0) a = make_double2(__longlong_as_double(((const long long*)(m.ent0 + 8))[0]),
+                                __longlong_as_double(((const long long*)(m.ent0 + 8))[1]));
+      if (!z1) b = make_double2(__longlong_as_double(((const long long*)(m.ent1 + 8))[0]),
+                                __longlong_as_double(((const long long*)(m.ent1 + 8))[1]));
+      apply_pair(L.g, a, b);
+      uint32_t h0[8], h1[8];
+      const uint32_t n0 = const_image((uint64_t)__double_as_longlong(a.x), (uint64_t)__double_as_longlong(a.y), S, h0);
+      const uint32_t n1 = const_image((uint64_t)__double_as_longlong(b.x), (uint64_t)__double_as_longlong(b.y), S, h1);
+      if (n0 == 0u || n1 == 0u) {
+        atomicOr(&ctl->err, (unsigned)E_NONFINITE);
+      } else {
+        uint32_t* w0 = dir_entry(P, c0);
+        uint32_t* w1 = dir_entry(P, c1);
+        for (int k = 0; k < 8; ++k) {
+          w0[4 + k] = h0[k];
+          w1[4 + k] = h1[k];
+        }
+        w0[0] = n0;
+        w1[0] = n1;
+        st.dE += (long long)n0 + (long long)n1 - (long long)b0 - (long long)b1;
+        st.wr += n0 + n1;
+      }
+    }
+    QC_PHASE(5);
+    return true;
+  }
+  // stage 2: both images in one pass (inline ones from the entry copies)
+  {
+    const uint32_t u0 = b0 >> 4, u1 = b1 >> 4;
+    constexpr uint32_t upp = kPage / 16;
+    for (uint32_t u = threadIdx.x; u < u0 + u1; u += kThreads) {
+      const bool second = u >= u0;
+      const uint32_t uu = second ? u - u0 : u;
+      const uint32_t* ent = second ? m.ent1 : m.ent0;
+      uint4 v;
+      if ((second ? np1 : np0) == 0u) v = reinterpret_cast<const uint4*>(ent + 4)[uu];
+      else v = __ldcs(reinterpret_cast<const uint4*>(P.pages + (unsigned long long)ent[4 + uu / upp] * kPage) + (uu % upp));
+      reinterpret_cast<uint4*>(second ? m.img1 : m.img0)[uu] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    free_pages_t0(P, st.cc, m.ent0 + 4, np0);
+    if (has1) free_pages_t0(P, st.cc, m.ent1 + 4, np1);
+  }
+  QC_PHASE(0);
+  const bool ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
+  const bool ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
+  QC_PHASE(1);
+  if (!ok0 || !ok1) {
+    if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
+    return false;
+  }
+  // apply the gate to every amplitude pair whose in-chunk control bits match
+  double2* t0 = reinterpret_cast<double2*>(m.tile0);
+  double2* t1 = reinterpret_cast<double2*>(m.tile1);
+  if (L.pair) {
+    for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+      if ((i & L.lo_mask) != L.lo_vals) continue;
+      const uint32_t pi = tile_amp(i);
+      double2 a = t0[pi], b = t1[pi];
+      apply_pair(L.g, a, b);
+      t0[pi] = a;
+      t1[pi] = b;
+    }
+  } else {
+    const uint32_t tb = 1u << L.target, lowm = tb - 1u;
+    const uint32_t tot = has1 ? A : A / 2u;  // pairs over both tiles
+    for (uint32_t q = threadIdx.x; q < tot; q += kThreads) {
+      const uint32_t p = q & (A / 2u - 1u);
+      double2* tt = (q < A / 2u) ? t0 : t1;
+      const uint32_t i0 = ((p & ~lowm) << 1) | (p & lowm);
+      if ((i0 & L.lo_mask) != L.lo_vals) continue;
+      const uint32_t p0 = tile_amp(i0), p1 = tile_amp(i0 | tb);
+      double2 a = tt[p0], b = tt[p1];
+      apply_pair(L.g, a, b);
+      tt[p0] = a;
+      tt[p1] = b;
+    }
+  }
+  __syncthreads();
+  QC_PHASE(2);
+  const uint32_t n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err);
+  const uint32_t n1 = has1 ? encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err) : 1u;
+  QC_PHASE(3);
+  if (n0 == 0u || n1 == 0u) return false;
+  if (threadIdx.x == 0) {
+    m.np[0] = pages_for(n0, kc);
+    m.np[1] = has1 ? pages_for(n1, kc) : 0u;
+    bool ok = alloc_pages_t0(P, st.cc, m.ent0 + 4, m.np[0]);
+    if (ok && has1) ok = alloc_pages_t0(P, st.cc, m.ent1 + 4, m.np[1]);
+    if (!ok) atomicOr(&ctl->err, (unsigned)E_OOM);
+    m.oom[0] = !ok;
+  }
+  __syncthreads();
+  if (m.oom[0]) return false;
+  store_image_block(P, c0, m.img0, n0, m.ent0 + 4, m.np[0]);
+  if (has1) store_image_block(P, c1, m.img1, n1, m.ent1 + 4, m.np[1]);
+  st.dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
+  st.wr += n0 + (has1 ? n1 : 0u);
+  __syncthreads();
+  QC_PHASE(4);
+
+  return true;
+#undef QC_PHASE
+}
+
+template <int VPT>
+__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3) k_gate(const __grid_constant__ GateLaunch L) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ long long s_ph[7];
+  __shared__ int s_oom;
+  __shared__ uint32_t s_np[2];
+  const GateSmem m = gate_smem(smem, L.P.kc, L.P.dir_words, s_ph, &s_oom, s_np);
+  GateCta st;
+  cta_begin(L.P, st, L.prof, s_ph);
+  const uint32_t S = gate_bits(L);
+  for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x)
+    if (!gate_item<VPT>(L, item, S, m, st)) break;
+  cta_end(L, st, s_ph);
+}
+
+// Many simulators in one launch: job j is one gate of one simulator, and its work
+// items are the global items [begin_j, begin_{j+1}).  All simulators share chunk_log2.
+template <int VPT>
+__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3)
+    k_gate_batch(const BatchJob* __restrict__ jobs, int njobs, unsigned long long total) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ long long s_ph[7];
+  __shared__ int s_oom;
+  __shared__ uint32_t s_np[2];
+  const GateSmem m = gate_smem(smem, jobs[0].L.P.kc, jobs[0].L.P.dir_words, s_ph, &s_oom, s_np);
+  GateCta st;
+  int cur = -1;
+  uint32_t S = 64;
+  for (unsigned long long g = blockIdx.x; g < total; g += gridDim.x) {
+    int lo = 0, hi = njobs - 1;  // last job whose first item is <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].begin <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    if (lo != cur) {
+      if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
+      cur = lo;
+      cta_begin(jobs[cur].L.P, st, jobs[cur].L.prof, s_ph);
+      S = gate_bits(jobs[cur].L);
+    }
+    gate_item<VPT>(jobs[cur].L, g - jobs[cur].begin, S, m, st);
+  }
+  if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
+}
+
 // After a gate: free pages back to the stack, then the controller bookkeeping.
-__global__ void __launch_bounds__(1024) k_post(const Pool P, const CtlParams cp, int grid_ctas) {
+// Called by one block of 1024 threads.
+__device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, int grid_ctas) {
   DevCtl* ctl = P.ctl;
   __shared__ unsigned long long s_top;
   if (threadIdx.x == 0) s_top = (unsigned long long)ctl->top;
@@ -259,6 +359,16 @@ __global__ void __launch_bounds__(1024) k_post(const Pool P, const CtlParams cp,
   }
 }
 
+__global__ void __launch_bounds__(1024) k_post(const Pool P, const CtlParams cp, int grid_ctas) {
+  post_body(P, cp, grid_ctas);
+}
+
+// One block per job of a batched launch.
+__global__ void __launch_bounds__(1024) k_post_batch(const BatchJob* __restrict__ jobs, int grid_ctas) {
+  const BatchJob& j = jobs[blockIdx.x];
+  post_body(j.L.P, j.L.ctl, grid_ctas);
+}
+
 // ------------------------------------------------------------ initialise -- //
 __global__ void k_pool_init(const Pool P, unsigned long long nchunks) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -288,7 +398,8 @@ __global__ void __launch_bounds__(kThreads) k_init_chunk0(const Pool P, unsigned
   __shared__ int s_ok;
   for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[tile_val(j)] = j == 0 ? 0x3FF0000000000000ull : 0ull;
   __syncthreads();
-  const uint32_t n0 = encode_block<VPT>(tile, kc, 64u, -1, img, imgcap(kc), s, &P.ctl->err);
+  int pp = 0;
+  const uint32_t n0 = encode_block<VPT>(tile, kc, 64u, -1, kDefaultModes, img, imgcap(kc), s, pp, &P.ctl->err);
   if (threadIdx.x == 0) {
     s_np = pages_for(n0, kc);
     CtaCache cc;
@@ -310,19 +421,20 @@ __global__ void __launch_bounds__(kThreads) k_init_chunk0(const Pool P, unsigned
 // -------------------------------------------------------- codec entries -- //
 template <int VPT>
 __global__ void __launch_bounds__(kThreads)
-    k_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force, uint8_t* out,
-                   unsigned long long stride, uint32_t* lens, unsigned int* err) {
+    k_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force, uint32_t modes,
+                   uint8_t* out, unsigned long long stride, uint32_t* lens, unsigned int* err) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t N = 2u << kc, cap = codedcap(kc);
   uint64_t* tile = reinterpret_cast<uint64_t*>(smem);
   uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  int pp = 0;
   for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in) + c * N;
     for (uint32_t j = threadIdx.x; j < N; j += kThreads) tile[tile_val(j)] = src[j];
     __syncthreads();
-    const uint32_t n = encode_block<VPT>(tile, kc, S, force, img, cap, s, err);
+    const uint32_t n = encode_block<VPT>(tile, kc, S, force, modes, img, cap, s, pp, err);
     uint4* dst = reinterpret_cast<uint4*>(out + c * stride);
     const uint4* sv = reinterpret_cast<const uint4*>(img);
     for (uint32_t u = threadIdx.x; u < n / 16u; u += kThreads) dst[u] = sv[u];
@@ -341,6 +453,7 @@ __global__ void __launch_bounds__(kThreads)
   uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  int pp = 0;
   for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const uint32_t len = lens[c];
     const bool fits = len <= cap && (len & 15u) == 0u && len >= 16u;
@@ -352,7 +465,7 @@ __global__ void __launch_bounds__(kThreads)
       reinterpret_cast<uint32_t*>(img)[0] = 0xffu;  // fails the header checks
     }
     __syncthreads();
-    const bool ok = decode_block<VPT>(img, fits ? len : 16u, kc, tile, s);
+    const bool ok = decode_block<VPT>(img, fits ? len : 16u, kc, tile, s, pp);
     if (!ok && threadIdx.x == 0) atomicOr(err, (unsigned)E_CORRUPT);
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(out) + c * N;
     for (uint32_t j = threadIdx.x; j < N; j += kThreads) dst[j] = tile[tile_val(j)];
@@ -372,6 +485,7 @@ __global__ void __launch_bounds__(kThreads)
   uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  int pp = 0;
   const unsigned long long cfirst = first_amp >> kc, clast = (first_amp + count - 1ull) >> kc;
   for (unsigned long long c = cfirst + blockIdx.x; c <= clast; c += gridDim.x) {
     const uint32_t* e = dir_entry(P, c);
@@ -381,7 +495,7 @@ __global__ void __launch_bounds__(kThreads)
       return;
     }
     load_image_block(P, c, img, pages, cap);
-    if (!decode_block<VPT>(img, b, kc, tile, s) && threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+    if (!decode_block<VPT>(img, b, kc, tile, s, pp) && threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
     const unsigned long long base = c << kc;
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(out);
     for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
@@ -407,6 +521,7 @@ __global__ void __launch_bounds__(kThreads)
   uint8_t* img = reinterpret_cast<uint8_t*>(tile + tile_words(kc));
   uint32_t* pages = reinterpret_cast<uint32_t*>(img + cap);
   ScanSmem& s = *reinterpret_cast<ScanSmem*>(pages + pagelist_words(kc));
+  int pp = 0;
   __shared__ double red[3][kThreads];
   for (unsigned long long cl = blockIdx.x; cl < nchunks; cl += gridDim.x) {
     const unsigned long long c = cfirst + cl;
@@ -417,7 +532,7 @@ __global__ void __launch_bounds__(kThreads)
       return;
     }
     load_image_block(P, c, img, pages, cap);
-    if (!decode_block<VPT>(img, b, kc, tile, s) && threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+    if (!decode_block<VPT>(img, b, kc, tile, s, pp) && threadIdx.x == 0) atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
     const double* v = reinterpret_cast<const double*>(tile);
     double x = 0.0, y = 0.0, z = 0.0;
     for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
@@ -559,6 +674,22 @@ cudaError_t launch_post(const Pool& P, const CtlParams& cp, int grid_ctas, cudaS
   return cudaGetLastError();
 }
 
+cudaError_t launch_gate_batch(const BatchJob* jobs, int njobs, unsigned long long total, int kc, int grid,
+                              cudaStream_t st) {
+  const size_t smem = gate_smem_bytes(kc);
+  QC_VPT_DISPATCH(kc, {
+    cudaError_t e = prep(k_gate_batch<V>, smem);
+    if (e != cudaSuccess) return e;
+    k_gate_batch<V><<<grid, kThreads, smem, st>>>(jobs, njobs, total);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_post_batch(const BatchJob* jobs, int njobs, int grid_ctas, cudaStream_t st) {
+  k_post_batch<<<njobs, 1024, 0, st>>>(jobs, grid_ctas);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pool_init(const Pool& P, unsigned long long nchunks, cudaStream_t st) {
   k_pool_init<<<num_sms() * 4, 256, 0, st>>>(P, nchunks);
   return cudaGetLastError();
@@ -577,12 +708,18 @@ cudaError_t launch_init_chunk0(const Pool& P, unsigned long long nchunks, cudaSt
 cudaError_t launch_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force,
                                 uint8_t* out, unsigned long long stride, uint32_t* lens, unsigned int* err,
                                 cudaStream_t st) {
+  return launch_codec_encode(in, nchunks, kc, S, force, kDefaultModes, out, stride, lens, err, st);
+}
+
+cudaError_t launch_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force,
+                                uint32_t modes, uint8_t* out, unsigned long long stride, uint32_t* lens,
+                                unsigned int* err, cudaStream_t st) {
   const size_t smem = codec_smem_bytes(kc);
   const unsigned long long g = nchunks < (unsigned long long)num_sms() * 8 ? nchunks : (unsigned long long)num_sms() * 8;
   QC_VPT_DISPATCH(kc, {
     cudaError_t e = prep(k_codec_encode<V>, smem);
     if (e != cudaSuccess) return e;
-    k_codec_encode<V><<<(unsigned)g, kThreads, smem, st>>>(in, nchunks, kc, S, force, out, stride, lens, err);
+    k_codec_encode<V><<<(unsigned)g, kThreads, smem, st>>>(in, nchunks, kc, S, force, modes, out, stride, lens, err);
   });
   return cudaGetLastError();
 }

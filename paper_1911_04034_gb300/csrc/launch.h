@@ -21,6 +21,14 @@ struct GateLaunch {
   int target;                    // target bit (in-chunk gates)
   int pair;                      // 1: target >= chunk_log2
   int prof;                      // 1: accumulate per-phase SM cycles
+  uint32_t modes;                // chunk modes the encoder may choose (bit m = mode m)
+};
+
+// One gate of one simulator inside a batched launch; its work items are the global
+// items [begin, begin + L.items).
+struct BatchJob {
+  GateLaunch L;
+  unsigned long long begin;
 };
 
 // Records the message sim_last_error() returns on the calling thread.
@@ -33,11 +41,17 @@ int gate_ctas_per_sm(int kc);
 
 cudaError_t launch_gate(const GateLaunch& L, int grid, cudaStream_t st);
 cudaError_t launch_post(const Pool& P, const CtlParams& cp, int grid_ctas, cudaStream_t st);
+cudaError_t launch_gate_batch(const BatchJob* jobs, int njobs, unsigned long long total, int kc, int grid,
+                              cudaStream_t st);
+cudaError_t launch_post_batch(const BatchJob* jobs, int njobs, int grid_ctas, cudaStream_t st);
 cudaError_t launch_pool_init(const Pool& P, unsigned long long nchunks, cudaStream_t st);
 cudaError_t launch_init_chunk0(const Pool& P, unsigned long long nchunks, cudaStream_t st);
 cudaError_t launch_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force,
                                 uint8_t* out, unsigned long long stride, uint32_t* lens, unsigned int* err,
                                 cudaStream_t st);
+cudaError_t launch_codec_encode(const double* in, unsigned long long nchunks, int kc, uint32_t S, int force,
+                                uint32_t modes, uint8_t* out, unsigned long long stride, uint32_t* lens,
+                                unsigned int* err, cudaStream_t st);
 cudaError_t launch_codec_decode(const uint8_t* in, unsigned long long stride, const uint32_t* lens,
                                 unsigned long long nchunks, int kc, double* out, unsigned int* err, cudaStream_t st);
 cudaError_t launch_decode_range(const Pool& P, unsigned long long first_amp, unsigned long long count, double* out,

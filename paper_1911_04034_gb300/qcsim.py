@@ -78,7 +78,11 @@ def lib():
             "sim_layout": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.POINTER(C.c_int)],
             "sim_codec_encode": [vp, u64, i32, dbl, i32, vp, u64, vp, i32],
             "sim_codec_decode": [vp, u64, vp, u64, i32, vp, i32],
+            "sim_codec_encode_ex": [vp, u64, i32, dbl, i32, C.c_uint32, vp, u64, vp, i32],
+            "sim_set_modes": [vp, C.c_uint32],
             "sim_codec_encode_noalloc": [vp, u64, i32, dbl, i32, vp, u64, vp],
+            "sim_batch_apply": [vp, i32, vp, vp, i32],
+            "sim_autotune_chunk": [i32, i32, dbl, vp, sz, vp, i32, C.POINTER(C.c_int), vp],
             "sim_set_timing": [vp, i32],
             "sim_timing": [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                            C.POINTER(C.c_uint64)],
@@ -178,6 +182,10 @@ class Sim:
         g = gates_array(gates)
         _check(lib().sim_apply_circuit(self._h, C.c_void_p(_ptr(g)), g.shape[0]), "sim_apply_circuit")
 
+    def set_modes(self, modes: int) -> None:
+        """0x1F: Solution C modes (default); 0x3F adds SPLIT (Solution D)."""
+        _check(lib().sim_set_modes(self._h, int(modes)), "sim_set_modes")
+
     def sync(self) -> None:
         _check(lib().sim_sync(self._h), "sim_sync")
 
@@ -234,12 +242,35 @@ class Sim:
         return buf[: ln.value].tobytes()
 
 
+def batch_apply(sims: list, circuits: list, use_graph: bool = True) -> None:
+    """Runs circuits[k] on sims[k] for all k in shared launches (sim_batch_apply)."""
+    arrs = [gates_array(c) for c in circuits]
+    n = len(sims)
+    handles = (C.c_void_p * n)(*[s._h.value for s in sims])
+    ptrs = (C.c_void_p * n)(*[_ptr(a) if a.size else 0 for a in arrs])
+    counts = (C.c_size_t * n)(*[a.shape[0] for a in arrs])
+    _check(lib().sim_batch_apply(C.cast(handles, C.c_void_p), n, C.cast(ptrs, C.c_void_p), C.cast(counts, C.c_void_p),
+                                 int(bool(use_graph))), "sim_batch_apply")
+
+
+def autotune_chunk(n_qubits: int, block_log2: int, err_bound: float, probe, candidates=(8, 9, 10, 11)):
+    """Returns (best chunk_log2, {candidate: amplitude updates/s of kernel time})."""
+    g = gates_array(probe)
+    cand = (C.c_int * len(candidates))(*candidates)
+    rates = np.zeros(len(candidates))
+    best = C.c_int()
+    _check(lib().sim_autotune_chunk(n_qubits, block_log2, float(err_bound), C.c_void_p(_ptr(g)), g.shape[0],
+                                    C.cast(cand, C.c_void_p), len(candidates), C.byref(best), C.c_void_p(_ptr(rates))),
+           "sim_autotune_chunk")
+    return int(best.value), dict(zip(candidates, rates.tolist()))
+
+
 def codec_stride(chunk_log2: int) -> int:
     need = 16 + (16 << chunk_log2) + (1 << chunk_log2) // 2 + 32
     return (need + 15) // 16 * 16
 
 
-def codec_encode(values, chunk_log2: int, eps: float, force_mode: int = -1):
+def codec_encode(values, chunk_log2: int, eps: float, force_mode: int = -1, modes: int = 0x1F):
     """Encodes chunks with the device encoder.  values: numpy complex128 of
     n_chunks * 2^chunk_log2 amplitudes (host) or a torch CUDA float64 tensor.
     Returns (images as a list of bytes, lengths) for host input; for device input
@@ -251,16 +282,16 @@ def codec_encode(values, chunk_log2: int, eps: float, force_mode: int = -1):
         n = values.numel() // (2 << chunk_log2)
         out = torch.zeros(n * stride, dtype=torch.uint8, device=values.device)
         lens = torch.zeros(n, dtype=torch.int32, device=values.device)
-        _check(lib().sim_codec_encode(C.c_void_p(_ptr(values)), n, chunk_log2, float(eps), force_mode,
-                                      C.c_void_p(_ptr(out)), stride, C.c_void_p(_ptr(lens)), 1), "sim_codec_encode")
+        _check(lib().sim_codec_encode_ex(C.c_void_p(_ptr(values)), n, chunk_log2, float(eps), force_mode, modes,
+                                         C.c_void_p(_ptr(out)), stride, C.c_void_p(_ptr(lens)), 1), "sim_codec_encode")
         return out, lens, stride
     x = np.ascontiguousarray(values, dtype=np.complex128)
     n = x.size >> chunk_log2
     assert n << chunk_log2 == x.size
     out = np.zeros(n * stride, dtype=np.uint8)
     lens = np.zeros(n, dtype=np.uint32)
-    _check(lib().sim_codec_encode(C.c_void_p(_ptr(x)), n, chunk_log2, float(eps), force_mode, C.c_void_p(_ptr(out)),
-                                  stride, C.c_void_p(_ptr(lens)), 0), "sim_codec_encode")
+    _check(lib().sim_codec_encode_ex(C.c_void_p(_ptr(x)), n, chunk_log2, float(eps), force_mode, modes,
+                                     C.c_void_p(_ptr(out)), stride, C.c_void_p(_ptr(lens)), 0), "sim_codec_encode")
     return [out[k * stride: k * stride + int(lens[k])].tobytes() for k in range(n)], lens
 
 

@@ -52,16 +52,17 @@ def chunk_families(rng, kc, count):
     return out
 
 
+@pytest.mark.parametrize("modes", [0x1F, 0x3F])
 @pytest.mark.parametrize("kc", [0, 1, 2, 3, 5, 7, 8, 9, 10, 11])
-def test_encode_bytes_match_oracle(kc):
+def test_encode_bytes_match_oracle(kc, modes):
     rng = np.random.default_rng(1000 + kc)
     chunks = chunk_families(rng, kc, 40)
     x = np.concatenate(chunks)
     for eps in EPS:
         S = O.sig_bits(eps)
-        imgs, lens = qc().codec_encode(x, kc, eps)
+        imgs, lens = qc().codec_encode(x, kc, eps, modes=modes)
         for k, a in enumerate(chunks):
-            ref = O.encode_chunk(a, kc, S)
+            ref = O.encode_chunk(a, kc, S, modes=modes)
             assert imgs[k] == ref, (kc, eps, k, imgs[k][:16].hex(), ref[:16].hex())
 
 
@@ -71,7 +72,7 @@ def test_forced_modes_match_oracle(kc):
     chunks = chunk_families(rng, kc, 20)
     for eps in (0.0, 1e-4):
         S = O.sig_bits(eps)
-        for m in range(5):
+        for m in range(6):
             for a in chunks:
                 try:
                     ref = O.encode_chunk(a, kc, S, force_mode=m)
@@ -89,7 +90,7 @@ def test_decode_matches_oracle(kc):
     chunks = chunk_families(rng, kc, 30)
     for eps in EPS:
         S = O.sig_bits(eps)
-        imgs = [O.encode_chunk(a, kc, S) for a in chunks]
+        imgs = [O.encode_chunk(a, kc, S) for a in chunks] + [O.encode_chunk(a, kc, S, force_mode=5) for a in chunks]
         got = qc().codec_decode(imgs, kc)
         want = np.concatenate([O.decode_chunk(b, kc) for b in imgs])
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64))

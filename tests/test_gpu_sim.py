@@ -39,7 +39,7 @@ def stats_match(gs, os_):
     assert gs["level"] == os_["level"]
     assert gs["fidelity_lb_sum"] == pytest.approx(os_["fid_lb_sum"], abs=1e-12)
     assert gs["fidelity_lb_prod"] == pytest.approx(os_["fid_lb_prod"], rel=1e-12)
-    assert gs["chunks_by_mode"][:5] == os_["chunks_by_mode"][:5]
+    assert gs["chunks_by_mode"][:6] == os_["chunks_by_mode"][:6]
 
 
 def test_grover_12q_every_gate_bit_exact():
@@ -97,6 +97,22 @@ def test_qaoa_and_qft_bit_exact(ladder):
         gpu = qc().Sim(n, 7, eps, chunk_log2=6, budget=budget, ladder=ladder, pool_bytes=2 * (16 << n) + (64 << 20))
         gpu.apply_circuit(gates)
         orc.apply(gates)
+        assert images_equal(gpu, orc) == []
+        stats_match(gpu.stats(), orc.stats())
+
+
+def test_solution_d_mode_bit_exact():
+    """SPLIT (Solution D) enabled on both sides: real-valued Grover states favour it."""
+    n = 11
+    gates, _ = Cc.grover(n, 6, seed=3)
+    rc = Cc.rcs(1, 11, 4, seed=2)
+    for circ, eps in ((gates, 1e-4), (rc, 1e-3)):
+        budget = (16 << n) // 5
+        orc = O.CSim(n, 8, 7, eps, budget, modes=0x3F)
+        gpu = qc().Sim(n, 8, eps, chunk_log2=7, budget=budget, pool_bytes=64 << 20)
+        gpu.set_modes(0x3F)
+        gpu.apply_circuit(circ)
+        orc.apply(circ)
         assert images_equal(gpu, orc) == []
         stats_match(gpu.stats(), orc.stats())
 

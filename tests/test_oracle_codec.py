@@ -130,8 +130,9 @@ def _expected_image(case) -> bytes:
     head = bytes([h["mode"], h["S"], h["log2P"], 0]) + h["payload_bytes"].to_bytes(4, "little") + \
         h["n_values"].to_bytes(4, "little") + h["resid_bits"].to_bytes(4, "little")
     payload = b""
-    if "codes_byte_bits" in case:
-        codes = bytes([int(case["codes_byte_bits"], 2)]).ljust(16, b"\0")
+    if "codes_byte_bits" in case or "codes_bytes_bits" in case:
+        cb = case.get("codes_bytes_bits", [case.get("codes_byte_bits")])
+        codes = bytes([int(b, 2) for b in cb]).ljust(16, b"\0")
         bits = "".join(case["residual_bits"])
         nwords = (len(bits) + 127) // 128 * 2
         bits = bits.ljust(64 * nwords, "0")
@@ -146,7 +147,7 @@ def _expected_image(case) -> bytes:
 @pytest.mark.parametrize("case", json.load(open(GOLDEN))["cases"], ids=lambda c: c["name"])
 def test_hand_derived_image(case):
     vals = np.array([int(v, 16) for v in case["values_hex"]], dtype=np.uint64)
-    img = O.encode_chunk(vals, case["kc"], case["S"])
+    img = O.encode_chunk(vals, case["kc"], case["S"], modes=case.get("modes", O.DEFAULT_MODES))
     assert img[0] == case["expect_mode"]
     assert img == _expected_image(case)
     dec = O.decode_chunk(img, case["kc"]).view(np.uint64)
@@ -181,13 +182,14 @@ def test_roundtrip(kc):
         bits = np.ascontiguousarray(a, dtype=np.complex128).view(np.uint64)
         has_sub = np.any(((bits >> np.uint64(52)) & np.uint64(0x7FF) == 0) & (bits & np.uint64((1 << 52) - 1) != 0))
         for S in (64, 29, 26, 22, 19, 16):
-            img = O.encode_chunk(a, kc, S)
+          for force in (-1, 5):
+            img = O.encode_chunk(a, kc, S, force_mode=force)
             assert len(img) % 16 == 0
             eff = 64 if has_sub else S
             if img[0] != 0:
                 assert img[1] == eff, (name, S)
             dec = O.decode_chunk(img, kc).view(np.uint64)
-            assert np.array_equal(dec, np_truncate(bits, eff)), (name, kc, S)
+            assert np.array_equal(dec, np_truncate(bits, eff)), (name, kc, S, force)
 
 
 def _smallest_period(t: np.ndarray, kc: int):
@@ -200,7 +202,8 @@ def _smallest_period(t: np.ndarray, kc: int):
 
 
 @pytest.mark.parametrize("kc", [1, 2, 4, 6])
-def test_selector_is_minimal_and_modes_apply(kc):
+@pytest.mark.parametrize("modes", [O.DEFAULT_MODES, 0x3F])
+def test_selector_is_minimal_and_modes_apply(kc, modes):
     rng = np.random.default_rng(kc)
     for name, a in _chunks(rng, kc):
         for S in (64, 26, 16):
@@ -212,15 +215,18 @@ def test_selector_is_minimal_and_modes_apply(kc):
                 2: _smallest_period(t, kc) is not None,
                 3: True,
                 4: True,
+                5: True,
             }
             sizes = {}
-            for m in range(5):
+            for m in range(6):
+                if not (modes >> m) & 1:
+                    continue
                 if applicable[m]:
                     sizes[m] = len(O.encode_chunk(a, kc, S, force_mode=m))
                 else:
                     with pytest.raises(O.OracleError):
                         O.encode_chunk(a, kc, S, force_mode=m)
-            auto = O.encode_chunk(a, kc, S)
+            auto = O.encode_chunk(a, kc, S, modes=modes)
             best = min(sizes.values())
             assert len(auto) == best
             assert auto[0] == min(m for m, s in sizes.items() if s == best)

@@ -1,0 +1,81 @@
+"""Pins of the selector network's oracle (oracle/mlp.py): bfloat16 rounding against
+torch's conversion, the float32 fixed-order forward against a float64 forward,
+backward against central finite differences of the loss, and a hand-computed path."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+
+def test_bf16_rounding_matches_torch_and_hand_values():
+    torch = pytest.importorskip("torch")
+    # hand values: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> even (1.0);
+    # 1 + 3 * 2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6 -> even (1 + 2^-6)
+    assert M.bf16_round(np.float32(1 + 2.0 ** -8)) == np.float32(1.0)
+    assert M.bf16_round(np.float32(1 + 3 * 2.0 ** -8)) == np.float32(1 + 2.0 ** -6)
+    x = np.random.default_rng(1).standard_normal(10000).astype(np.float32) * 7
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(M.bf16_round(x), want)
+
+
+def test_forward32_close_to_float64_forward():
+    p = M.init_params(3)
+    x = np.random.default_rng(2).standard_normal((64, M.N_IN)).astype(np.float32)
+    out32 = M.forward32(p, x)
+    h1 = np.maximum(x.astype(np.float64) @ p["W1"].T.astype(np.float64) + p["b1"], 0)
+    h2 = np.maximum(h1 @ p["W2"].T.astype(np.float64) + p["b2"], 0)
+    out64 = h2 @ p["W3"].T.astype(np.float64) + p["b3"]
+    assert np.max(np.abs(out32 - out64)) <= 1e-4 * max(1.0, np.max(np.abs(out64)))
+
+
+def test_hand_computed_path():
+    p = {k: np.zeros(M.SHAPES[k], dtype=np.float32) for k in M.ORDER}
+    p["W1"][0, 3] = 2.0   # h1[0] = relu(2 x3 - 1)
+    p["b1"][0] = -1.0
+    p["W2"][5, 0] = 0.5   # h2[5] = relu(0.5 h1[0])
+    p["W3"][7, 5] = -4.0  # out[7] = -4 h2[5] + 0.25
+    p["b3"][7] = 0.25
+    x = np.zeros((2, M.N_IN), dtype=np.float32)
+    x[0, 3] = 3.0         # h1 = 5, h2 = 2.5, out7 = -9.75
+    x[1, 3] = 0.25        # h1 = relu(-0.5) = 0 -> out7 = 0.25
+    out = M.forward32(p, x)
+    assert out[0, 7] == np.float32(-9.75) and out[1, 7] == np.float32(0.25)
+    assert np.all(out[:, :7] == 0)
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    p = {k: v.astype(np.float64) for k, v in M.init_params(5).items()}
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.standard_normal(M.SHAPES[k]) * 0.1
+    x = rng.standard_normal((32, M.N_IN))
+    mode = rng.integers(0, M.N_MODES, size=32)
+    sizes = rng.random((32, 2))
+    _, g = M.loss_and_grads(p, x, mode, sizes)
+    h = 1e-6
+    for k in M.ORDER:
+        flat = p[k].ravel()
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = M.loss_only(p, x, mode, sizes)
+            flat[idx] = old - h
+            lm = M.loss_only(p, x, mode, sizes)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k].ravel()[idx]) <= 1e-6 + 1e-5 * abs(fd), (k, idx)
+
+
+def test_plain_gradient_descent_reduces_the_loss():
+    rng = np.random.default_rng(6)
+    p = {k: v.astype(np.float64) for k, v in M.init_params(7).items()}
+    x = rng.standard_normal((256, M.N_IN))
+    mode = np.where(x[:, 0] > 0, 5, 3)  # a separable rule
+    sizes = np.stack([0.4 + 0.1 * np.tanh(x[:, 1]), 0.3 + 0.1 * np.tanh(x[:, 2])], axis=1)
+    l0, _ = M.loss_and_grads(p, x, mode, sizes)
+    for _ in range(300):
+        _, g = M.loss_and_grads(p, x, mode, sizes)
+        for k in M.ORDER:
+            p[k] -= 0.05 * g[k]
+    l1, _ = M.loss_and_grads(p, x, mode, sizes)
+    assert l1 < 0.5 * l0

@@ -30,7 +30,7 @@ def golden_pin() -> bool:
     for case in json.load(open(GOLDEN))["cases"]:
         vals = np.array([int(v, 16) for v in case["values_hex"]], dtype=np.uint64)
         try:
-            if O.encode_chunk(vals, case["kc"], case["S"]) != _expected_image(case):
+            if O.encode_chunk(vals, case["kc"], case["S"], modes=case.get("modes", O.DEFAULT_MODES)) != _expected_image(case):
                 return False
         except O.OracleError:
             return False
