@@ -91,6 +91,7 @@ typedef struct sim_stats_t {
   int32_t chunk_log2, block_log2;
   uint64_t phase_cycles[6];   /* with sim_set_timing(sim, 2): SM cycles of the fused kernel's CTAs in
                                  stage / decode / apply / encode / commit / constant fast paths */
+  uint64_t split_trials;      /* chunk encodes that ran the Solution D trial */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
@@ -153,6 +154,36 @@ sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, co
  * SPLIT, Solution D (the real parts, then the imaginary parts, XOR-coded).  The set
  * must contain 0x1F. */
 sim_status sim_set_modes(sim_t* sim, uint32_t modes);
+
+/* Learned selector (not from the paper).  selector 0: Solution C modes only (the
+ * default); 1: Solution C and D, every chunk trying both orders (exhaustive);
+ * 2: Solution C and D, a chunk trying the Solution D order only where a
+ * 16 -> 32 -> 32 -> 8 network with bfloat16 weights (1864 values, W1[32][16] b1 W2[32][32]
+ * b2 W3[8][32] b3, host pointer) predicts that SPLIT wins.  The network reads the chunk's
+ * previous image header and the gate (see the selector section of device.cuh); its
+ * float32 inference has a fixed order, so its decisions are reproducible.  The bound
+ * is enforced by the codec whatever the network says. */
+sim_status sim_set_selector(sim_t* sim, int selector, const uint16_t* bf16_params);
+
+/* Selector training records: with capacity > 0, every chunk encode that tries both
+ * orders appends 20 floats (16 network inputs, the chosen mode, STREAM and SPLIT image
+ * sizes as fractions of RAW, 0) until capacity records exist; 0 stops and frees. */
+sim_status sim_trace(sim_t* sim, uint64_t capacity);
+sim_status sim_trace_read(sim_t* sim, float* out, uint64_t cap_records, uint64_t* n_records);
+
+/* Selector training on the GPU with the library's own kernels: n samples of 16 inputs
+ * (x), the exhaustive mode (0..5) and the two size fractions; float32 master weights
+ * (params, 1864 values, in: initial, out: trained) rounded to bfloat16 for every
+ * forward and backward pass; Adam (beta 0.9, 0.999), minibatches from a seeded
+ * shuffle.  bf16_out (may be NULL) receives the trained bfloat16 weights, last_loss
+ * the mean loss of the last epoch. */
+sim_status sim_mlp_train(const float* x, const int32_t* mode, const float* sizes, uint64_t n, int epochs, int batch,
+                         float lr, uint64_t seed, float* params, uint16_t* bf16_out, float* last_loss);
+
+/* Loss and its gradient over n samples at the bfloat16 rounding of params (float32
+ * arithmetic), for checking the training kernels. */
+sim_status sim_mlp_grad(const float* params, const float* x, const int32_t* mode, const float* sizes, uint64_t n,
+                        float* grad_out, float* loss_out);
 
 /* Waits for queued work and returns the device error state. */
 sim_status sim_sync(sim_t* sim);

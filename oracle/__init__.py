@@ -98,6 +98,11 @@ def lib():
             "orc_encode_chunk": (C.c_long, [u64p, C.c_int, C.c_int, C.c_int, u8p, C.c_size_t]),
             "orc_encode_chunk_mask": (C.c_long, [u64p, C.c_int, C.c_int, C.c_int, C.c_uint, u8p, C.c_size_t]),
             "orc_csim_set_modes": (C.c_int, [C.c_void_p, C.c_uint]),
+            "orc_csim_set_mlp": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),
+            "orc_mlp_forward": (None, [C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+            "orc_mlp_wants_split": (C.c_int, [C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+            "orc_mlp_features": (None, [u8p, C.c_size_t, C.c_int, C.POINTER(_Gate), C.c_int, C.POINTER(C.c_uint64),
+                                     C.POINTER(C.c_float)]),
             "orc_decode_chunk": (C.c_int, [u8p, C.c_size_t, C.c_int, u64p]),
             "orc_gate_check": (C.c_int, [C.POINTER(_Gate), C.c_int]),
             "orc_sv_init": (None, [dp, C.c_int]),
@@ -247,6 +252,34 @@ def fidelity(ideal: np.ndarray, sim: np.ndarray, n: int) -> float:
     return abs(sv_inner(ideal, sim, n))
 
 
+def mlp_forward_c(params_flat, x) -> np.ndarray:
+    """The C oracle's selector inference on one feature row."""
+    v = np.ascontiguousarray(params_flat, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(8, dtype=np.float32)
+    lib().orc_mlp_forward(_ptr(v, C.c_float), _ptr(xx, C.c_float), _ptr(out, C.c_float))
+    return out
+
+
+def mlp_wants_split_c(params_flat, x) -> bool:
+    """The C oracle's selector decision on one feature row."""
+    v = np.ascontiguousarray(params_flat, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    return bool(lib().orc_mlp_wants_split(_ptr(v, C.c_float), _ptr(xx, C.c_float)))
+
+
+def mlp_features_c(img: bytes, kc: int, gate_rec, S_gate: int, values) -> np.ndarray:
+    """The C oracle's selector inputs for a chunk with image img whose values after
+    the gate are `values` (2^kc complex128)."""
+    buf = np.frombuffer(bytes(img), dtype=np.uint8).copy()
+    x = _as_bits(values)
+    assert x.size == 2 << kc
+    out = np.zeros(16, dtype=np.float32)
+    lib().orc_mlp_features(_ptr(buf, C.c_uint8), buf.size, kc, _gates(gate_rec), S_gate, _ptr(x, C.c_uint64),
+                           _ptr(out, C.c_float))
+    return out
+
+
 def splitmix64(x: int) -> int:
     return int(lib().orc_splitmix64(C.c_uint64(int(x) & (2**64 - 1))))
 
@@ -305,6 +338,13 @@ class CSim:
         if rc:
             raise OracleError(rc, "csim_amplitudes")
         return out
+
+    def set_mlp(self, params_flat) -> None:
+        """Solution D is tried for a chunk only where the selector network says so;
+        params_flat: the network's 1864 parameters (bfloat16 values) in W1 b1 W2 b2 W3 b3 order."""
+        v = np.ascontiguousarray(params_flat, dtype=np.float32)
+        assert v.size == 1864
+        lib().orc_csim_set_mlp(self._h, 1, _ptr(v, C.c_float))
 
     def image(self, c: int) -> bytes:
         cap = 16 + 16 * (1 << self.kc)

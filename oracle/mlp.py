@@ -75,16 +75,24 @@ def _layer32(W, b, x):
 def forward32(p: dict, x) -> np.ndarray:
     """Outputs (float32) for feature rows x (float32), in the order that fixes decisions."""
     x = np.asarray(x, dtype=np.float32)
-    h1 = np.maximum(_layer32(p["W1"], p["b1"], x), np.float32(0))
-    h2 = np.maximum(_layer32(p["W2"], p["b2"], h1), np.float32(0))
+    z1 = _layer32(p["W1"], p["b1"], x)
+    h1 = np.where(z1 > 0, z1, np.float32(0)).astype(np.float32)  # ReLU giving +0
+    z2 = _layer32(p["W2"], p["b2"], h1)
+    h2 = np.where(z2 > 0, z2, np.float32(0)).astype(np.float32)
     return _layer32(p["W3"], p["b3"], h2)
 
 
+SPLIT_MARGIN = np.float32(2.0)
+
+
 def wants_split(p: dict, x) -> np.ndarray:
-    """The selector's decision: run the Solution D trial iff the largest mode logit is
-    SPLIT's (lowest index wins a tie)."""
+    """The selector's decision: run the Solution D trial iff the SPLIT logit plus a
+    margin of 2 reaches the largest mode logit (float32 sum and comparison).  The
+    margin leans towards a trial: a missed SPLIT costs memory, a needless trial only
+    time."""
     out = forward32(p, x)
-    return np.argmax(out[:, :N_MODES], axis=1) == 5
+    lifted = (out[:, 5] + SPLIT_MARGIN).astype(np.float32)
+    return lifted >= out[:, :N_MODES].max(axis=1)
 
 
 def loss_and_grads(p: dict, x, mode, sizes, w_size: float = 1.0):
@@ -128,3 +136,42 @@ def loss_and_grads(p: dict, x, mode, sizes, w_size: float = 1.0):
 
 def loss_only(p: dict, x, mode, sizes, w_size: float = 1.0) -> float:
     return loss_and_grads(p, x, mode, sizes, w_size)[0]
+
+
+def zero_groups(values, kc: int) -> tuple[int, int, int]:
+    """Splits the chunk's 2^kc amplitudes into G = min(2^kc, 256) equal groups and
+    counts the groups whose real parts, and those whose imaginary parts, are all zero
+    (+0 or -0).  Returns (real-zero groups, imaginary-zero groups, G)."""
+    v = np.ascontiguousarray(values, dtype=np.complex128)
+    A = 1 << kc
+    G = min(A, 256)
+    re = v.real.reshape(G, A // G)
+    im = v.imag.reshape(G, A // G)
+    return int(np.sum(np.all(re == 0, axis=1))), int(np.sum(np.all(im == 0, axis=1))), G
+
+
+def features(prev_image: bytes, kc: int, u, target: int, S_gate: int, values) -> np.ndarray:
+    """The selector's 16 inputs for one chunk about to be re-encoded (float32):
+    one-hot of the previous image's mode (6), its size / RAW size, its S / 64, its
+    residual bits / (64 N), whether the gate matrix is real, diagonal, a permutation,
+    whether the target lies inside the chunk, the fraction of amplitude groups whose
+    real parts are all zero, the gate's S / 64, and the fraction of groups whose
+    imaginary parts are all zero.  `values` are the chunk's amplitudes after the gate."""
+    f32 = np.float32
+    mode, S = prev_image[0], prev_image[1]
+    bits = int.from_bytes(prev_image[12:16], "little")
+    zre, zim, G = zero_groups(values, kc)
+    x = np.zeros(16, dtype=np.float32)
+    x[mode] = 1
+    x[6] = f32(len(prev_image)) / f32(16 + (16 << kc))
+    x[7] = f32(S) / f32(64)
+    x[8] = f32(bits) / f32(64 * (2 << kc))
+    u = [float(v) for v in u]
+    x[9] = float(u[1] == 0 and u[3] == 0 and u[5] == 0 and u[7] == 0)
+    x[10] = float(u[2] == 0 and u[3] == 0 and u[4] == 0 and u[5] == 0)
+    x[11] = float(u[0] == 0 and u[1] == 0 and u[6] == 0 and u[7] == 0)
+    x[12] = float(target < kc)
+    x[13] = f32(zre) / f32(G)
+    x[14] = f32(S_gate) / f32(64)
+    x[15] = f32(zim) / f32(G)
+    return x

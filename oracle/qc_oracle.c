@@ -591,6 +591,93 @@ int orc_sv_measure(const double* psi, int n, uint64_t seed, uint64_t* outcome, d
 }
 
 /* ------------------------------------------------------------------------- */
+/* 9. Learned selector (not from the paper): when to try Solution D          */
+/* ------------------------------------------------------------------------- */
+/* 16 -> 32 (ReLU) -> 32 (ReLU) -> 8, parameters W1[32][16] b1[32] W2[32][32] b2[32]
+ * W3[8][32] b3[8] (bfloat16 values held as float).  float32, every unit summing its
+ * products over its inputs in index order, one rounding per product and per sum. */
+#define ORC_MLP_NPARAMS 1864
+
+static float mlp_unit(const float* w, const float* x, int n, float b) {
+  float acc = 0.0f;
+  for (int i = 0; i < n; ++i) {
+    float prod = w[i] * x[i];
+    acc = acc + prod;
+  }
+  return acc + b;
+}
+
+void orc_mlp_forward(const float* prm, const float* x, float* out) {
+  const float *W1 = prm, *b1 = W1 + 512, *W2 = b1 + 32, *b2 = W2 + 1024, *W3 = b2 + 32, *b3 = W3 + 256;
+  float h1[32], h2[32];
+  for (int j = 0; j < 32; ++j) {
+    float z = mlp_unit(W1 + 16 * j, x, 16, b1[j]);
+    h1[j] = z > 0.0f ? z : 0.0f;
+  }
+  for (int j = 0; j < 32; ++j) {
+    float z = mlp_unit(W2 + 32 * j, h1, 32, b2[j]);
+    h2[j] = z > 0.0f ? z : 0.0f;
+  }
+  for (int j = 0; j < 8; ++j) out[j] = mlp_unit(W3 + 32 * j, h2, 32, b3[j]);
+}
+
+/* Decision: try Solution D iff the SPLIT logit, plus a margin of 2, reaches the largest
+ * of the six mode logits (float32 sum and comparison).  The margin makes the rule
+ * lean towards a trial: a missed SPLIT costs memory, a needless trial only time. */
+int orc_mlp_wants_split(const float* prm, const float* x) {
+  float out[8];
+  orc_mlp_forward(prm, x, out);
+  float mx = out[0];
+  for (int m = 1; m < 6; ++m)
+    if (out[m] > mx) mx = out[m];
+  float lifted = out[5] + 2.0f;
+  return lifted >= mx;
+}
+
+/* Counts, over the chunk's amplitudes split into G = min(2^kc, 256) equal groups, the
+ * groups whose real parts (*zre) and whose imaginary parts (*zim) are all zero (+0 or
+ * -0); vals = the chunk's 2^(kc+1) words as the gate left them. */
+static void zero_groups(const uint64_t* vals, int kc, uint32_t* zre, uint32_t* zim, uint32_t* G) {
+  const uint64_t A = (uint64_t)1 << kc;
+  const uint64_t ng = A < 256 ? A : 256, gs = A / ng;
+  uint32_t cr = 0, ci = 0;
+  for (uint64_t k = 0; k < ng; ++k) {
+    int re_nz = 0, im_nz = 0;
+    for (uint64_t a = k * gs; a < (k + 1) * gs; ++a) {
+      re_nz |= (vals[2 * a] << 1) != 0;
+      im_nz |= (vals[2 * a + 1] << 1) != 0;
+    }
+    cr += !re_nz;
+    ci += !im_nz;
+  }
+  *zre = cr;
+  *zim = ci;
+  *G = (uint32_t)ng;
+}
+
+/* The selector's inputs for a chunk whose current image is img (length len) and whose
+ * values after the gate are vals. */
+void orc_mlp_features(const uint8_t* img, size_t len, int kc, const orc_gate* g, int S_gate, const uint64_t* vals,
+                      float* x) {
+  uint32_t bits = (uint32_t)img[12] | ((uint32_t)img[13] << 8) | ((uint32_t)img[14] << 16) | ((uint32_t)img[15] << 24);
+  const double* u = g->u;
+  uint32_t zre, zim, G;
+  zero_groups(vals, kc, &zre, &zim, &G);
+  for (int m = 0; m < 16; ++m) x[m] = 0.0f;
+  if (img[0] < 6) x[img[0]] = 1.0f;
+  x[6] = (float)len / (float)(16 + (16 << kc));
+  x[7] = (float)img[1] / 64.0f;
+  x[8] = (float)bits / (float)(64 * (2 << kc));
+  x[9] = (u[1] == 0 && u[3] == 0 && u[5] == 0 && u[7] == 0) ? 1.0f : 0.0f;
+  x[10] = (u[2] == 0 && u[3] == 0 && u[4] == 0 && u[5] == 0) ? 1.0f : 0.0f;
+  x[11] = (u[0] == 0 && u[1] == 0 && u[6] == 0 && u[7] == 0) ? 1.0f : 0.0f;
+  x[12] = g->target < kc ? 1.0f : 0.0f;
+  x[13] = (float)zre / (float)G;
+  x[14] = (float)S_gate / 64.0f;
+  x[15] = (float)zim / (float)G;
+}
+
+/* ------------------------------------------------------------------------- */
 /* 6. Compressed simulator                                                    */
 /* ------------------------------------------------------------------------- */
 
@@ -604,6 +691,8 @@ typedef struct {
 typedef struct {
   int n, b, kc, ladder, S_cur, level, nlevels;
   unsigned modes;
+  int use_mlp;                    /* 1: Solution D tried only where the selector says so */
+  float mlp[ORC_MLP_NPARAMS];
   double levels[8];
   double eps_max, tau;
   uint64_t budget, thresh, inflight, nchunks, E, Emax, gates;
@@ -616,10 +705,10 @@ typedef struct {
 
 void orc_csim_destroy(orc_csim* s);
 
-static int csim_store(orc_csim* s, uint64_t c, const uint64_t* vals) {
+static int csim_store(orc_csim* s, uint64_t c, const uint64_t* vals, unsigned mask) {
   size_t cap = 16 + 8 * ((size_t)2 << s->kc);
   uint8_t* buf = (uint8_t*)malloc(cap);
-  long L = orc_encode_chunk_mask(vals, s->kc, s->S_cur, -1, s->modes, buf, cap);
+  long L = orc_encode_chunk_mask(vals, s->kc, s->S_cur, -1, mask, buf, cap);
   if (L < 0) { free(buf); return (int)L; }
   uint8_t* fit = (uint8_t*)realloc(buf, (size_t)L);
   if (fit) buf = fit;
@@ -669,7 +758,7 @@ orc_csim* orc_csim_create(int n, int block_log2, int chunk_log2, double eps_max,
   for (uint64_t c = 0; c < s->nchunks; ++c) {
     memset(vals, 0, N * 8);
     if (c == 0) { double one = 1.0; memcpy(&vals[0], &one, 8); }
-    if (csim_store(s, c, vals)) { free(vals); orc_csim_destroy(s); return NULL; }
+    if (csim_store(s, c, vals, ORC_DEFAULT_MODES)) { free(vals); orc_csim_destroy(s); return NULL; }
   }
   free(vals);
   s->Emax = s->E;
@@ -710,6 +799,8 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
   uint64_t lo_mask = g->ctrl_mask & (A - 1), lo_vals = g->ctrl_vals & (A - 1);
   uint64_t* x0 = (uint64_t*)malloc(N * 8);
   uint64_t* x1 = (uint64_t*)malloc(N * 8);
+  unsigned m0 = s->modes, m1 = s->modes;
+  float feat[16];
   for (uint64_t q = 0; q < s->nchunks && rc == ORC_OK; ++q) {
     if ((q & hi_mask) != hi_vals) continue;
     if (t < kc) {
@@ -721,7 +812,11 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
         if ((i & lo_mask) != lo_vals) continue;
         apply_pair(g->u, d + 2 * i, d + 2 * (i | ((size_t)1 << t)));
       }
-      rc = csim_store(s, q, x0);
+      if (s->use_mlp) {
+        orc_mlp_features(s->img[q], s->len[q], kc, g, s->S_cur, x0, feat);
+        m0 = orc_mlp_wants_split(s->mlp, feat) ? 0x3Fu : ORC_DEFAULT_MODES;
+      }
+      rc = csim_store(s, q, x0, m0);
     } else {
       uint64_t qb = (uint64_t)1 << (t - kc);
       if (q & qb) continue;
@@ -734,8 +829,14 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
         if ((i & lo_mask) != lo_vals) continue;
         apply_pair(g->u, d0 + 2 * i, d1 + 2 * i);
       }
-      rc = csim_store(s, q, x0);
-      if (!rc) rc = csim_store(s, q1, x1);
+      if (s->use_mlp) {
+        orc_mlp_features(s->img[q], s->len[q], kc, g, s->S_cur, x0, feat);
+        m0 = orc_mlp_wants_split(s->mlp, feat) ? 0x3Fu : ORC_DEFAULT_MODES;
+        orc_mlp_features(s->img[q1], s->len[q1], kc, g, s->S_cur, x1, feat);
+        m1 = orc_mlp_wants_split(s->mlp, feat) ? 0x3Fu : ORC_DEFAULT_MODES;
+      }
+      rc = csim_store(s, q, x0, m0);
+      if (!rc) rc = csim_store(s, q1, x1, m1);
     }
   }
   free(x0);
@@ -814,6 +915,14 @@ void orc_csim_stats(const orc_csim* s, orc_stats* st) {
 }
 
 uint64_t orc_csim_nchunks(const orc_csim* s) { return s->nchunks; }
+
+/* Selector for later gates: use_mlp = 0 keeps the mode set; 1 tries Solution D for a
+ * chunk only when the network (params, ORC_MLP_NPARAMS floats) says so. */
+int orc_csim_set_mlp(orc_csim* s, int use_mlp, const float* params) {
+  s->use_mlp = use_mlp;
+  if (use_mlp) memcpy(s->mlp, params, sizeof(s->mlp));
+  return ORC_OK;
+}
 
 /* Mode set the encoder chooses from for later gates (bit m = mode m). */
 int orc_csim_set_modes(orc_csim* s, unsigned mask) {

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqcsim.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "mlp.cu"]
 HEADERS = ["device.cuh", "launch.h"]
 
 NVCC = os.environ.get("NVCC", "nvcc")

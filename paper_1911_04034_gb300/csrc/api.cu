@@ -141,6 +141,10 @@ struct sim {
   bool timing = false;
   bool phases = false;
   uint32_t modes = qc::kDefaultModes;
+  int selector = 0;                  // 0 mode set, 2 selector network
+  unsigned short* d_mlp = nullptr;   // bfloat16 parameters of the selector network
+  float* d_trace = nullptr;          // selector training records
+  uint64_t trace_cap = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   size_t ev_next = 0;
@@ -148,6 +152,8 @@ struct sim {
 
   ~sim() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    cudaFree(d_mlp);
+    cudaFree(d_trace);
     cudaFree(P.pages);
     cudaFree(P.dir);
     cudaFree(P.stack);
@@ -356,6 +362,18 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
   L.target = t;
   L.prof = s->phases ? 1 : 0;
   L.modes = s->modes;
+  L.selector = s->selector;
+  L.mlp = s->d_mlp;
+  {
+    const double* u = g->u;
+    const bool real = u[1] == 0 && u[3] == 0 && u[5] == 0 && u[7] == 0;
+    const bool diag = u[2] == 0 && u[3] == 0 && u[4] == 0 && u[5] == 0;
+    const bool perm = u[0] == 0 && u[1] == 0 && u[6] == 0 && u[7] == 0;
+    L.gfeat = (real ? 1u : 0u) | (diag ? 2u : 0u) | (perm ? 4u : 0u) | (t < kc ? 8u : 0u);
+  }
+  L.trace = s->d_trace;
+  L.trace_n = s->d_trace ? &s->d_ctl->trace_n : nullptr;
+  L.trace_cap = s->trace_cap;
   if (t >= kc) {
     L.pair = 1;
     L.pair_bit = 1ull << (t - kc);
@@ -467,6 +485,44 @@ sim_status sim_set_modes(sim_t* s, uint32_t modes) {
   if ((modes & qc::kDefaultModes) != qc::kDefaultModes || (modes >> qc::M_NMODES))
     return fail(SIM_ERR_INVALID, "the mode set must contain ZERO..RAW (0x1F) and only known modes");
   s->modes = modes;
+  return SIM_OK;
+}
+
+sim_status sim_set_selector(sim_t* s, int selector, const uint16_t* bf16_params) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  if (selector < 0 || selector > 2) return fail(SIM_ERR_INVALID, "selector must be 0, 1 or 2");
+  if (selector == 2) {
+    if (!bf16_params) return fail(SIM_ERR_INVALID, "the selector network needs its parameters");
+    if (!s->d_mlp) CK(cudaMalloc(&s->d_mlp, qc::kMlpParams * 2), "selector parameters");
+    CK(cudaMemcpy(s->d_mlp, bf16_params, qc::kMlpParams * 2, cudaMemcpyHostToDevice), "selector parameters");
+  }
+  s->modes = selector == 1 ? (qc::kDefaultModes | (1u << qc::M_SPLIT)) : qc::kDefaultModes;
+  s->selector = selector == 2 ? 2 : 0;
+  return SIM_OK;
+}
+
+sim_status sim_trace(sim_t* s, uint64_t capacity) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  cudaFree(s->d_trace);
+  s->d_trace = nullptr;
+  s->trace_cap = 0;
+  CK(cudaMemset(&s->d_ctl->trace_n, 0, sizeof(unsigned long long)), "trace counter");
+  if (capacity == 0) return SIM_OK;
+  CK(cudaMalloc(&s->d_trace, capacity * qc::kTraceFloats * sizeof(float)), "trace buffer");
+  s->trace_cap = capacity;
+  return SIM_OK;
+}
+
+sim_status sim_trace_read(sim_t* s, float* out, uint64_t cap_records, uint64_t* n_records) {
+  if (!s || !out || !n_records) return fail(SIM_ERR_INVALID, "NULL argument");
+  unsigned long long n = 0;
+  CK(cudaMemcpyAsync(&n, &s->d_ctl->trace_n, sizeof(n), cudaMemcpyDeviceToHost, s->st), "trace counter");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  if (n > s->trace_cap) n = s->trace_cap;
+  if (n > cap_records) n = cap_records;
+  if (n) CK(cudaMemcpy(out, s->d_trace, n * qc::kTraceFloats * sizeof(float), cudaMemcpyDeviceToHost), "trace copy");
+  *n_records = n;
   return SIM_OK;
 }
 
@@ -613,6 +669,7 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->chunk_log2 = s->kc;
   o->block_log2 = s->b;
   for (int k = 0; k < 6; ++k) o->phase_cycles[k] = h.phase_cycles[k];
+  o->split_trials = h.split_trials;
   if (h.err) return s->check_device();
   return SIM_OK;
 }

@@ -67,6 +67,8 @@ struct DevCtl {
   unsigned long long bytes_in;  // image bytes the gate kernels read (cumulative)
   unsigned long long bytes_out; // image bytes the gate kernels wrote (cumulative)
   unsigned long long phase_cycles[6];  // SM cycles of CTA thread 0 per phase when profiling
+  unsigned long long split_trials;     // chunk encodes that ran the Solution D trial
+  unsigned long long trace_n;          // selector training records written
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -132,7 +134,8 @@ struct ScanSmem {
   uint32_t wand[2][kWarps];
   int wmax[2][3][kWarps];
   uint32_t bits_period;
-  uint32_t pad[3];
+  int split_pick;  // the selector network's decision for the chunk being encoded
+  uint32_t zcnt[2];  // selector inputs: amplitude groups with all-zero real / imaginary parts
 };
 
 // Exclusive prefix sum over the CTA with one barrier; also ORs `fo` and ANDs `fa`
@@ -446,6 +449,97 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
   return ok;
 }
 
+// ------------------------------------------------------- learned selector -- //
+// Not from the paper.  A 16 -> 32 -> 32 -> 8 network with bfloat16 weights predicts
+// whether the Solution D trial (SPLIT) can win for a chunk, so that trial runs only
+// where it may pay.  Inference is float32 with a fixed order: each unit sums its
+// products over its inputs in index order, one rounding per product and per sum
+// (no fused multiply-add), then adds its bias; ReLU maps non-positive sums to +0.
+// The trial runs iff the SPLIT logit plus 2 reaches the largest mode logit: a missed
+// SPLIT costs memory, a needless trial only time.
+constexpr int kMlpParams = 1864;  // W1[32][16] b1[32] W2[32][32] b2[32] W3[8][32] b3[8]
+constexpr int kTraceFloats = 20;  // features[16], best mode, STREAM and SPLIT size / RAW, 0
+
+struct SelCtx {
+  int selector;                    // 0: the mode set decides; 2: the network decides SPLIT trials
+  const unsigned short* mlp;       // bfloat16 parameters (device), selector 2
+  uint32_t gfeat;                  // gate features: bit0 real, 1 diagonal, 2 permutation, 3 target in chunk
+  uint32_t S_gate;                 // significant bits the controller chose for this gate
+  uint32_t prev_hdr[4];            // header of the chunk's previous image
+  uint32_t prev_len;               // and its length
+  float* trace;                    // trace records (device) or nullptr
+  unsigned long long* trace_n;
+  unsigned long long trace_cap;
+  unsigned long long* split_trials;  // counts chunks that ran the Solution D trial
+};
+
+__device__ __forceinline__ float bf16_at(const unsigned short* w, int i) { return __uint_as_float((uint32_t)w[i] << 16); }
+
+// Input i of the network for the chunk described by sel (kc = chunk_log2); zre / zim
+// count the chunk's G = min(2^kc, 256) groups of consecutive amplitudes whose real /
+// imaginary parts are all zero after the gate.
+__device__ __forceinline__ float sel_feature(const SelCtx& sel, int kc, int i, uint32_t zre, uint32_t zim) {
+  const uint32_t pmode = sel.prev_hdr[0] & 0xffu, pS = (sel.prev_hdr[0] >> 8) & 0xffu, pbits = sel.prev_hdr[3];
+  const float G = __uint2float_rn(min(1u << kc, 256u));
+  if (i < 6) return pmode == (uint32_t)i ? 1.0f : 0.0f;
+  if (i == 6) return __fdiv_rn(__uint2float_rn(sel.prev_len), __uint2float_rn(16u + (16u << kc)));
+  if (i == 7) return __fdiv_rn(__uint2float_rn(pS), 64.0f);
+  if (i == 8) return __fdiv_rn(__uint2float_rn(pbits), __uint2float_rn(64u * (2u << kc)));
+  if (i < 13) return ((sel.gfeat >> (i - 9)) & 1u) ? 1.0f : 0.0f;
+  if (i == 13) return __fdiv_rn(__uint2float_rn(zre), G);
+  if (i == 14) return __fdiv_rn(__uint2float_rn(sel.S_gate), 64.0f);
+  return __fdiv_rn(__uint2float_rn(zim), G);
+}
+
+// Counts the groups of sel_feature (every thread of the block calls it; each thread's
+// VPT values form one group, or, at VPT = 1, one half of an amplitude).
+template <int VPT>
+__device__ __forceinline__ void zero_group_counts(const uint64_t* tile, uint32_t N, uint32_t& zre, uint32_t& zim) {
+  const uint32_t j0 = threadIdx.x * VPT;
+  uint64_t v[VPT];
+  load_vals<VPT>(tile, j0, N, v);
+  bool re_nz = false, im_nz = false;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    if (j0 + k < N) {
+      const bool nz = (v[k] << 1) != 0ull;
+      if ((j0 + k) & 1u) im_nz |= nz;
+      else re_nz |= nz;
+    }
+  }
+  const uint32_t G = min(N >> 1, 256u);
+  zre = G - (uint32_t)__syncthreads_count(re_nz);
+  zim = G - (uint32_t)__syncthreads_count(im_nz);
+}
+
+// Warp-level inference; every lane of the warp must call it.  Returns (to all lanes)
+// whether SPLIT has the largest of the six mode logits (first maximum wins).
+__device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint32_t zre, uint32_t zim) {
+  const int lane = threadIdx.x & 31;
+  const unsigned short* w = sel.mlp;
+  const float x = lane < 16 ? sel_feature(sel, kc, lane, zre, zim) : 0.0f;
+  float acc = 0.0f;
+  for (int i = 0; i < 16; ++i) acc = __fadd_rn(acc, __fmul_rn(bf16_at(w, 16 * lane + i), __shfl_sync(0xffffffffu, x, i)));
+  acc = __fadd_rn(acc, bf16_at(w, 512 + lane));
+  const float h1 = acc > 0.0f ? acc : 0.0f;
+  acc = 0.0f;
+  for (int i = 0; i < 32; ++i)
+    acc = __fadd_rn(acc, __fmul_rn(bf16_at(w, 544 + 32 * lane + i), __shfl_sync(0xffffffffu, h1, i)));
+  acc = __fadd_rn(acc, bf16_at(w, 1568 + lane));
+  const float h2 = acc > 0.0f ? acc : 0.0f;
+  const int o = lane & 7;
+  acc = 0.0f;
+  for (int i = 0; i < 32; ++i)
+    acc = __fadd_rn(acc, __fmul_rn(bf16_at(w, 1600 + 32 * o + i), __shfl_sync(0xffffffffu, h2, i)));
+  acc = __fadd_rn(acc, bf16_at(w, 1856 + o));
+  float mx = __shfl_sync(0xffffffffu, acc, 0);
+  for (int m = 1; m < 6; ++m) {
+    const float v = __shfl_sync(0xffffffffu, acc, m);
+    if (v > mx) mx = v;
+  }
+  return __fadd_rn(__shfl_sync(0xffffffffu, acc, 5), 2.0f) >= mx;
+}
+
 // ----------------------------------------------------------- encoder ----- //
 // Writes the 2-bit codes and the residual stream of coded values [j0, j0 + VPT) of this
 // thread (values >= nv are not coded) into an image whose payload was cleared; o0 is
@@ -515,8 +609,22 @@ do {                                                        \
 // not fit in img_cap).
 template <int VPT>
 __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int force_mode, uint32_t modes, uint8_t* img,
-                                 uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err) {
+                                 uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err,
+                                 const SelCtx* sel = nullptr) {
   const uint32_t N = 2u << kc, A = 1u << kc;
+  // the selector network decides whether this chunk gets the Solution D trial
+  if (sel && (sel->selector == 2 || sel->trace)) {
+    uint32_t zre, zim;
+    zero_group_counts<VPT>(tile, N, zre, zim);
+    if (threadIdx.x == 0) {
+      s.zcnt[0] = zre;
+      s.zcnt[1] = zim;
+    }
+    if (sel->selector == 2 && threadIdx.x < 32u) {
+      const bool pick = sel_wants_split(*sel, kc, zre, zim);
+      if (threadIdx.x == 0) s.split_pick = pick ? 1 : 0;
+    }
+  }
   const uint32_t j0 = threadIdx.x * VPT;
   const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
   // 0. clear the payload area the packers OR into (the buffer is free here)
@@ -581,6 +689,7 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
     }
   }
   // Solution D order (SPLIT): only its residual length is needed unless it wins
+  if (sel && sel->selector == 2) modes = s.split_pick ? (modes | (1u << M_SPLIT)) : (modes & ~(1u << M_SPLIT));
   const bool want_split = force_mode == (int)M_SPLIT || (force_mode < 0 && ((modes >> M_SPLIT) & 1u));
   uint32_t sum2 = 0;
   if (want_split) {
@@ -666,6 +775,20 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   if (mode == M_STREAM) { nv = N; rbits = total; }
   if (mode == M_RAW) nv = N;
   if (mode == M_SPLIT) { nv = N; rbits = total2; }
+  if (sel && sel->split_trials && threadIdx.x == 0 && want_split && force_mode < 0) atomicAdd(sel->split_trials, 1ull);
+  // training record: the chunk's inputs, the exhaustive choice and both trial sizes
+  if (sel && sel->trace && threadIdx.x == 0 && want_split) {
+    const unsigned long long k = atomicAdd(sel->trace_n, 1ull);
+    if (k < sel->trace_cap) {
+      float* rec = sel->trace + k * kTraceFloats;
+      for (int i = 0; i < 16; ++i) rec[i] = sel_feature(*sel, kc, i, s.zcnt[0], s.zcnt[1]);
+      const float rawf = __uint2float_rn(16u + 8u * N);
+      rec[16] = (float)mode;
+      rec[17] = __fdiv_rn(__uint2float_rn(size[M_STREAM]), rawf);
+      rec[18] = __fdiv_rn(__uint2float_rn(size[M_SPLIT]), rawf);
+      rec[19] = 0.0f;
+    }
+  }
   if (threadIdx.x == 0) {
     uint32_t* h = reinterpret_cast<uint32_t*>(img);
     h[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | ((mode == M_PERIOD ? (uint32_t)period : 0u) << 16);

@@ -245,8 +245,28 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   __syncthreads();
   QC_PHASE(2);
-  const uint32_t n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err);
-  const uint32_t n1 = has1 ? encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err) : 1u;
+  SelCtx sel;
+  sel.selector = L.selector;
+  sel.mlp = L.mlp;
+  sel.gfeat = L.gfeat;
+  sel.S_gate = S;
+  sel.trace = L.trace;
+  sel.trace_n = L.trace_n;
+  sel.trace_cap = L.trace_cap;
+  sel.split_trials = &ctl->split_trials;
+  {
+    const uint4 h = reinterpret_cast<const uint4*>(m.img0)[0];  // previous image header (still staged)
+    sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
+    sel.prev_len = b0;
+  }
+  const uint32_t n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
+  uint32_t n1 = 1u;
+  if (has1) {
+    const uint4 h = reinterpret_cast<const uint4*>(m.img1)[0];
+    sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
+    sel.prev_len = b1;
+    n1 = encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
+  }
   QC_PHASE(3);
   if (n0 == 0u || n1 == 0u) return false;
   if (threadIdx.x == 0) {

@@ -22,6 +22,12 @@ struct GateLaunch {
   int pair;                      // 1: target >= chunk_log2
   int prof;                      // 1: accumulate per-phase SM cycles
   uint32_t modes;                // chunk modes the encoder may choose (bit m = mode m)
+  int selector;                  // 0: the mode set decides; 2: the selector network decides SPLIT trials
+  const unsigned short* mlp;     // selector parameters (bfloat16, device)
+  uint32_t gfeat;                // gate features for the selector (see SelCtx)
+  float* trace;                  // selector training records (device) or nullptr
+  unsigned long long* trace_n;
+  unsigned long long trace_cap;
 };
 
 // One gate of one simulator inside a batched launch; its work items are the global

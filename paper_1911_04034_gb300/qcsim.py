@@ -40,6 +40,7 @@ class Stats(C.Structure):
         ("fidelity_lb_sum", C.c_double), ("fidelity_lb_prod", C.c_double), ("eps_switch_gate", C.c_int64),
         ("sig_bits_current", C.c_int32), ("level", C.c_int32), ("chunk_log2", C.c_int32), ("block_log2", C.c_int32),
         ("phase_cycles", C.c_uint64 * 6),
+        ("split_trials", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -84,6 +85,11 @@ def lib():
             "sim_batch_apply": [vp, i32, vp, vp, i32],
             "sim_autotune_chunk": [i32, i32, dbl, vp, sz, vp, i32, C.POINTER(C.c_int), vp],
             "sim_set_timing": [vp, i32],
+            "sim_set_selector": [vp, i32, vp],
+            "sim_trace": [vp, u64],
+            "sim_trace_read": [vp, vp, u64, C.POINTER(C.c_uint64)],
+            "sim_mlp_train": [vp, vp, vp, u64, i32, i32, C.c_float, u64, vp, vp, C.POINTER(C.c_float)],
+            "sim_mlp_grad": [vp, vp, vp, vp, u64, vp, C.POINTER(C.c_float)],
             "sim_timing": [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                            C.POINTER(C.c_uint64)],
             "sim_sv_create": [i32, pp],
@@ -186,6 +192,26 @@ class Sim:
         """0x1F: Solution C modes (default); 0x3F adds SPLIT (Solution D)."""
         _check(lib().sim_set_modes(self._h, int(modes)), "sim_set_modes")
 
+    def set_selector(self, selector: int, bf16_params=None) -> None:
+        """0 Solution C only, 1 Solution C and D exhaustively, 2 C and D with the
+        selector network deciding the D trials (bf16_params: 1864 uint16)."""
+        p = None
+        if bf16_params is not None:
+            p = np.ascontiguousarray(bf16_params, dtype=np.uint16)
+            assert p.size == 1864
+        _check(lib().sim_set_selector(self._h, int(selector), C.c_void_p(_ptr(p)) if p is not None else None),
+               "sim_set_selector")
+
+    def trace(self, capacity: int) -> None:
+        _check(lib().sim_trace(self._h, int(capacity)), "sim_trace")
+
+    def trace_read(self, cap: int = 1 << 20) -> np.ndarray:
+        """Records as an array of shape (n, 20)."""
+        out = np.zeros((cap, 20), dtype=np.float32)
+        n = C.c_uint64()
+        _check(lib().sim_trace_read(self._h, C.c_void_p(_ptr(out)), cap, C.byref(n)), "sim_trace_read")
+        return out[: n.value]
+
     def sync(self) -> None:
         _check(lib().sim_sync(self._h), "sim_sync")
 
@@ -263,6 +289,34 @@ def autotune_chunk(n_qubits: int, block_log2: int, err_bound: float, probe, cand
                                     C.cast(cand, C.c_void_p), len(candidates), C.byref(best), C.c_void_p(_ptr(rates))),
            "sim_autotune_chunk")
     return int(best.value), dict(zip(candidates, rates.tolist()))
+
+
+def mlp_grad(params, x, mode, sizes):
+    """(loss, gradient) of the selector loss at bfloat16(params), computed on the GPU."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    m = np.ascontiguousarray(mode, dtype=np.int32)
+    sz = np.ascontiguousarray(sizes, dtype=np.float32)
+    g = np.zeros(1864, dtype=np.float32)
+    loss = C.c_float()
+    _check(lib().sim_mlp_grad(C.c_void_p(_ptr(p)), C.c_void_p(_ptr(xx)), C.c_void_p(_ptr(m)), C.c_void_p(_ptr(sz)),
+                              m.size, C.c_void_p(_ptr(g)), C.byref(loss)), "sim_mlp_grad")
+    return float(loss.value), g
+
+
+def mlp_train(x, mode, sizes, params, epochs: int = 20, batch: int = 256, lr: float = 3e-3, seed: int = 1):
+    """Trains the selector on the GPU; returns (float32 params, bfloat16 params as
+    uint16, last epoch's loss)."""
+    p = np.ascontiguousarray(params, dtype=np.float32).copy()
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    m = np.ascontiguousarray(mode, dtype=np.int32)
+    sz = np.ascontiguousarray(sizes, dtype=np.float32)
+    wb = np.zeros(1864, dtype=np.uint16)
+    loss = C.c_float()
+    _check(lib().sim_mlp_train(C.c_void_p(_ptr(xx)), C.c_void_p(_ptr(m)), C.c_void_p(_ptr(sz)), m.size, int(epochs),
+                               int(batch), C.c_float(lr), C.c_uint64(seed), C.c_void_p(_ptr(p)), C.c_void_p(_ptr(wb)),
+                               C.byref(loss)), "sim_mlp_train")
+    return p, wb, float(loss.value)
 
 
 def codec_stride(chunk_log2: int) -> int:

@@ -79,3 +79,74 @@ def test_plain_gradient_descent_reduces_the_loss():
             p[k] -= 0.05 * g[k]
     l1, _ = M.loss_and_grads(p, x, mode, sizes)
     assert l1 < 0.5 * l0
+
+
+def test_c_inference_equals_numpy_definition_bit_for_bit():
+    import oracle as O
+
+    rng = np.random.default_rng(11)
+    for seed in range(3):
+        p = M.init_params(seed)
+        for k in ("b1", "b2", "b3"):
+            p[k] = M.bf16_round(rng.standard_normal(M.SHAPES[k]).astype(np.float32) * 0.3)
+        flat = M.flatten(p)
+        x = rng.standard_normal((200, M.N_IN)).astype(np.float32)
+        want = M.forward32(p, x)
+        got = np.stack([O.mlp_forward_c(flat, row) for row in x])
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_decision_rule_margin_edges():
+    """Output layer weights zero: the logits are the biases b3, so the rule can be
+    checked at its edges (SPLIT logit exactly 2 below the top one is a trial, and so is
+    one whose float32 sum with 2 rounds up to the top; one float32 step of the sum
+    below is not); C and numpy agree."""
+    import oracle as O
+
+    x = np.zeros((1, M.N_IN), dtype=np.float32)
+    below1 = np.nextafter(np.float32(1), np.float32(0))  # 1 - 2^-24: + 2 rounds back to 3 in float32
+    cases = [([0, 0, 0, 3.0, 0, 1.0], True), ([0, 0, 0, 3.0, 0, below1], True),
+             ([0, 0, 0, 3.0, 0, np.float32(1 - 2.0 ** -22)], False),
+             ([5.0, 0, 0, 0, 0, 3.0], True), ([0, 0, 0, 0, 0, -1.0], True), ([0, 0, 8.0, 0, 0, 5.0], False),
+             ([1.0, 1.0, 1.0, 1.0, 1.0, 1.0], True)]
+    for b, want in cases:
+        p = M.init_params(0)
+        p["W3"] = np.zeros_like(p["W3"])
+        p["b3"] = np.array(list(b) + [0, 0], dtype=np.float32)
+        assert M.wants_split(p, x)[0] == want, b
+        assert O.mlp_wants_split_c(M.flatten(p), x[0]) == want, b
+
+
+def test_zero_group_counts_hand_cases():
+    # kc = 10: 256 groups of 4 amplitudes; kc = 3: 8 groups of one amplitude
+    v = np.zeros(1 << 10, dtype=np.complex128)
+    assert M.zero_groups(v, 10) == (256, 256, 256)
+    v[5] = 1.0          # group 1 gets a real part
+    v[6] = 1j           # group 1 an imaginary part
+    v[1023] = -0.0 - 0.0j   # -0 counts as zero
+    v[12] = 3e-320      # a subnormal is not zero: group 3
+    assert M.zero_groups(v, 10) == (254, 255, 256)
+    w = np.array([1, 1j, 0, 1 + 1j, -0.0, 2, 3j, 0], dtype=np.complex128)
+    assert M.zero_groups(w, 3) == (5, 5, 8)  # zero real parts at 1, 2, 4, 6, 7; imaginary at 0, 2, 4, 5, 7
+
+
+def test_features_c_equal_python_definition():
+    import oracle as O
+    from paper_1911_04034_gb300 import circuits as Cc
+
+    rng = np.random.default_rng(12)
+    for kc in (3, 6, 10):
+        A = 1 << kc
+        a = rng.standard_normal(A) + 1j * rng.standard_normal(A)
+        real = rng.standard_normal(A) + 0j
+        sparse = np.where(rng.random(A) < 0.3, a, 0)
+        for img in (O.encode_chunk(a, kc, 26), O.encode_chunk(np.zeros(A, complex), kc, 64),
+                    O.encode_chunk(a, kc, 26, force_mode=5)):
+            for vals in (a, real, sparse, 1j * real):
+                for g in (Cc.gate(2, Cc.H), Cc.gate(9, Cc.T, {1: 1}), Cc.gate(2, Cc.X), Cc.gate(7, Cc.SX)):
+                    for S in (64, 26):
+                        want = M.features(img, kc, g["u"], int(g["target"]), S, vals)
+                        got = O.mlp_features_c(img, kc, g, S, vals)
+                        assert np.array_equal(got, want)
+    x = M.features(O.encode_chunk(real, 10, 26), 10, Cc.H.ravel().view(np.float64), 3, 26, real)
+    assert x[13] == 0.0 and x[15] == 1.0 and x[9] == 1.0 and x[12] == 1.0
