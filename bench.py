@@ -152,7 +152,7 @@ def run_gpu(args) -> dict | None:
     layers = layers_of(gates, n, depth)
     raw = 16 << n
     stream = torch.cuda.Stream()
-    sim = qcsim.Sim(n, BLOCK_LOG2, args.eps, chunk_log2=CHUNK_LOG2, budget=raw // 4, pool_bytes=raw + raw // 8,
+    sim = qcsim.Sim(n, BLOCK_LOG2, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=raw + raw // 8,
                     stream=stream)
     kc = sim.chunk_log2
 
@@ -424,6 +424,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)
+    ap.add_argument("--kc", type=int, default=CHUNK_LOG2, help="chunk_log2 (amplitudes per coded chunk = 2^kc)")
     args = ap.parse_args()
     global ROWS, COLS, BLOCK_LOG2
     ROWS, COLS = args.rows, args.cols

@@ -105,6 +105,7 @@ GateCoef coef_of(const sim_gate* g) {
     if (k > 0 && c.c[4 * r] == 1.0) c.first[r] = 1;
     if (k > 0 && c.c[4 * r] == -1.0) c.first[r] = 2;
   }
+  c.dense = (c.cnt[0] == 4 && c.cnt[1] == 4 && c.cnt[2] == 4 && c.cnt[3] == 4) ? 1 : 0;
   return c;
 }
 
@@ -386,6 +387,26 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
     L.free_mask = chunk_bits & ~hi_mask;
     L.nact = 1ull << popcount64(L.free_mask);
     L.items = (L.nact + 1ull) / 2ull;
+  }
+  // free_mask as runs: run i at bit p receives counter bits [q, q + len) shifted by p - q
+  L.nruns = 0;
+  int q = 0;
+  for (int p = 0; p < 64 && L.nruns >= 0;) {
+    if (!((L.free_mask >> p) & 1ull)) {
+      ++p;
+      continue;
+    }
+    int len = 0;
+    while (p + len < 64 && ((L.free_mask >> (p + len)) & 1ull)) ++len;
+    if (L.nruns == qc::kMaxRuns) {
+      L.nruns = -1;
+      break;
+    }
+    L.run_mask[L.nruns] = (len == 64 ? ~0ull : ((1ull << len) - 1ull)) << p;
+    L.run_shift[L.nruns] = (uint32_t)(p - q);
+    ++L.nruns;
+    q += len;
+    p += len;
   }
   return L;
 }

@@ -132,7 +132,8 @@ struct ScanSmem {
   uint32_t wsum[2][kWarps];
   uint32_t wor[2][kWarps];
   uint32_t wand[2][kWarps];
-  int wmax[2][3][kWarps];
+  uint32_t wlm[2][kWarps];  // lead-byte scan: bytes set, and their values
+  uint32_t wlv[2][kWarps];
   uint32_t bits_period;
   int split_pick;  // the selector network's decision for the chunk being encoded
   uint32_t zcnt[2];  // selector inputs: amplitude groups with all-zero real / imaginary parts
@@ -204,26 +205,36 @@ __device__ __forceinline__ void block_scan2(uint32_t v, uint32_t v2, uint32_t fo
   *all_and = a;
 }
 
-// Exclusive max-scan of three ints over the CTA (identity -1), one barrier.
-__device__ __forceinline__ void block_excl_max3(int a[3], ScanSmem& s, int& pp) {
+// The leading three bytes of a value that a thread's run of coded values leaves for its
+// successor: bytes a value writes explicitly replace the running ones, bytes it copies
+// keep them.  A run is summarised as (M, V): the bits of the top three bytes (of the
+// value's high word) that it sets, and their values.  Composition (earlier, later) =
+// (M1 | M2, (V1 & ~M2) | V2) is associative; this is its exclusive scan over the CTA
+// (identity (0, 0): the first value's predecessor is 0), one barrier.  Returns V.
+__device__ __forceinline__ uint32_t block_lead_scan(uint32_t M, uint32_t V, ScanSmem& s, int& pp) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int inc[3];
+  uint32_t im = M, iv = V;
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    inc[b] = warp_incl_max(a[b]);
-    if (lane == 31) s.wmax[pp][b][w] = inc[b];
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t um = __shfl_up_sync(0xffffffffu, im, d), uv = __shfl_up_sync(0xffffffffu, iv, d);
+    if (lane >= d) {
+      iv = (uv & ~im) | iv;
+      im |= um;
+    }
+  }
+  uint32_t em = __shfl_up_sync(0xffffffffu, im, 1), ev = __shfl_up_sync(0xffffffffu, iv, 1);
+  if (lane == 0) em = ev = 0u;
+  if (lane == 31) {
+    s.wlm[pp][w] = im;
+    s.wlv[pp][w] = iv;
   }
   __syncthreads();
+  uint32_t pv = 0;
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    int ex = __shfl_up_sync(0xffffffffu, inc[b], 1);
-    if (lane == 0) ex = -1;
-#pragma unroll
-    for (int i = 0; i < kWarps; ++i)
-      if (i < w) ex = max(ex, s.wmax[pp][b][i]);
-    a[b] = ex;
-  }
+  for (int i = 0; i < kWarps; ++i)
+    if (i < w) pv = (pv & ~s.wlm[pp][i]) | s.wlv[pp][i];
   pp ^= 1;
+  return (pv & ~em) | ev;
 }
 
 // ---------------------------------------------------------- bit helpers --- //
@@ -310,7 +321,16 @@ __device__ __forceinline__ uint32_t coded_pos(uint32_t k, uint32_t A) {
   return SPLIT ? (k < A ? 2u * k : 2u * (k - A) + 1u) : k;
 }
 
-template <int VPT, bool SPLIT>
+// Bits of the top three bytes of a high word that a value with code c writes
+// explicitly (bytes c..2), and those it copies from its predecessor (bytes 0..c-1).
+__device__ __forceinline__ uint32_t lead_explicit(uint32_t c) { return 0xFFFFFF00u & (0xFFFFFFFFu >> (8u * c)); }
+__device__ __forceinline__ uint32_t lead_copied(uint32_t c) { return ~(0xFFFFFFFFu >> (8u * c)); }
+
+// Decodes the XOR-coded values of a PERIOD / STREAM / SPLIT image.  W32: S <= 32, so
+// every value's low word is zero and only high words are read from the stream.
+// FULL: all 2^(kc+1) values are coded (STREAM, SPLIT), so with VPT >= 2 every value
+// of every thread exists.
+template <int VPT, bool SPLIT, bool W32, bool FULL>
 __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t nv, uint32_t S, uint32_t bits,
                                  uint64_t* tile, ScanSmem& s, int& pp) {
   const uint32_t A = nv >> 1;
@@ -318,8 +338,12 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
   const uint32_t cb = code_bytes(nv);
   const uint32_t* m32 = reinterpret_cast<const uint32_t*>(payload + cb);
   const uint32_t j0 = threadIdx.x * VPT;
+  bool has[VPT];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) has[k] = FULL ? (VPT >= 2 || j0 < nv) : (j0 + k < nv);
   // the 2-bit codes of this thread's values share one 32-bit word (VPT divides 16)
   const uint32_t cword = j0 < nv ? codes32[j0 >> 4] : 0u;
+  const uint32_t cbase = VPT >= 4 ? cword >> (8u * ((j0 >> 2) & 3u)) : cword;
   uint32_t c[VPT], r[VPT];
   uint32_t sum = 0;
 #pragma unroll
@@ -327,8 +351,9 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
     const uint32_t j = j0 + k;
     c[k] = 3u;
     r[k] = 0u;
-    if (j < nv) {
-      c[k] = (cword >> (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u))) & 3u;
+    if (has[k]) {
+      c[k] = VPT >= 4 ? (cbase >> (8 * (k >> 2) + 6 - 2 * (k & 3))) & 3u
+                      : (cword >> (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u))) & 3u;
       r[k] = resid_len(c[k], S);
       sum += r[k];
     }
@@ -336,62 +361,49 @@ __device__ bool decode_xor_block(const uint8_t* payload, uint32_t plen, uint32_t
   uint32_t total, fo, fa;
   uint32_t o = block_scan(sum, 0u, 0u, s, pp, &total, &fo, &fa);
   if (total != bits || cb + resid_bytes(bits) != plen) return false;
-  // explicit part of every value: the residual bits placed at [8c, S)
+  // explicit part of every value (the residual bits placed at [8c, S)) and the run's
+  // effect on the leading bytes
   const uint64_t mS = trunc_mask(S);
   const uint32_t mhi = (uint32_t)(mS >> 32), mlo = (uint32_t)mS;
-  uint64_t e[VPT];
-  int lw[3] = {-1, -1, -1};
+  uint32_t ehi[VPT], elo[VPT];
+  uint32_t M = 0u, V = 0u;
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    e[k] = 0ull;
-    if (j < nv) {
-      uint32_t hi, lo;
-      stream_window(m32, o, hi, lo);
+    ehi[k] = elo[k] = 0u;
+    if (has[k]) {
       const uint32_t d = 8u * c[k];
-      const uint32_t lo2 = __funnelshift_r(lo, hi, d), hi2 = hi >> d;
-      e[k] = ((uint64_t)(hi2 & mhi) << 32) | (uint64_t)(lo2 & mlo);
+      if (W32) {
+        const uint32_t q = o >> 5, sh = o & 31u;
+        const uint32_t x = __funnelshift_l(m32[(q + 1u) ^ 1u], m32[q ^ 1u], sh);
+        ehi[k] = (x >> d) & mhi;
+      } else {
+        uint32_t hi, lo;
+        stream_window(m32, o, hi, lo);
+        ehi[k] = (hi >> d) & mhi;
+        elo[k] = __funnelshift_r(lo, hi, d) & mlo;
+      }
       o += r[k];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-        if (c[k] <= (uint32_t)b) lw[b] = (int)j;
+      const uint32_t ex = lead_explicit(c[k]);
+      V = (V & ~ex) | (ehi[k] & 0xFFFFFF00u);
+      M |= ex;
     }
   }
-  if (SPLIT) {
-#pragma unroll
-    for (int k = 0; k < VPT; ++k)
-      if (j0 + k < nv) tile[tile_val(coded_pos<true>(j0 + k, A))] = e[k];
-  } else {
-    store_vals<VPT>(tile, j0, nv, e);
-  }
-  // last explicit writer of leading byte b before this thread's first value (the
-  // scan's barrier also makes every explicit part visible)
-  block_excl_max3(lw, s, pp);
-  // byte b of a value with code c > b repeats byte b of the last value that wrote it
-  // explicitly (code <= b); before the first value it is 0
-  uint64_t lastb[3];
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-    lastb[b] = lw[b] >= 0 ? (tile[tile_val(coded_pos<SPLIT>((uint32_t)lw[b], A))] & (0xFF00000000000000ull >> (8 * b)))
-                          : 0ull;
-  __syncthreads();  // every thread has read the explicit parts it needs
+  // leading bytes of the predecessor of value j0, then the copies in order
+  uint32_t P = block_lead_scan(M, V, s, pp);
+  uint64_t e[VPT];
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    if (j0 + k < nv) {
-      uint64_t v = e[k];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-        if ((uint32_t)b < c[k]) v |= lastb[b];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-        if (c[k] <= (uint32_t)b) lastb[b] = v & (0xFF00000000000000ull >> (8 * b));
-      e[k] = v;
+    e[k] = 0ull;
+    if (has[k]) {
+      const uint32_t hi = ehi[k] | (P & lead_copied(c[k]));
+      P = hi;
+      e[k] = ((uint64_t)hi << 32) | (uint64_t)(W32 ? 0u : elo[k]);
     }
   }
   if (SPLIT) {
 #pragma unroll
     for (int k = 0; k < VPT; ++k)
-      if (j0 + k < nv) tile[tile_val(coded_pos<true>(j0 + k, A))] = e[k];
+      if (has[k]) tile[tile_val(coded_pos<true>(j0 + k, A))] = e[k];
   } else {
     store_vals<VPT>(tile, j0, nv, e);
   }
@@ -424,11 +436,18 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
     }
   }
   if (ok && mode == M_SPLIT) {
-    if (decode_xor_block<VPT, true>(payload, plen, nv, S, bits, tile, s, pp)) return true;
+    if (S <= 32u ? decode_xor_block<VPT, true, true, true>(payload, plen, nv, S, bits, tile, s, pp)
+                 : decode_xor_block<VPT, true, false, true>(payload, plen, nv, S, bits, tile, s, pp))
+      return true;
     ok = false;
   }
   if (ok && (mode == M_PERIOD || mode == M_STREAM)) {
-    ok = decode_xor_block<VPT, false>(payload, plen, nv, S, bits, tile, s, pp);
+    if (mode == M_STREAM)
+      ok = S <= 32u ? decode_xor_block<VPT, false, true, true>(payload, plen, nv, S, bits, tile, s, pp)
+                    : decode_xor_block<VPT, false, false, true>(payload, plen, nv, S, bits, tile, s, pp);
+    else
+      ok = S <= 32u ? decode_xor_block<VPT, false, true, false>(payload, plen, nv, S, bits, tile, s, pp)
+                    : decode_xor_block<VPT, false, false, false>(payload, plen, nv, S, bits, tile, s, pp);
     if (ok && mode == M_PERIOD) {
       ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tile);
       const uint32_t P = nv >> 1;  // period in amplitudes
@@ -541,6 +560,25 @@ __device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint3
 }
 
 // ----------------------------------------------------------- encoder ----- //
+// The 2-bit codes of values [j0, j0 + VPT) placed in their 32-bit code word (four
+// codes per byte, the first in the top bits); values >= nv get no code.
+template <int VPT>
+__device__ __forceinline__ uint32_t code_word(const uint32_t c[VPT], uint32_t j0, uint32_t nv) {
+  uint32_t cw = 0;
+  if (VPT >= 4) {  // j0 is a multiple of 4: the layout within the thread's bytes is fixed
+#pragma unroll
+    for (int k = 0; k < VPT; ++k)
+      if (j0 + k < nv) cw |= c[k] << (8 * (k >> 2) + 6 - 2 * (k & 3));
+    return cw << (8u * ((j0 >> 2) & 3u));
+  }
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t j = j0 + k;
+    if (j < nv) cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
+  }
+  return cw;
+}
+
 // Writes the 2-bit codes and the residual stream of coded values [j0, j0 + VPT) of this
 // thread (values >= nv are not coded) into an image whose payload was cleared; o0 is
 // the stream offset of value j0.
@@ -549,16 +587,11 @@ __device__ __forceinline__ void pack_xor(uint8_t* img, uint32_t nv, uint32_t j0,
                                          const uint32_t c[VPT], const uint32_t r[VPT]) {
   // codes: one 32-bit word per 16 values
   uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
-  uint32_t cw = 0;
+  const uint32_t cw = code_word<VPT>(c, j0, nv);
   uint32_t oend = o0;
 #pragma unroll
-  for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    if (j < nv) {
-      cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
-      oend += r[k];
-    }
-  }
+  for (int k = 0; k < VPT; ++k)
+    if (j0 + k < nv) oend += r[k];
   if (j0 < nv && cw) atomicOr(&codes32[j0 >> 4], cw);
   // residual bits: this thread owns stream bits [o0, oend); interior 32-bit units are
   // written once with plain stores, the two end units (shared with the neighbours)
@@ -602,67 +635,85 @@ do {                                                        \
 }
 
 
-// Encodes the tile (raw bit patterns; overwritten with the truncated values) into
-// img (img_cap bytes, nothing else in it is live).  S_req = 12 - EXP(eps) or 64.
-// force_mode < 0: smallest image (never larger than RAW).  Returns the image length,
-// or 0 with *err set (non-finite value, or a forced mode that does not apply or does
-// not fit in img_cap).
+// pack_xor for S <= 32: every residual is at most 32 bits of the value's high word h,
+// so a value touches at most two 32-bit units of the stream.
 template <int VPT>
-__device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int force_mode, uint32_t modes, uint8_t* img,
-                                 uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err,
-                                 const SelCtx* sel = nullptr) {
-  const uint32_t N = 2u << kc, A = 1u << kc;
-  // the selector network decides whether this chunk gets the Solution D trial
-  if (sel && (sel->selector == 2 || sel->trace)) {
-    uint32_t zre, zim;
-    zero_group_counts<VPT>(tile, N, zre, zim);
-    if (threadIdx.x == 0) {
-      s.zcnt[0] = zre;
-      s.zcnt[1] = zim;
-    }
-    if (sel->selector == 2 && threadIdx.x < 32u) {
-      const bool pick = sel_wants_split(*sel, kc, zre, zim);
-      if (threadIdx.x == 0) s.split_pick = pick ? 1 : 0;
-    }
-  }
-  const uint32_t j0 = threadIdx.x * VPT;
-  const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
-  // 0. clear the payload area the packers OR into (the buffer is free here)
-  {
-    const uint32_t span = min(img_cap, max_coded_bytes(kc)) - 16u;
-    uint4* z = reinterpret_cast<uint4*>(img + 16);
-    for (uint32_t u = threadIdx.x; u < span / 16u; u += kThreads) z[u] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  // 1. chunk-wide width: a nonzero subnormal forces 64 bits; non-finite is an error
-  uint64_t t[VPT];
-  load_vals<VPT>(tile, j0, N, t);
-  bool sub = false, nonfin = false;
+__device__ __forceinline__ void pack_xor32(uint8_t* img, uint32_t nv, uint32_t j0, uint32_t o0, const uint32_t h[VPT],
+                                           const uint32_t c[VPT], const uint32_t r[VPT]) {
+  uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
+  const uint32_t cw = code_word<VPT>(c, j0, nv);
+  uint32_t oend = o0;
 #pragma unroll
-  for (int k = 0; k < VPT; ++k) {
-    if (j0 + k < N) {
-      const uint32_t e = (uint32_t)(t[k] >> 52) & 0x7ffu;
-      nonfin |= e == 0x7ffu;
-      sub |= (e == 0u) && ((t[k] << 12) != 0ull);
+  for (int k = 0; k < VPT; ++k)
+    if (j0 + k < nv) oend += r[k];
+  if (j0 < nv && cw) atomicOr(&codes32[j0 >> 4], cw);
+  if (oend > o0) {
+    uint32_t* m32 = reinterpret_cast<uint32_t*>(img + 16 + code_bytes(nv));
+    const uint32_t qf = o0 >> 5, ql = (oend - 1u) >> 5;
+    uint32_t qb = qf, w0 = 0, w1 = 0, o = o0;
+#define QC_FLUSH(q, v)                                        \
+do {                                                        \
+  if ((q) <= ql && (v) != 0u) {                             \
+    if ((q) == qf || (q) == ql) atomicOr(&m32[(q) ^ 1u], (v)); \
+    else m32[(q) ^ 1u] = (v);                               \
+  }                                                         \
+} while (0)
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (j0 + k < nv && r[k]) {
+        const uint32_t q = o >> 5, sh = o & 31u;
+        if (qb < q) {  // residuals are at most 32 bits: the window moves by one unit at most
+          QC_FLUSH(qb, w0);
+          w0 = w1;
+          w1 = 0;
+          ++qb;
+        }
+        const uint32_t x = h[k] << (8u * c[k]);
+        w0 |= x >> sh;
+        w1 |= __funnelshift_r(0u, x, sh);
+        o += r[k];
+      }
     }
+    QC_FLUSH(qb, w0);
+    QC_FLUSH(qb + 1u, w1);
+#undef QC_FLUSH
   }
-  bool anysub = false;
-  if (__syncthreads_or(nonfin || sub)) {  // rare: settle which of the two it was
-    if (__syncthreads_or(nonfin)) {
-      if (threadIdx.x == 0) atomicOr(err, (unsigned)E_NONFINITE);
-      return 0;
-    }
-    anysub = true;
-  }
-  const uint32_t S = anysub ? 64u : S_req;
+}
+
+// Leading identical bytes of two high words (values whose low words are zero), capped at 3.
+__device__ __forceinline__ uint32_t xor_code32(uint32_t v, uint32_t prev) {
+  return min((uint32_t)__clz((int)(v ^ prev)) >> 3, 3u);
+}
+
+// Steps 2-6 of encode_block once the chunk's width S is known.  W32 (S <= 32): the
+// truncated values' low words are zero, so codes, the Solution D trial and packing
+// work on high words only.
+template <int VPT, bool W32>
+__device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t S, int force_mode, uint32_t modes,
+                                                uint8_t* img, uint32_t img_cap, ScanSmem& s, int& pp,
+                                                unsigned int* err, const SelCtx* sel, uint64_t t[VPT]) {
+  const uint32_t N = 2u << kc, A = 1u << kc;
+  const uint32_t j0 = threadIdx.x * VPT;
+  const bool act = VPT >= 2 || j0 < N;  // every value of a run with VPT >= 2 exists
+  const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
   const uint64_t mask = trunc_mask(S);
   // 2. truncate (and store -0 as +0)
   bool nz = false;
+  uint32_t h[VPT];  // W32: high words of the truncated values
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    uint64_t v = t[k] & mask;
-    if (v == 0x8000000000000000ull) v = 0;
-    t[k] = (j0 + k < N) ? v : 0ull;
-    nz |= t[k] != 0ull;
+    if constexpr (W32) {
+      uint32_t v = (uint32_t)(t[k] >> 32) & (uint32_t)(mask >> 32);
+      if (v == 0x80000000u || !act) v = 0u;
+      h[k] = v;
+      t[k] = (uint64_t)v << 32;
+      nz |= v != 0u;
+    } else {
+      uint64_t v = t[k] & mask;
+      if (v == 0x8000000000000000ull) v = 0;
+      t[k] = act ? v : 0ull;
+      nz |= t[k] != 0ull;
+    }
   }
   store_vals<VPT>(tile, j0, N, t);
   __syncthreads();
@@ -673,20 +724,37 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   const uint64_t a0x = tile[tile_val(0)], a0y = tile[tile_val(1)];
   const uint32_t Ptop = kc >= 2 ? (1u << (kc - 1)) : 0u;
   bool cst = true, gtop = true;
+  if constexpr (W32) {
+    uint32_t ph = (uint32_t)(prev >> 32);
+    const uint32_t a0xh = (uint32_t)(a0x >> 32), a0yh = (uint32_t)(a0y >> 32);
 #pragma unroll
-  for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    c[k] = 3u;
-    r[k] = 0u;
-    if (j < N) {
-      c[k] = xor_code(t[k], prev);
-      r[k] = resid_len(c[k], S);
-      sum += r[k];
-      prev = t[k];
-      cst &= t[k] == ((j & 1u) ? a0y : a0x);
-      const uint32_t a = j >> 1;
-      if (a & Ptop) gtop &= t[k] == tile[tile_val(2u * (a ^ Ptop) + (j & 1u))];
+    for (int k = 0; k < VPT; ++k) {
+      c[k] = 3u;
+      r[k] = 0u;
+      if (act) {
+        c[k] = xor_code32(h[k], ph);
+        r[k] = resid_len(c[k], S);
+        sum += r[k];
+        ph = h[k];
+        cst &= h[k] == (((j0 + k) & 1u) ? a0yh : a0xh);
+      }
     }
+    if (act && ((j0 >> 1) & Ptop))
+      gtop = h[0] == reinterpret_cast<const uint32_t*>(tile)[2u * tile_val(j0 ^ (2u * Ptop)) + 1u];
+  } else {
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      c[k] = 3u;
+      r[k] = 0u;
+      if (act) {
+        c[k] = xor_code(t[k], prev);
+        r[k] = resid_len(c[k], S);
+        sum += r[k];
+        prev = t[k];
+        cst &= t[k] == (((j0 + k) & 1u) ? a0y : a0x);
+      }
+    }
+    if (act && ((j0 >> 1) & Ptop)) gtop = t[0] == tile[tile_val(j0 ^ (2u * Ptop))];
   }
   // Solution D order (SPLIT): only its residual length is needed unless it wins
   if (sel && sel->selector == 2) modes = s.split_pick ? (modes | (1u << M_SPLIT)) : (modes & ~(1u << M_SPLIT));
@@ -696,9 +764,10 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
     uint64_t pv = j0 > 0 && j0 <= N ? tile[tile_val(coded_pos<true>(j0 - 1, A))] : 0ull;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
-      if (j0 + k < N) {
+      if (act) {
         const uint64_t v = tile[tile_val(coded_pos<true>(j0 + k, A))];
-        sum2 += resid_len(xor_code(v, pv), S);
+        if constexpr (W32) sum2 += resid_len(xor_code32((uint32_t)(v >> 32), (uint32_t)(pv >> 32)), S);
+        else sum2 += resid_len(xor_code(v, pv), S);
         pv = v;
       }
     }
@@ -709,10 +778,12 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   const bool allzero = (f_or & 1u) == 0u;
   const bool allconst = (f_and & 1u) != 0u;
   // 4. smallest power-of-two period P (amplitudes), 2 <= P < 2^kc: the chunk is
-  //    P-periodic iff flipping any amplitude-index bit >= log2 P leaves it unchanged
+  //    P-periodic iff flipping any amplitude-index bit >= log2 P leaves it unchanged.
+  //    The scan's flag compared one value per thread with its partner half a chunk
+  //    away (a necessary condition); the loop checks every candidate in full.
   int period = -1;
   if (kc >= 2 && (f_and & 2u) && (!allconst || force_mode == (int)M_PERIOD)) {
-    int p = kc - 2;
+    int p = kc - 1;
     for (; p >= 1; --p) {
       const uint32_t P = 1u << p;
       bool ok = true;
@@ -724,7 +795,7 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
       }
       if (!__syncthreads_and(ok)) break;
     }
-    period = p + 1;
+    period = p + 1 < kc ? p + 1 : -1;
   }
   // residual bits of the first 2P values (rare: only periodic chunks)
   uint32_t bits_p = 0;
@@ -810,23 +881,88 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
     uint64_t pv = j0 > 0 && j0 <= N ? tile[tile_val(coded_pos<true>(j0 - 1, A))] : 0ull;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
-      if (j0 + k < N) {
+      if (act) {
         t[k] = tile[tile_val(coded_pos<true>(j0 + k, A))];
-        c[k] = xor_code(t[k], pv);
+        if constexpr (W32) {
+          h[k] = (uint32_t)(t[k] >> 32);
+          c[k] = xor_code32(h[k], (uint32_t)(pv >> 32));
+        } else {
+          c[k] = xor_code(t[k], pv);
+        }
         r[k] = resid_len(c[k], S);
         pv = t[k];
       } else {
         t[k] = 0ull;
+        h[k] = 0u;
         c[k] = 3u;
         r[k] = 0u;
       }
     }
-    pack_xor<VPT>(img, nv, j0, o2, t, c, r);
+    if constexpr (W32) pack_xor32<VPT>(img, nv, j0, o2, h, c, r);
+    else pack_xor<VPT>(img, nv, j0, o2, t, c, r);
   } else if (mode == M_PERIOD || mode == M_STREAM) {
-    pack_xor<VPT>(img, nv, j0, o0, t, c, r);
+    if constexpr (W32) pack_xor32<VPT>(img, nv, j0, o0, h, c, r);
+    else pack_xor<VPT>(img, nv, j0, o0, t, c, r);
   }
   __syncthreads();
   return best;
+}
+
+// Encodes the tile (raw bit patterns; overwritten with the truncated values) into
+// img (img_cap bytes, nothing else in it is live).  S_req = 12 - EXP(eps) or 64.
+// force_mode < 0: smallest image (never larger than RAW).  Returns the image length,
+// or 0 with *err set (non-finite value, or a forced mode that does not apply or does
+// not fit in img_cap).
+template <int VPT>
+__device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int force_mode, uint32_t modes, uint8_t* img,
+                                 uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err,
+                                 const SelCtx* sel = nullptr) {
+  const uint32_t N = 2u << kc;
+  // the selector network decides whether this chunk gets the Solution D trial
+  if (sel && (sel->selector == 2 || sel->trace)) {
+    uint32_t zre, zim;
+    zero_group_counts<VPT>(tile, N, zre, zim);
+    if (threadIdx.x == 0) {
+      s.zcnt[0] = zre;
+      s.zcnt[1] = zim;
+    }
+    if (sel->selector == 2 && threadIdx.x < 32u) {
+      const bool pick = sel_wants_split(*sel, kc, zre, zim);
+      if (threadIdx.x == 0) s.split_pick = pick ? 1 : 0;
+    }
+  }
+  const uint32_t j0 = threadIdx.x * VPT;
+  // 0. clear the payload area the packers OR into (the buffer is free here)
+  {
+    const uint32_t span = min(img_cap, max_coded_bytes(kc)) - 16u;
+    uint4* z = reinterpret_cast<uint4*>(img + 16);
+    for (uint32_t u = threadIdx.x; u < span / 16u; u += kThreads) z[u] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  // 1. chunk-wide width: a nonzero subnormal forces 64 bits; non-finite is an error
+  //    (with VPT >= 2 every thread's run of values lies inside the chunk)
+  const bool act = VPT >= 2 || j0 < N;
+  uint64_t t[VPT];
+  load_vals<VPT>(tile, j0, N, t);
+  bool sub = false, nonfin = false;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    if (act) {
+      const uint32_t hi = (uint32_t)(t[k] >> 32) & 0x7fffffffu;
+      nonfin |= hi >= 0x7ff00000u;
+      sub |= hi < 0x00100000u && (hi | (uint32_t)t[k]) != 0u;
+    }
+  }
+  bool anysub = false;
+  if (__syncthreads_or(nonfin || sub)) {  // rare: settle which of the two it was
+    if (__syncthreads_or(nonfin)) {
+      if (threadIdx.x == 0) atomicOr(err, (unsigned)E_NONFINITE);
+      return 0;
+    }
+    anysub = true;
+  }
+  const uint32_t S = anysub ? 64u : S_req;
+  if (S <= 32u) return encode_core<VPT, true>(tile, kc, S, force_mode, modes, img, img_cap, s, pp, err, sel, t);
+  return encode_core<VPT, false>(tile, kc, S, force_mode, modes, img, img_cap, s, pp, err, sel, t);
 }
 
 // -------------------------------------------------------- gate arithmetic -- //
@@ -843,6 +979,7 @@ struct GateCoef {
   uint8_t op[16];    // operand of each term: 0 ar, 1 ai, 2 br, 3 bi
   uint8_t cnt[4];    // kept terms per row
   uint8_t first[4];  // first term: 0 product, 1 copy, 2 sign flip
+  uint8_t dense;     // all 16 terms kept: rows in the order written, no operand lookup
 };
 
 __device__ __forceinline__ double pick4(const double x[4], uint32_t i) {
@@ -866,6 +1003,15 @@ __device__ __forceinline__ double row_eval(const GateCoef& g, int r, const doubl
 }
 
 __device__ __forceinline__ void apply_pair(const GateCoef& g, double2& a, double2& b) {
+  if (g.dense) {  // the same sums with the operands fixed (a first coefficient of +-1 multiplies exactly)
+    const double* c = g.c;
+    const double ar = a.x, ai = a.y, br = b.x, bi = b.y;
+    a.x = __fma_rn(c[3], bi, __fma_rn(c[2], br, __fma_rn(c[1], ai, __dmul_rn(c[0], ar))));
+    a.y = __fma_rn(c[7], br, __fma_rn(c[6], bi, __fma_rn(c[5], ar, __dmul_rn(c[4], ai))));
+    b.x = __fma_rn(c[11], bi, __fma_rn(c[10], br, __fma_rn(c[9], ai, __dmul_rn(c[8], ar))));
+    b.y = __fma_rn(c[15], br, __fma_rn(c[14], bi, __fma_rn(c[13], ar, __dmul_rn(c[12], ai))));
+    return;
+  }
   const double x[4] = {a.x, a.y, b.x, b.y};
   a.x = row_eval(g, 0, x);
   a.y = row_eval(g, 1, x);
@@ -929,35 +1075,57 @@ __device__ __forceinline__ uint32_t load_image_block(const Pool& P, unsigned lon
   return bytes;
 }
 
+// A CTA's page cache: ids of pages its work items freed, reused first by its later
+// items, held in shared memory during a launch (the post kernel returns the rest).
 struct CtaCache {
-  uint32_t* ids;  // global, kCacheCap entries of this CTA
-  uint32_t n;     // kept in shared memory by thread 0
+  uint32_t* ids;  // shared memory, kCacheCap entries
+  uint32_t* n;    // shared memory
 };
 
-// Thread 0 only: returns the chunk's old pages to this CTA's cache (overflow to the
-// global freed list, merged into the stack after the gate).
-__device__ __forceinline__ void free_pages_t0(const Pool& P, CtaCache& cc, const uint32_t* smem_pages, uint32_t np) {
-  for (uint32_t q = 0; q < np; ++q) {
-    if (cc.n < (uint32_t)kCacheCap) {
-      cc.ids[cc.n++] = smem_pages[q];
-    } else {
-      unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->nfreed), 1ull);
-      P.freed[pos] = smem_pages[q];
-    }
+// Warp 0: returns the old pages of the two staged chunks (p0[0..np0), p1[0..np1)) to the
+// CTA cache; what does not fit goes to the global freed list, merged into the stack
+// after the gate.
+__device__ __forceinline__ void free_pages_warp(const Pool& P, const CtaCache& cc, const uint32_t* p0, uint32_t np0,
+                                                const uint32_t* p1, uint32_t np1) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = *cc.n, tot = np0 + np1, room = (uint32_t)kCacheCap - n;
+  unsigned long long base = 0;
+  if (tot > room) {
+    if (lane == 0)
+      base = atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->nfreed), (unsigned long long)(tot - room));
+    base = __shfl_sync(0xffffffffu, base, 0);
   }
+  for (uint32_t q = lane; q < tot; q += 32u) {
+    const uint32_t id = q < np0 ? p0[q] : p1[q - np0];
+    if (q < room) cc.ids[n + q] = id;
+    else P.freed[base + (q - room)] = id;
+  }
+  __syncwarp();
+  if (lane == 0) *cc.n = n + min(tot, room);
+  __syncwarp();
 }
 
-// Thread 0 only: takes np pages (cache first, then the global stack).  False: pool dry.
-__device__ __forceinline__ bool alloc_pages_t0(const Pool& P, CtaCache& cc, uint32_t* out, uint32_t np) {
-  uint32_t q = 0;
-  while (q < np && cc.n > 0) out[q++] = cc.ids[--cc.n];
-  if (q < np) {
-    const long long need = (long long)(np - q);
-    const long long old = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top),
-                                               (unsigned long long)(-need));
-    if (old - need < 0) return false;
-    for (long long k = 0; k < need; ++k) out[q++] = P.stack[old - 1 - k];
+// Warp 0: takes np0 + np1 pages (the cache's most recent first, then the global stack)
+// into out0 / out1.  False: the pool is dry.
+__device__ __forceinline__ bool alloc_pages_warp(const Pool& P, const CtaCache& cc, uint32_t* out0, uint32_t np0,
+                                                 uint32_t* out1, uint32_t np1) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n = *cc.n, tot = np0 + np1, take = min(tot, n), need = tot - take;
+  long long old = 0;
+  if (need) {
+    if (lane == 0)
+      old = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top), (unsigned long long)(-(long long)need));
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old - (long long)need < 0) return false;
   }
+  for (uint32_t q = lane; q < tot; q += 32u) {
+    const uint32_t id = q < take ? cc.ids[n - 1u - q] : P.stack[old - 1 - (long long)(q - take)];
+    if (q < np0) out0[q] = id;
+    else out1[q - np0] = id;
+  }
+  __syncwarp();
+  if (lane == 0) *cc.n = n - take;
+  __syncwarp();
   return true;
 }
 

@@ -68,10 +68,15 @@ __device__ __forceinline__ GateSmem gate_smem(uint8_t* smem, int kc, uint32_t di
   return m;
 }
 
+// Warp 0 loads this CTA's page cache of the simulator into shared memory (empty
+// unless this CTA already worked for it in the same launch).
 __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof, long long* ph) {
-  st.cc.ids = P.cache + (size_t)blockIdx.x * kCacheCap;
-  st.cc.n = 0;
-  if (threadIdx.x == 0) st.cc.n = P.cache_n[blockIdx.x];
+  if (threadIdx.x < 32u) {
+    const uint32_t n = P.cache_n[blockIdx.x];
+    for (uint32_t q = threadIdx.x; q < n; q += 32u) st.cc.ids[q] = P.cache[(size_t)blockIdx.x * kCacheCap + q];
+    if (threadIdx.x == 0) *st.cc.n = n;
+    __syncwarp();
+  }
   st.dE = 0;
   st.rd = st.wr = 0;
   st.pp = 0;
@@ -81,14 +86,17 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
   }
 }
 
-// Thread 0: hands the CTA's page cache and counters back to the simulator.
+// Warp 0: hands the CTA's page cache and counters back to the simulator.
 __device__ __forceinline__ void cta_end(const GateLaunch& L, GateCta& st, const long long* ph) {
+  if (threadIdx.x >= 32u) return;
+  const uint32_t n = *st.cc.n;
+  for (uint32_t q = threadIdx.x; q < n; q += 32u) L.P.cache[(size_t)blockIdx.x * kCacheCap + q] = st.cc.ids[q];
   if (threadIdx.x != 0) return;
   DevCtl* ctl = L.P.ctl;
   if (L.prof)
     for (int k = 0; k < 6; ++k)
       if (ph[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)ph[k]);
-  L.P.cache_n[blockIdx.x] = st.cc.n;
+  L.P.cache_n[blockIdx.x] = n;
   if (st.dE) atomicAdd(&ctl->dE, (unsigned long long)st.dE);
   if (st.rd) atomicAdd(&ctl->bytes_in, st.rd);
   if (st.wr) atomicAdd(&ctl->bytes_out, st.wr);
@@ -98,6 +106,15 @@ __device__ __forceinline__ void cta_end(const GateLaunch& L, GateCta& st, const 
 // CTA evaluates the same rule on the same values (only the post kernel writes them).
 __device__ __forceinline__ uint32_t gate_bits(const GateLaunch& L) {
   return (uint32_t)level_bits(L.ctl, next_level(L.ctl, L.P.ctl->E, L.P.ctl->level));
+}
+
+// The chunk index of the k-th active chunk (or pair): the bits of k deposited into the
+// free chunk-index bits, run by run.
+__device__ __forceinline__ unsigned long long item_chunk(const GateLaunch& L, unsigned long long k) {
+  if (L.nruns < 0) return deposit_bits(k, L.free_mask);
+  unsigned long long out = 0;
+  for (int i = 0; i < L.nruns; ++i) out |= (k << L.run_shift[i]) & L.run_mask[i];
+  return out;
 }
 
 // One work item (two chunks) of a gate: stage, decode, apply, encode, commit.
@@ -122,14 +139,14 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   unsigned long long c0, c1;
   bool has1;
   if (L.pair) {
-    c0 = deposit_bits(item, L.free_mask) | L.hi_vals;
+    c0 = item_chunk(L, item) | L.hi_vals;
     c1 = c0 | L.pair_bit;
     has1 = true;
   } else {
     const unsigned long long k0 = 2ull * item;
-    c0 = deposit_bits(k0, L.free_mask) | L.hi_vals;
+    c0 = item_chunk(L, k0) | L.hi_vals;
     has1 = k0 + 1 < L.nact;
-    c1 = has1 ? (deposit_bits(k0 + 1, L.free_mask) | L.hi_vals) : 0ull;
+    c1 = has1 ? (item_chunk(L, k0 + 1) | L.hi_vals) : 0ull;
   }
   // stage 1: both directory entries (warp 0 and warp 1)
   if (threadIdx.x < 32u) {
@@ -204,10 +221,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    free_pages_t0(P, st.cc, m.ent0 + 4, np0);
-    if (has1) free_pages_t0(P, st.cc, m.ent1 + 4, np1);
-  }
+  if (threadIdx.x < 32u) free_pages_warp(P, st.cc, m.ent0 + 4, np0, m.ent1 + 4, has1 ? np1 : 0u);
   QC_PHASE(0);
   const bool ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
   const bool ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
@@ -269,13 +283,15 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   QC_PHASE(3);
   if (n0 == 0u || n1 == 0u) return false;
-  if (threadIdx.x == 0) {
-    m.np[0] = pages_for(n0, kc);
-    m.np[1] = has1 ? pages_for(n1, kc) : 0u;
-    bool ok = alloc_pages_t0(P, st.cc, m.ent0 + 4, m.np[0]);
-    if (ok && has1) ok = alloc_pages_t0(P, st.cc, m.ent1 + 4, m.np[1]);
-    if (!ok) atomicOr(&ctl->err, (unsigned)E_OOM);
-    m.oom[0] = !ok;
+  if (threadIdx.x < 32u) {
+    const uint32_t q0 = pages_for(n0, kc), q1 = has1 ? pages_for(n1, kc) : 0u;
+    const bool ok = alloc_pages_warp(P, st.cc, m.ent0 + 4, q0, m.ent1 + 4, q1);
+    if (threadIdx.x == 0) {
+      m.np[0] = q0;
+      m.np[1] = q1;
+      if (!ok) atomicOr(&ctl->err, (unsigned)E_OOM);
+      m.oom[0] = !ok;
+    }
   }
   __syncthreads();
   if (m.oom[0]) return false;
@@ -296,8 +312,12 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3) k_gate(const __gr
   __shared__ long long s_ph[7];
   __shared__ int s_oom;
   __shared__ uint32_t s_np[2];
+  __shared__ uint32_t s_cache[kCacheCap];
+  __shared__ uint32_t s_cache_n;
   const GateSmem m = gate_smem(smem, L.P.kc, L.P.dir_words, s_ph, &s_oom, s_np);
   GateCta st;
+  st.cc.ids = s_cache;
+  st.cc.n = &s_cache_n;
   cta_begin(L.P, st, L.prof, s_ph);
   const uint32_t S = gate_bits(L);
   for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x)
@@ -314,8 +334,12 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3)
   __shared__ long long s_ph[7];
   __shared__ int s_oom;
   __shared__ uint32_t s_np[2];
+  __shared__ uint32_t s_cache[kCacheCap];
+  __shared__ uint32_t s_cache_n;
   const GateSmem m = gate_smem(smem, jobs[0].L.P.kc, jobs[0].L.P.dir_words, s_ph, &s_oom, s_np);
   GateCta st;
+  st.cc.ids = s_cache;
+  st.cc.n = &s_cache_n;
   int cur = -1;
   uint32_t S = 64;
   for (unsigned long long g = blockIdx.x; g < total; g += gridDim.x) {
@@ -420,13 +444,20 @@ __global__ void __launch_bounds__(kThreads) k_init_chunk0(const Pool P, unsigned
   __syncthreads();
   int pp = 0;
   const uint32_t n0 = encode_block<VPT>(tile, kc, 64u, -1, kDefaultModes, img, imgcap(kc), s, pp, &P.ctl->err);
-  if (threadIdx.x == 0) {
-    s_np = pages_for(n0, kc);
+  __shared__ uint32_t s_cache_n;
+  if (threadIdx.x < 32u) {
+    const uint32_t q0 = pages_for(n0, kc);
+    if (threadIdx.x == 0) s_cache_n = 0u;
+    __syncwarp();
     CtaCache cc;
-    cc.ids = nullptr;
-    cc.n = 0;
-    s_ok = n0 != 0u && alloc_pages_t0(P, cc, pages, s_np);
-    if (!s_ok) atomicOr(&P.ctl->err, (unsigned)E_OOM);
+    cc.ids = nullptr;  // empty cache: every page comes from the stack
+    cc.n = &s_cache_n;
+    const bool ok = n0 != 0u && alloc_pages_warp(P, cc, pages, q0, nullptr, 0u);
+    if (threadIdx.x == 0) {
+      s_np = q0;
+      s_ok = ok;
+      if (!ok) atomicOr(&P.ctl->err, (unsigned)E_OOM);
+    }
   }
   __syncthreads();
   if (!s_ok) return;

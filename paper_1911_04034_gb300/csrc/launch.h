@@ -7,6 +7,8 @@
 
 namespace qc {
 
+constexpr int kMaxRuns = 6;
+
 // One gate on the compressed state.
 struct GateLaunch {
   Pool P;
@@ -15,6 +17,9 @@ struct GateLaunch {
   unsigned long long items;      // work items (chunk pairs)
   unsigned long long nact;       // active chunks (in-chunk gates pair them up)
   unsigned long long free_mask;  // chunk-index bits enumerated by the item counter
+  unsigned long long run_mask[kMaxRuns];  // free_mask as runs of contiguous bits ...
+  uint32_t run_shift[kMaxRuns];           // ... each receiving the counter's bits shifted up by run_shift
+  int nruns;                              // -1: more runs than kMaxRuns (deposit bit by bit)
   unsigned long long hi_vals;    // control values on chunk-index bits
   unsigned long long pair_bit;   // chunk-index bit of the target (cross-chunk gates), else 0
   uint32_t lo_mask, lo_vals;     // controls inside a chunk
