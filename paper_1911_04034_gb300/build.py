@@ -18,6 +18,8 @@ HEADERS = ["device.cuh", "launch.h"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-O2", "-I" + os.path.join(ROOT, "include")]
+# extra definitions for tuning builds, e.g. QC_NVCC_DEFS="-DQC_GATE_MIN_CTAS=2"
+FLAGS += os.environ.get("QC_NVCC_DEFS", "").split()
 
 
 def _stale() -> bool:

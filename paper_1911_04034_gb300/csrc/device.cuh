@@ -212,10 +212,13 @@ __device__ __forceinline__ void block_scan2(uint32_t v, uint32_t v2, uint32_t fo
 // (M1 | M2, (V1 & ~M2) | V2) is associative; this is its exclusive scan over the CTA
 // (identity (0, 0): the first value's predecessor is 0), one barrier.  Returns V.
 __device__ __forceinline__ uint32_t block_lead_scan(uint32_t M, uint32_t V, ScanSmem& s, int& pp) {
+  constexpr uint32_t kFull = 0xFFFFFF00u;  // all three leading bytes set: earlier runs no longer matter
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t im = M, iv = V;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
+    // lanes below d already cover the whole warp prefix; full lanes cannot change
+    if (__all_sync(0xffffffffu, im == kFull || lane < d)) break;
     const uint32_t um = __shfl_up_sync(0xffffffffu, im, d), uv = __shfl_up_sync(0xffffffffu, iv, d);
     if (lane >= d) {
       iv = (uv & ~im) | iv;
@@ -229,10 +232,12 @@ __device__ __forceinline__ uint32_t block_lead_scan(uint32_t M, uint32_t V, Scan
     s.wlv[pp][w] = iv;
   }
   __syncthreads();
-  uint32_t pv = 0;
-#pragma unroll
-  for (int i = 0; i < kWarps; ++i)
-    if (i < w) pv = (pv & ~s.wlm[pp][i]) | s.wlv[pp][i];
+  // earlier warps, nearest first, until every leading byte is set
+  uint32_t pm = 0u, pv = 0u;
+  for (int i = w - 1; i >= 0 && pm != kFull; --i) {
+    pv |= s.wlv[pp][i] & ~pm;
+    pm |= s.wlm[pp][i];
+  }
   pp ^= 1;
   return (pv & ~em) | ev;
 }
@@ -635,49 +640,38 @@ do {                                                        \
 }
 
 
-// pack_xor for S <= 32: every residual is at most 32 bits of the value's high word h,
-// so a value touches at most two 32-bit units of the stream.
+// pack_xor for S <= 32: every residual is at most 32 bits of the value's high word h.
+// The thread fills 32-bit stream units in order in a register; a completed unit is
+// stored (the first one with atomicOr: the previous thread may own its leading bits),
+// the unfinished last one is ORed in (the next thread owns its trailing bits).
 template <int VPT>
 __device__ __forceinline__ void pack_xor32(uint8_t* img, uint32_t nv, uint32_t j0, uint32_t o0, const uint32_t h[VPT],
                                            const uint32_t c[VPT], const uint32_t r[VPT]) {
   uint32_t* codes32 = reinterpret_cast<uint32_t*>(img + 16);
   const uint32_t cw = code_word<VPT>(c, j0, nv);
-  uint32_t oend = o0;
-#pragma unroll
-  for (int k = 0; k < VPT; ++k)
-    if (j0 + k < nv) oend += r[k];
   if (j0 < nv && cw) atomicOr(&codes32[j0 >> 4], cw);
-  if (oend > o0) {
-    uint32_t* m32 = reinterpret_cast<uint32_t*>(img + 16 + code_bytes(nv));
-    const uint32_t qf = o0 >> 5, ql = (oend - 1u) >> 5;
-    uint32_t qb = qf, w0 = 0, w1 = 0, o = o0;
-#define QC_FLUSH(q, v)                                        \
-do {                                                        \
-  if ((q) <= ql && (v) != 0u) {                             \
-    if ((q) == qf || (q) == ql) atomicOr(&m32[(q) ^ 1u], (v)); \
-    else m32[(q) ^ 1u] = (v);                               \
-  }                                                         \
-} while (0)
+  uint32_t* m32 = reinterpret_cast<uint32_t*>(img + 16 + code_bytes(nv));
+  uint32_t q = o0 >> 5, fill = o0 & 31u, cur = 0u;
+  bool first = true;
 #pragma unroll
-    for (int k = 0; k < VPT; ++k) {
-      if (j0 + k < nv && r[k]) {
-        const uint32_t q = o >> 5, sh = o & 31u;
-        if (qb < q) {  // residuals are at most 32 bits: the window moves by one unit at most
-          QC_FLUSH(qb, w0);
-          w0 = w1;
-          w1 = 0;
-          ++qb;
-        }
-        const uint32_t x = h[k] << (8u * c[k]);
-        w0 |= x >> sh;
-        w1 |= __funnelshift_r(0u, x, sh);
-        o += r[k];
+  for (int k = 0; k < VPT; ++k) {
+    if (j0 + k < nv) {
+      const uint32_t f = h[k] << (8u * c[k]);  // the residual in the top r bits, zeros below
+      cur |= f >> fill;
+      const uint32_t nf = fill + r[k];
+      if (nf >= 32u) {
+        if (first) atomicOr(&m32[q ^ 1u], cur);
+        else m32[q ^ 1u] = cur;
+        first = false;
+        ++q;
+        cur = __funnelshift_r(0u, f, fill);  // the residual's bits past the unit
+        fill = nf - 32u;
+      } else {
+        fill = nf;
       }
     }
-    QC_FLUSH(qb, w0);
-    QC_FLUSH(qb + 1u, w1);
-#undef QC_FLUSH
   }
+  if (fill > 0u && cur) atomicOr(&m32[q ^ 1u], cur);
 }
 
 // Leading identical bytes of two high words (values whose low words are zero), capped at 3.
@@ -772,9 +766,12 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
       }
     }
   }
-  uint32_t total, f_or, f_and, o0, o2, total2;
-  block_scan2(sum, sum2, nz ? 1u : 0u, (cst ? 1u : 0u) | (gtop ? 2u : 0u), s, pp, &o0, &o2, &total, &total2, &f_or,
-              &f_and);
+  uint32_t total, f_or, f_and, o0, o2 = 0, total2 = 0;
+  if (want_split)
+    block_scan2(sum, sum2, nz ? 1u : 0u, (cst ? 1u : 0u) | (gtop ? 2u : 0u), s, pp, &o0, &o2, &total, &total2, &f_or,
+                &f_and);
+  else
+    o0 = block_scan(sum, nz ? 1u : 0u, (cst ? 1u : 0u) | (gtop ? 2u : 0u), s, pp, &total, &f_or, &f_and);
   const bool allzero = (f_or & 1u) == 0u;
   const bool allconst = (f_and & 1u) != 0u;
   // 4. smallest power-of-two period P (amplitudes), 2 <= P < 2^kc: the chunk is

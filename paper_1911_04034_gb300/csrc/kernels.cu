@@ -11,6 +11,12 @@
 // others   initialisation, codec entry points, readout and the uncompressed path.
 #include "launch.h"
 
+// Resident CTAs per SM that the fused kernel's register budget is sized for (the grid
+// follows the occupancy the build achieves).
+#ifndef QC_GATE_MIN_CTAS
+#define QC_GATE_MIN_CTAS 3
+#endif
+
 namespace qc {
 
 int vpt_for(int kc) {
@@ -26,7 +32,7 @@ __host__ __device__ __forceinline__ uint32_t pagelist_words(int kc) { return (ma
 // past the end of a residual stream.
 __host__ __device__ __forceinline__ uint32_t imgbuf(int kc) { return imgcap(kc) + 16u; }
 size_t gate_smem_bytes(int kc) {
-  return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgbuf(kc)) + 2 * size_t(dir_stride(kc)) +
+  return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgbuf(kc)) + 4 * size_t(dir_stride(kc)) +
          round16(sizeof(ScanSmem));
 }
 size_t codec_smem_bytes(int kc) {
@@ -39,7 +45,8 @@ size_t codec_smem_bytes(int kc) {
 struct GateSmem {
   uint64_t *tile0, *tile1;
   uint8_t *img0, *img1;
-  uint32_t *ent0, *ent1;  // copies of the two directory entries (header, page ids or image)
+  uint32_t* ent[2][2];    // two sets of copies of the two directory entries (header, page
+                          // ids or image): the current item's and the next item's
   ScanSmem* s;
   long long* ph;          // per-phase cycles, [6] = last clock (profiling)
   int* oom;
@@ -50,7 +57,21 @@ struct GateCta {
   long long dE;
   unsigned long long rd, wr;
   int pp;
+  int cur;                        // directory-entry buffer set of the current item
+  unsigned long long next_item;   // item whose entries were prefetched into set cur ^ 1
 };
+
+// Asynchronous 16-byte global -> shared copies (the next item's directory entries).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// Pulls one page of a later item's image into L2 (no data returned to the SM).
+__device__ __forceinline__ void prefetch_l2_page(const void* gmem) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"((uint32_t)kPage) : "memory");
+}
 
 __device__ __forceinline__ GateSmem gate_smem(uint8_t* smem, int kc, uint32_t dir_words, long long* ph, int* oom,
                                                uint32_t* np) {
@@ -59,9 +80,11 @@ __device__ __forceinline__ GateSmem gate_smem(uint8_t* smem, int kc, uint32_t di
   m.tile1 = m.tile0 + tile_words(kc);
   m.img0 = reinterpret_cast<uint8_t*>(m.tile1 + tile_words(kc));
   m.img1 = m.img0 + imgbuf(kc);
-  m.ent0 = reinterpret_cast<uint32_t*>(m.img1 + imgbuf(kc));
-  m.ent1 = m.ent0 + dir_words;
-  m.s = reinterpret_cast<ScanSmem*>(m.ent1 + dir_words);
+  m.ent[0][0] = reinterpret_cast<uint32_t*>(m.img1 + imgbuf(kc));
+  m.ent[0][1] = m.ent[0][0] + dir_words;
+  m.ent[1][0] = m.ent[0][1] + dir_words;
+  m.ent[1][1] = m.ent[1][0] + dir_words;
+  m.s = reinterpret_cast<ScanSmem*>(m.ent[1][1] + dir_words);
   m.ph = ph;
   m.oom = oom;
   m.np = np;
@@ -80,6 +103,8 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
   st.dE = 0;
   st.rd = st.wr = 0;
   st.pp = 0;
+  st.cur = 0;
+  st.next_item = ~0ull;
   if (prof && threadIdx.x == 0) {
     for (int k = 0; k < 6; ++k) ph[k] = 0;
     ph[6] = clock64();
@@ -119,7 +144,9 @@ __device__ __forceinline__ unsigned long long item_chunk(const GateLaunch& L, un
 
 // One work item (two chunks) of a gate: stage, decode, apply, encode, commit.
 // Returns false if the simulator's error word is set (nothing more to do for it).
-template <int VPT>
+// PREF: the CTA's next item is item + gridDim.x of the same gate; its directory
+// entries are fetched asynchronously during this item and its pages pulled into L2.
+template <int VPT, bool PREF>
 __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long long item, uint32_t S,
                                           const GateSmem& m, GateCta& st) {
   const int kc = L.P.kc;
@@ -134,8 +161,15 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     m.ph[k] += now_ - m.ph[6];          \
     m.ph[6] = now_;                     \
   }
-  // one barrier that also broadcasts thread 0's view of the error word
+  // one barrier that also broadcasts thread 0's view of the error word (and publishes
+  // the entries prefetched during the previous item)
+  if (PREF) cp_async_wait_all();
   if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned int*)&ctl->err) != 0u)) return false;
+  const bool have_entries = PREF && st.next_item == item;
+  if (PREF && st.next_item != ~0ull) st.cur ^= 1;
+  st.next_item = ~0ull;
+  uint32_t* const ent0 = m.ent[st.cur][0];
+  uint32_t* const ent1 = m.ent[st.cur][1];
   unsigned long long c0, c1;
   bool has1;
   if (L.pair) {
@@ -148,17 +182,45 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     has1 = k0 + 1 < L.nact;
     c1 = has1 ? (item_chunk(L, k0 + 1) | L.hi_vals) : 0ull;
   }
-  // stage 1: both directory entries (warp 0 and warp 1)
-  if (threadIdx.x < 32u) {
-    const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, c0));
-    for (uint32_t i = threadIdx.x; i < dw4; i += 32u) reinterpret_cast<uint4*>(m.ent0)[i] = src[i];
-  } else if (threadIdx.x < 64u && has1) {
-    const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, c1));
-    for (uint32_t i = threadIdx.x - 32u; i < dw4; i += 32u) reinterpret_cast<uint4*>(m.ent1)[i] = src[i];
+  // stage 1: both directory entries (warp 0 and warp 1), unless prefetched
+  if (!have_entries) {
+    if (threadIdx.x < 32u) {
+      const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, c0));
+      for (uint32_t i = threadIdx.x; i < dw4; i += 32u) reinterpret_cast<uint4*>(ent0)[i] = src[i];
+    } else if (threadIdx.x < 64u && has1) {
+      const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, c1));
+      for (uint32_t i = threadIdx.x - 32u; i < dw4; i += 32u) reinterpret_cast<uint4*>(ent1)[i] = src[i];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const uint32_t np0 = m.ent0[1], np1 = has1 ? m.ent1[1] : 0u;
-  const uint32_t b0 = m.ent0[0], b1 = has1 ? m.ent1[0] : 0u;
+  // the next item's entries (asynchronously, into the other set); no other CTA writes
+  // them, and this item touches only its own chunks
+  unsigned long long nc0 = 0, nc1 = 0;
+  bool nhas1 = false;
+  if (PREF && item + gridDim.x < L.items) {
+    const unsigned long long nx = item + gridDim.x;
+    if (L.pair) {
+      nc0 = item_chunk(L, nx) | L.hi_vals;
+      nc1 = nc0 | L.pair_bit;
+      nhas1 = true;
+    } else {
+      nc0 = item_chunk(L, 2ull * nx) | L.hi_vals;
+      nhas1 = 2ull * nx + 1 < L.nact;
+      nc1 = nhas1 ? (item_chunk(L, 2ull * nx + 1) | L.hi_vals) : 0ull;
+    }
+    if (threadIdx.x < 32u) {
+      const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, nc0));
+      for (uint32_t i = threadIdx.x; i < dw4; i += 32u) cp_async16(reinterpret_cast<uint4*>(m.ent[st.cur ^ 1][0]) + i, src + i);
+    } else if (threadIdx.x < 64u && nhas1) {
+      const uint4* src = reinterpret_cast<const uint4*>(dir_entry(P, nc1));
+      for (uint32_t i = threadIdx.x - 32u; i < dw4; i += 32u)
+        cp_async16(reinterpret_cast<uint4*>(m.ent[st.cur ^ 1][1]) + i, src + i);
+    }
+    cp_async_commit();
+    st.next_item = nx;
+  }
+  const uint32_t np0 = ent0[1], np1 = has1 ? ent1[1] : 0u;
+  const uint32_t b0 = ent0[0], b1 = has1 ? ent1[0] : 0u;
   if (b0 > cap || b1 > cap || np0 > max_pages(kc) || np1 > max_pages(kc) || (np0 == 0u && b0 > inline_cap(kc)) ||
       (np1 == 0u && b1 > inline_cap(kc)) || (b0 & 15u) || (b1 & 15u)) {
     if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
@@ -166,8 +228,8 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   // An all-zero chunk maps to an all-zero chunk under any gate (signed zeros are
   // stored as +0), and its image does not depend on the bound: skip it.
-  const bool z0 = np0 == 0 && b0 == 16u && m.ent0[4] == 0u;
-  const bool z1 = !has1 || (np1 == 0 && b1 == 16u && m.ent1[4] == 0u);
+  const bool z0 = np0 == 0 && b0 == 16u && ent0[4] == 0u;
+  const bool z1 = !has1 || (np1 == 0 && b1 == 16u && ent1[4] == 0u);
   st.rd += b0 + b1;
   if (z0 && z1) {
     QC_PHASE(5);
@@ -177,13 +239,13 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   // with no in-chunk controls: every pair sees the same inputs, so one pair gives
   // both output chunks, which are constant again.
   if (L.pair && L.lo_mask == 0u && inline_cap(kc) >= 32u && np0 == 0u && np1 == 0u &&
-      (z0 || (m.ent0[4] & 0xffu) == M_CONST) && (z1 || (m.ent1[4] & 0xffu) == M_CONST)) {
+      (z0 || (ent0[4] & 0xffu) == M_CONST) && (z1 || (ent1[4] & 0xffu) == M_CONST)) {
     if (threadIdx.x == 0) {
       double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
-      if (!z0) a = make_double2(__longlong_as_double(((const long long*)(m.ent0 + 8))[0]),
-                                __longlong_as_double(((const long long*)(m.ent0 + 8))[1]));
-      if (!z1) b = make_double2(__longlong_as_double(((const long long*)(m.ent1 + 8))[0]),
-                                __longlong_as_double(((const long long*)(m.ent1 + 8))[1]));
+      if (!z0) a = make_double2(__longlong_as_double(((const long long*)(ent0 + 8))[0]),
+                                __longlong_as_double(((const long long*)(ent0 + 8))[1]));
+      if (!z1) b = make_double2(__longlong_as_double(((const long long*)(ent1 + 8))[0]),
+                                __longlong_as_double(((const long long*)(ent1 + 8))[1]));
       apply_pair(L.g, a, b);
       uint32_t h0[8], h1[8];
       const uint32_t n0 = const_image((uint64_t)__double_as_longlong(a.x), (uint64_t)__double_as_longlong(a.y), S, h0);
@@ -206,25 +268,39 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     QC_PHASE(5);
     return true;
   }
-  // stage 2: both images in one pass (inline ones from the entry copies)
+  // stage 2: both images in one pass (inline ones from the entry copies); page data is
+  // copied asynchronously, so every copy of the thread is in flight at once
   {
     const uint32_t u0 = b0 >> 4, u1 = b1 >> 4;
     constexpr uint32_t upp = kPage / 16;
     for (uint32_t u = threadIdx.x; u < u0 + u1; u += kThreads) {
       const bool second = u >= u0;
       const uint32_t uu = second ? u - u0 : u;
-      const uint32_t* ent = second ? m.ent1 : m.ent0;
-      uint4 v;
-      if ((second ? np1 : np0) == 0u) v = reinterpret_cast<const uint4*>(ent + 4)[uu];
-      else v = __ldcs(reinterpret_cast<const uint4*>(P.pages + (unsigned long long)ent[4 + uu / upp] * kPage) + (uu % upp));
-      reinterpret_cast<uint4*>(second ? m.img1 : m.img0)[uu] = v;
+      const uint32_t* ent = second ? ent1 : ent0;
+      uint4* dst = reinterpret_cast<uint4*>(second ? m.img1 : m.img0) + uu;
+      if ((second ? np1 : np0) == 0u) *dst = reinterpret_cast<const uint4*>(ent + 4)[uu];
+      else cp_async16(dst, reinterpret_cast<const uint4*>(P.pages + (unsigned long long)ent[4 + uu / upp] * kPage) + (uu % upp));
     }
+    cp_async_commit();
+    cp_async_wait_all();
   }
   __syncthreads();
-  if (threadIdx.x < 32u) free_pages_warp(P, st.cc, m.ent0 + 4, np0, m.ent1 + 4, has1 ? np1 : 0u);
+  if (threadIdx.x < 32u) free_pages_warp(P, st.cc, ent0 + 4, np0, ent1 + 4, has1 ? np1 : 0u);
   QC_PHASE(0);
   const bool ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
   const bool ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
+  // the next item's pages into L2: warp 0 for its first chunk, warp 1 for its second
+  // (each warp waits only for the entry copies it issued itself)
+  if (PREF && st.next_item != ~0ull && threadIdx.x < 64u && (threadIdx.x < 32u || nhas1)) {
+    cp_async_wait_all();
+    __syncwarp();
+    const uint32_t* e = m.ent[st.cur ^ 1][threadIdx.x >> 5];
+    const uint32_t q = min(e[1], max_pages(kc));
+    for (uint32_t k = threadIdx.x & 31u; k < q; k += 32u) {
+      const uint32_t pid = e[4 + k];
+      if (pid < P.npages) prefetch_l2_page(P.pages + (unsigned long long)pid * kPage);
+    }
+  }
   QC_PHASE(1);
   if (!ok0 || !ok1) {
     if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
@@ -285,7 +361,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   if (n0 == 0u || n1 == 0u) return false;
   if (threadIdx.x < 32u) {
     const uint32_t q0 = pages_for(n0, kc), q1 = has1 ? pages_for(n1, kc) : 0u;
-    const bool ok = alloc_pages_warp(P, st.cc, m.ent0 + 4, q0, m.ent1 + 4, q1);
+    const bool ok = alloc_pages_warp(P, st.cc, ent0 + 4, q0, ent1 + 4, q1);
     if (threadIdx.x == 0) {
       m.np[0] = q0;
       m.np[1] = q1;
@@ -295,8 +371,8 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   __syncthreads();
   if (m.oom[0]) return false;
-  store_image_block(P, c0, m.img0, n0, m.ent0 + 4, m.np[0]);
-  if (has1) store_image_block(P, c1, m.img1, n1, m.ent1 + 4, m.np[1]);
+  store_image_block(P, c0, m.img0, n0, ent0 + 4, m.np[0]);
+  if (has1) store_image_block(P, c1, m.img1, n1, ent1 + 4, m.np[1]);
   st.dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
   st.wr += n0 + (has1 ? n1 : 0u);
   __syncthreads();
@@ -307,7 +383,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
 }
 
 template <int VPT>
-__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3) k_gate(const __grid_constant__ GateLaunch L) {
+__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_gate(const __grid_constant__ GateLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ long long s_ph[7];
   __shared__ int s_oom;
@@ -321,14 +397,15 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3) k_gate(const __gr
   cta_begin(L.P, st, L.prof, s_ph);
   const uint32_t S = gate_bits(L);
   for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x)
-    if (!gate_item<VPT>(L, item, S, m, st)) break;
+    if (!gate_item<VPT, true>(L, item, S, m, st)) break;
+  cp_async_wait_all();  // no copy may still target shared memory at exit
   cta_end(L, st, s_ph);
 }
 
 // Many simulators in one launch: job j is one gate of one simulator, and its work
 // items are the global items [begin_j, begin_{j+1}).  All simulators share chunk_log2.
 template <int VPT>
-__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3)
+__global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
     k_gate_batch(const BatchJob* __restrict__ jobs, int njobs, unsigned long long total) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ long long s_ph[7];
@@ -355,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : 3)
       cta_begin(jobs[cur].L.P, st, jobs[cur].L.prof, s_ph);
       S = gate_bits(jobs[cur].L);
     }
-    gate_item<VPT>(jobs[cur].L, g - jobs[cur].begin, S, m, st);
+    gate_item<VPT, false>(jobs[cur].L, g - jobs[cur].begin, S, m, st);
   }
   if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
 }

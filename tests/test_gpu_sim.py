@@ -42,6 +42,15 @@ def stats_match(gs, os_):
     assert gs["chunks_by_mode"][:6] == os_["chunks_by_mode"][:6]
 
 
+@pytest.mark.parametrize("kc", [0, 1, 4, 7, 8, 9, 10, 11])
+def test_initial_state_images_match_oracle(kc):
+    """|0...0>: chunk 0 holds amplitude 1 coded losslessly, every other chunk is ZERO."""
+    n = max(kc + 2, 6)
+    gpu = qc().Sim(n, n, 1e-4, chunk_log2=kc, budget=16 << n, pool_bytes=(32 << n) + (16 << 20))
+    orc = O.CSim(n, n, kc, 1e-4, 16 << n)
+    assert images_equal(gpu, orc) == []
+
+
 def test_grover_12q_every_gate_bit_exact():
     """Grover search, 12 qubits, one marked item, 50 iterations; blocks of 2^8
     amplitudes; lossless, then lossy at 1e-4 once the budget (raw/4) is reached."""
