@@ -341,6 +341,60 @@ def run_batch(args) -> dict:
             "min_fidelity_lb_sum": lb, "mean_compression_ratio": float(np.mean(ratio))}
 
 
+def run_qaoa34(args) -> dict:
+    """QAOA p = 2 MaxCut on a seeded random 3-regular graph (51 edges), 34 qubits: the
+    raw state (256 GiB) does not fit, so the compressed state has to stay inside a
+    180 GB page pool.  Bound 1e-4 reached through the guarded ladder (before each gate
+    the smallest level 1e-5 / 1e-4 whose worst case fits 0.9 x 180 GB).  Timed: every
+    gate after the Hadamard layer and `warmup` further gates, on the device."""
+    import torch
+
+    from paper_1911_04034_gb300 import qcsim
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, kc = 34, args.kc
+    pool = 180 * 10**9
+    gates, edges = Cc.qaoa_maxcut(n, 2, 3, seed=SEED)
+    stream = torch.cuda.Stream()
+    sim = qcsim.Sim(n, 20, args.eps, chunk_log2=kc, budget=pool, ladder=2, pool_bytes=pool, stream=stream)
+    w = n + args.warmup
+    sim.apply_circuit(gates[:w])
+    st0 = sim.stats()
+    timed = gates[w:]
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    sim.set_timing(1)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.apply_circuit(timed)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    tm = sim.timing()
+    st = sim.stats()
+    updates = st["amp_updates"] - st0["amp_updates"]
+    kernel_ms = tm["gate_kernel_ms"] / max(1, tm["launches"])
+    bpl = (tm["bytes_read"] + tm["bytes_written"]) / max(1, tm["launches"])
+    pk = peaks().get("hbm_gbs")
+    return {"metric": METRIC, "value": updates / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": len(timed),
+            "warmup": args.warmup, "ms_per_step": ms / len(timed), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"QAOA p=2 MaxCut, random 3-regular graph ({len(edges)} edges), {n} qubits, "
+                                   f"eps {args.eps} via the guarded ladder, page pool 180 GB; gates {w}-{len(gates) - 1} timed",
+                       "n_qubits": n, "chunk_log2": kc, "block_log2": 20, "gates": len(gates), "pool_bytes": pool,
+                       "raw_bytes": 16 << n},
+            "max_encoded_gb": st["max_encoded_bytes"] / 1e9, "peak_pages_gb": st["peak_pages_bytes"] / 1e9,
+            "device_gb": st["device_bytes"] / 1e9, "compression_ratio": st["ratio"], "min_compression_ratio": st["min_ratio"],
+            "eps_final": st["eps_current"], "eps_switch_gate": st["eps_switch_gate"],
+            "fidelity_lb_sum": st["fidelity_lb_sum"], "fidelity_lb_prod": st["fidelity_lb_prod"],
+            "roofline": {"bound": "hbm", "achieved": bpl / (kernel_ms * 1e-3) / 1e9 if kernel_ms else None, "peak": pk,
+                         "unit": "GB/s", "frac": (bpl / (kernel_ms * 1e-3) / 1e9 / pk) if (pk and kernel_ms) else None,
+                         "traffic": None, "kernel": "k_gate", "kernel_ms_avg": kernel_ms},
+            "gpu_launches": 2 * tm["launches"], "clocks": clk}
+
+
 def cpu_sample(eps: float, n: int = 20, warm_layers: int = 3, timed_layers: int = 2, budget_s: float = 25.0):
     """The oracle on the host: same circuit family on a 4 x 5 grid (20 qubits), same
     bound and budget rule; times whole layers after a warm-up until budget_s."""
@@ -419,8 +473,9 @@ def main():
     ap.add_argument("--no-sv", action="store_true", help="skip the uncompressed comparator and fidelity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="also count SM cycles per phase of the fused kernel")
-    ap.add_argument("--workload", default="rcs30", choices=["rcs30", "batch"],
-                    help="rcs30: the 30-qubit random circuit (default); batch: 256 circuits of 14-24 qubits")
+    ap.add_argument("--workload", default="rcs30", choices=["rcs30", "batch", "qaoa34"],
+                    help="rcs30: the 30-qubit random circuit (default); batch: 256 circuits of 14-24 qubits; "
+                         "qaoa34: 34-qubit QAOA in a 180 GB pool")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)
@@ -433,6 +488,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload == "batch" and args.impl == "gpu":
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.workload == "qaoa34" and args.impl == "gpu":
+        print(json.dumps(run_qaoa34(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args)

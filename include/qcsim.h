@@ -106,10 +106,16 @@ sim_status sim_create(int n_qubits, int block_log2, double err_bound, sim_t** ou
  * block); budget in bytes (> 0): the memory the compressed state may use, against
  * which the controller compares E + two blocks with threshold floor(tau * budget),
  * tau in (0, 1]; ladder 0 = lossless then err_bound, 1 = the paper's ladder 1e-5,
- * 1e-4, ... up to err_bound, one level per gate (Section 3.7).  pool_bytes is the page
- * arena actually allocated (0: budget + 1/8 for page rounding + the per-CTA page
- * caches).  The controller acts before a gate, so one gate can grow the state past
- * the threshold; if the images then exceed the arena the gate fails with SIM_ERR_OOM. */
+ * 1e-4, ... up to err_bound, one level per gate (Section 3.7); 2 = the same levels,
+ * guarded: before each gate the smallest level (never below the current one) at
+ * which the largest images the encoder can write on every chunk the gate rewrites
+ * still keep the compressed size within floor(tau * budget) -- a gate that rewrites
+ * every chunk ends with at most (chunks x largest image) bytes, any other gate grows
+ * the size by at most (rewritten chunks x largest image); if no level satisfies that,
+ * err_bound.  pool_bytes is the page arena actually allocated (0: budget + 1/8 for
+ * page rounding + the per-CTA page caches).  With ladders 0 and 1 the controller acts
+ * before a gate, so one gate can grow the state past the threshold; if the images
+ * then exceed the arena the gate fails with SIM_ERR_OOM. */
 sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double err_bound, uint64_t budget,
                          double tau, int ladder, uint64_t pool_bytes, sim_t** out);
 

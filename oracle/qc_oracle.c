@@ -746,7 +746,7 @@ orc_csim* orc_csim_create(int n, int block_log2, int chunk_log2, double eps_max,
   static const double paper_levels[5] = {1e-5, 1e-4, 1e-3, 1e-2, 1e-1};
   s->nlevels = 0;
   if (eps_max > 0.0) {
-    if (ladder == 1)
+    if (ladder >= 1)
       for (int k = 0; k < 5; ++k) if (paper_levels[k] < eps_max) s->levels[s->nlevels++] = paper_levels[k];
     s->levels[s->nlevels++] = eps_max;
   }
@@ -778,12 +778,40 @@ void orc_csim_destroy(orc_csim* s) {
  * image bytes and W two decompressed blocks.  If nbBytes exceeds floor(tau * budget)
  * the bound is relaxed: the jump ladder goes from lossless to eps_max at once, the
  * paper's ladder steps one level per gate.  The bound never tightens. */
-static void controller(orc_csim* s) {
-  if (s->nlevels == 0) return;
-  if (s->E + s->inflight <= s->thresh) return;
-  if (s->level >= s->nlevels) return;
-  if (s->ladder == 1) s->level += 1;
-  else s->level = s->nlevels;
+/* The largest image a chunk can take at S significant bits: every value coded with
+ * the full S bits (2-bit code each), or the verbatim values if that is smaller. */
+static uint64_t max_level_image(int kc, int S) {
+  uint64_t N = (uint64_t)2 << kc;
+  uint64_t codes = ((N + 3) / 4 + 15) / 16 * 16;
+  uint64_t resid = (S * N + 127) / 128 * 16;
+  uint64_t stream = 16 + codes + resid, raw = 16 + 8 * N;
+  return stream < raw ? stream : raw;
+}
+
+/* Section 3.7, before gate g (touched = chunks the gate rewrites).  Ladders 0 and 1:
+ * relax when E + two decompressed blocks (Eq. totalnbBytes) exceed floor(tau budget).
+ * Ladder 2 reads the rule for a device that rewrites all of a gate's chunks at once:
+ * take the smallest level, never below the current one, whose worst case still fits
+ * -- the gate ends with at most touched x (largest image) bytes if it rewrites every
+ * chunk, else with at most E + touched x (largest image). */
+static void controller(orc_csim* s, uint64_t touched) {
+  if (s->nlevels == 0 || s->level >= s->nlevels) return;
+  int lvl = s->level;
+  if (s->ladder == 2) {
+    lvl = s->nlevels;
+    for (int l = s->level; l < s->nlevels; ++l) {
+      uint64_t worst = touched * max_level_image(s->kc, l == 0 ? 64 : orc_sig_bits(s->levels[l - 1]));
+      if ((touched >= s->nchunks ? worst : s->E + worst) <= s->thresh) {
+        lvl = l;
+        break;
+      }
+    }
+  } else {
+    if (s->E + s->inflight <= s->thresh) return;
+    lvl = s->ladder == 1 ? s->level + 1 : s->nlevels;
+  }
+  if (lvl == s->level) return;
+  s->level = lvl;
   s->S_cur = orc_sig_bits(s->levels[s->level - 1]);
   if (s->switch_gate < 0) s->switch_gate = (int64_t)s->gates;
 }
@@ -794,8 +822,8 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
   if (rc) return rc;
   int kc = s->kc, t = g->target;
   size_t A = (size_t)1 << kc, N = 2 * A;
-  controller(s);
   uint64_t hi_mask = g->ctrl_mask >> kc, hi_vals = g->ctrl_vals >> kc;
+  controller(s, s->nchunks >> __builtin_popcountll(hi_mask & (s->nchunks - 1)));
   uint64_t lo_mask = g->ctrl_mask & (A - 1), lo_vals = g->ctrl_vals & (A - 1);
   uint64_t* x0 = (uint64_t*)malloc(N * 8);
   uint64_t* x1 = (uint64_t*)malloc(N * 8);

@@ -222,7 +222,7 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
   if (sig_bits_of(err_bound) < 0) return fail(SIM_ERR_INVALID, "err_bound must be 0 or in [2^-52, 1)");
   if (budget == 0) return fail(SIM_ERR_INVALID, "budget must be > 0");
   if (!(tau > 0.0 && tau <= 1.0)) return fail(SIM_ERR_INVALID, "tau must be in (0, 1]");
-  if (ladder != 0 && ladder != 1) return fail(SIM_ERR_INVALID, "ladder must be 0 or 1");
+  if (ladder < 0 || ladder > 2) return fail(SIM_ERR_INVALID, "ladder must be 0, 1 or 2");
 
   sim* s = new sim();
   s->n = n_qubits;
@@ -242,7 +242,7 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
   cp.nlevels = 0;
   if (err_bound > 0.0) {
     static const double paper[5] = {1e-5, 1e-4, 1e-3, 1e-2, 1e-1};
-    if (ladder == 1)
+    if (ladder >= 1)
       for (double e : paper)
         if (e < err_bound) s->level_eps[cp.nlevels++] = e;
     s->level_eps[cp.nlevels++] = err_bound;
@@ -251,6 +251,9 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
     cp.S[k] = sig_bits_of(s->level_eps[k]);
     cp.delta[k] = std::ldexp(1.0, 12 - cp.S[k]);
   }
+  cp.nchunks = s->nchunks;
+  cp.touched = s->nchunks;
+  for (int l = 0; l <= cp.nlevels; ++l) cp.maxb[l] = qc::max_level_image(s->kc, l == 0 ? 64 : cp.S[l - 1]);
 
   // page arena: the budget, 1/8 more for page rounding, and the pages that the
   // per-CTA caches may hold while a gate runs
@@ -388,6 +391,7 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
     L.nact = 1ull << popcount64(L.free_mask);
     L.items = (L.nact + 1ull) / 2ull;
   }
+  L.ctl.touched = L.nact;  // the guarded ladder bounds the gate by the chunks it rewrites
   // free_mask as runs: run i at bit p receives counter bits [q, q + len) shifted by p - q
   L.nruns = 0;
   int q = 0;
@@ -430,7 +434,7 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
     CK(cudaEventRecord(e1, s->st), "event record");
     s->ev_pending.emplace_back(e0, e1);
   }
-  CK(qc::launch_post(s->P, s->cp, s->grid, s->st), "post kernel launch");
+  CK(qc::launch_post(s->P, L.ctl, s->grid, s->st), "post kernel launch");
   s->amp_updates += L.nact << s->kc;
   return SIM_OK;
 }

@@ -76,16 +76,38 @@ struct CtlParams {
   unsigned long long thresh;    // floor(tau * budget)
   unsigned long long inflight;  // two decompressed blocks (Eq. totalnbBytes, r = 1)
   int nlevels;                  // lossy levels on the ladder (0 = lossless only)
-  int ladder;                   // 0 jump, 1 one level per gate
+  int ladder;                   // 0 jump, 1 one level per gate, 2 guarded (worst case fits)
   int S[8];                     // significant bits per level (index level-1)
   double delta[8];              // 2^EXP(eps) per level
+  unsigned long long nchunks;   // chunks of the state
+  unsigned long long touched;   // chunks the running gate rewrites (set per gate)
+  unsigned long long maxb[9];   // largest image the encoder can write at level l (0 = lossless)
 };
 
 // Section 3.7: before a gate, relax the bound if E + inflight > floor(tau * budget).
+// Guarded ladder: the smallest level (never below the current one) at which even
+// the largest images on every chunk the gate rewrites keep E within floor(tau *
+// budget): a gate rewriting every chunk ends with at most touched * maxb bytes,
+// otherwise E grows by at most touched * maxb.
 __host__ __device__ __forceinline__ int next_level(const CtlParams& p, unsigned long long E, int level) {
   if (p.nlevels == 0 || level >= p.nlevels) return level;
+  if (p.ladder == 2) {
+    for (int l = level; l < p.nlevels; ++l) {
+      const unsigned long long worst = p.touched * p.maxb[l];
+      if ((p.touched >= p.nchunks ? worst : E + worst) <= p.thresh) return l;
+    }
+    return p.nlevels;
+  }
   if (E + p.inflight <= p.thresh) return level;
   return p.ladder == 1 ? level + 1 : p.nlevels;
+}
+// Largest image of a chunk at S significant bits: STREAM with every value fully
+// explicit, or RAW if smaller (the encoder never writes more than both).
+__host__ __device__ __forceinline__ unsigned long long max_level_image(int kc, int S) {
+  const uint32_t N = 2u << kc;
+  const unsigned long long stream = 16ull + code_bytes(N) + resid_bytes((uint32_t)S * N);
+  const unsigned long long raw = 16ull + 8ull * N;
+  return stream < raw ? stream : raw;
 }
 __host__ __device__ __forceinline__ int level_bits(const CtlParams& p, int level) {
   return level == 0 ? 64 : p.S[level - 1];

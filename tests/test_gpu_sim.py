@@ -95,7 +95,7 @@ def test_random_circuit_bit_exact(eps, kc):
     assert np.array_equal(gpu.amplitudes().view(np.uint64), orc.amplitudes().view(np.uint64))
 
 
-@pytest.mark.parametrize("ladder", [0, 1])
+@pytest.mark.parametrize("ladder", [0, 1, 2])
 def test_qaoa_and_qft_bit_exact(ladder):
     n = 12
     qa, _ = Cc.qaoa_maxcut(n, 2, 3, seed=5)
@@ -108,6 +108,27 @@ def test_qaoa_and_qft_bit_exact(ladder):
         orc.apply(gates)
         assert images_equal(gpu, orc) == []
         stats_match(gpu.stats(), orc.stats())
+
+
+def test_guarded_ladder_switches_mid_run_like_the_oracle():
+    """Ladder 2 with a budget that admits the lossless stage at first: the level rises
+    when a gate's worst case (controlled gates rewrite half the chunks) stops fitting;
+    every gate's images and the controller state match the oracle's."""
+    n, kc = 14, 6
+    gates, _ = Cc.qaoa_maxcut(n, 2, 3, seed=9)
+    nch = 1 << (n - kc)
+    raw_img = 16 + 8 * (2 << kc)
+    budget = -(-nch * raw_img * 10 // 9) + 1
+    orc = O.CSim(n, n, kc, 1e-3, budget, ladder=2)
+    gpu = qc().Sim(n, n, 1e-3, chunk_log2=kc, budget=budget, ladder=2, pool_bytes=2 * (16 << n) + (64 << 20))
+    levels = []
+    for k in range(0, len(gates), 16):
+        gpu.apply_circuit(gates[k:k + 16])
+        orc.apply(gates[k:k + 16])
+        assert images_equal(gpu, orc) == []
+        stats_match(gpu.stats(), orc.stats())
+        levels.append(gpu.stats()["level"])
+    assert levels[0] == 0 and levels[-1] > 0
 
 
 def test_solution_d_mode_bit_exact():

@@ -247,6 +247,76 @@ def test_paper_ladder_one_level_per_gate():
     assert seen == [1e-5, 1e-4, 1e-3, 1e-2, 1e-2]
 
 
+def _format_max_image(kc, S):
+    """Largest image the format allows at S bits: 16-byte header, one 2-bit code per
+    value padded to 16 bytes, S residual bits per value padded to 16 bytes -- or the
+    verbatim values (RAW) when that is smaller."""
+    N = 2 << kc
+    codes = -(-(-(-N // 4)) // 16) * 16
+    resid = -(-(S * N) // 128) * 16
+    return min(16 + codes + resid, 16 + 8 * N)
+
+
+@pytest.mark.parametrize("kc", [2, 6, 10])
+def test_largest_image_bound_is_attained_and_never_exceeded(kc):
+    """Positive real and negative imaginary parts: in the interleaved order every value
+    differs from its predecessor in the sign bit, so all take code 0 and all S bits
+    and STREAM reaches the bound; no other chunk exceeds it."""
+    A = 1 << kc
+    rng = np.random.default_rng(kc)
+    worst = rng.uniform(1, 2, A) - 1j * rng.uniform(1, 2, A)
+    for S in (13, 22, 26, 29, 40, 64):
+        bound = _format_max_image(kc, S)
+        assert len(O.encode_chunk(worst, kc, S)) == bound
+        for _ in range(5):
+            a = (rng.standard_normal(A) + 1j * rng.standard_normal(A)) * 2.0 ** rng.integers(-30, 30, A)
+            assert len(O.encode_chunk(a, kc, S)) <= bound
+
+
+def test_guarded_ladder_picks_the_smallest_level_that_fits():
+    """Ladder 2 before an uncontrolled gate: the smallest level whose largest images on
+    every chunk fit floor(tau * budget)."""
+    n, b, kc, tau = 10, 10, 4, 0.9
+    nch = 1 << (n - kc)
+    levels = [(1e-5, 29), (1e-4, 26), (1e-3, 22)]
+    g = Cc.gate(0, Cc.H)
+    for want in range(4):
+        S_fit = 64 if want == 0 else levels[want - 1][1]
+        # the budget admits exactly level `want` (and every level after it)
+        budget = math.ceil(nch * _format_max_image(kc, S_fit) / tau) + 1
+        cs = O.CSim(n, b, kc, 1e-3, budget=budget, tau=tau, ladder=2)
+        cs.apply([g])
+        st = cs.stats()
+        assert st["level"] == want
+        if want:
+            assert st["S_current"] == S_fit and st["eps_switch_gate"] == 0
+        else:
+            assert st["S_current"] == 64 and st["eps_switch_gate"] == -1
+    # nothing fits: the largest bound
+    cs = O.CSim(n, b, kc, 1e-3, budget=16, tau=tau, ladder=2)
+    cs.apply([g])
+    assert cs.stats()["S_current"] == 22
+
+
+def test_guarded_ladder_keeps_the_state_under_the_threshold():
+    """QAOA (CNOTs with controls on chunk bits rewrite half the chunks): whenever the
+    largest level fits, every gate ends with E <= floor(tau * budget)."""
+    n, kc = 12, 6
+    gates, _ = Cc.qaoa_maxcut(n, 2, 3, seed=5)
+    nch = 1 << (n - kc)
+    budget = math.ceil(nch * _format_max_image(kc, 64) / 0.9) + 1  # lossless fits at first
+    thresh = math.floor(0.9 * budget)
+    cs = O.CSim(n, n, kc, 1e-3, budget=budget, ladder=2)
+    levels = []
+    for g in gates:
+        cs.apply([g])
+        st = cs.stats()
+        assert st["encoded_bytes"] <= thresh
+        levels.append(st["level"])
+    assert levels == sorted(levels)  # the bound never tightens
+    assert levels[0] == 0 and levels[-1] > 0
+
+
 def test_error_statistics_section_4_2():
     """All relative errors below the bound; errors normalised by the last kept
     mantissa unit are spread over [0, 1); lag-1 autocorrelation near zero."""
