@@ -395,6 +395,86 @@ def run_qaoa34(args) -> dict:
             "gpu_launches": 2 * tm["launches"], "clocks": clk}
 
 
+def train_selector(qcsim, eps: float, seed: int):
+    """Selector network trained on the GPU from exhaustive-trial traces of a 20-qubit
+    random circuit and a 20-qubit QAOA circuit (the families of the 30- and 34-qubit
+    workloads); returns (bfloat16 parameters, trace rows, last loss)."""
+    rows = []
+    for g in (Cc.rcs(4, 5, 8, seed=seed), Cc.qaoa_maxcut(20, 2, 3, seed=seed)[0]):
+        s = qcsim.Sim(20, 20, eps, chunk_log2=10, budget=(16 << 20) // 4, pool_bytes=2 * (16 << 20) + (64 << 20))
+        s.set_selector(1)
+        s.trace(1 << 20)
+        s.apply_circuit(g)
+        rows.append(s.trace_read())
+        s.close()
+    tr = np.concatenate(rows)
+    p0 = Cc.selector_init(seed)
+    _, wb, loss = qcsim.mlp_train(tr[:, :16], tr[:, 16].astype(np.int32), tr[:, 17:19], p0, epochs=40, batch=256,
+                                  lr=3e-3, seed=seed)
+    return wb, int(tr.shape[0]), loss
+
+
+def run_grover(args) -> dict:
+    """Grover search, 8 iterations, 32 qubits (64 GiB raw; the 36-qubit state does not
+    fit one GB300 with this codec at 1e-4), blocks of 2^20, lossless then 1e-4 at raw/4:
+    the chunk-mode selectors side by side -- Solution C only, the exhaustive C + D
+    trial, and the trained network deciding the D trials.  Per selector: time per
+    iteration (CUDA events), peak compressed bytes, D trials, and the marked item's
+    probability against sin^2((2k+1) theta)."""
+    import math
+
+    import torch
+
+    from paper_1911_04034_gb300 import qcsim
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, iters = args.grover_n, 8
+    gates, marked = Cc.grover(n, iters, seed=SEED)
+    per_iter = 4 * n + 2
+    raw = 16 << n
+    t0 = time.perf_counter()
+    wb, nrows, loss = train_selector(qcsim, args.eps, SEED)
+    train_s = time.perf_counter() - t0
+    theta = math.asin(2.0 ** (-n / 2))
+    out = {}
+    for name, sel in (("C only", 0), ("exhaustive C+D", 1), ("network", 2)):
+        stream = torch.cuda.Stream()
+        s = qcsim.Sim(n, 20, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=raw + raw // 8, stream=stream)
+        if sel == 2:
+            s.set_selector(2, wb)
+        else:
+            s.set_selector(sel)
+        s.apply_circuit(gates[:n])
+        st0 = s.stats()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
+        ev[0].record(stream)
+        for k in range(iters):
+            s.apply_circuit(gates[n + k * per_iter: n + (k + 1) * per_iter])
+            ev[k + 1].record(stream)
+        ev[-1].synchronize()
+        ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(iters)]
+        st = s.stats()
+        a = s.amplitudes(marked, 1)[0]
+        out[name] = {"ms_per_iteration": ms, "amp_updates_per_s": (st["amp_updates"] - st0["amp_updates"]) / (sum(ms) * 1e-3),
+                     "max_encoded_gb": st["max_encoded_bytes"] / 1e9, "min_compression_ratio": st["min_ratio"],
+                     "split_trials": st["split_trials"], "eps_switch_gate": st["eps_switch_gate"],
+                     "p_marked": abs(a) ** 2, "p_closed_form": math.sin((2 * iters + 1) * theta) ** 2,
+                     "fidelity_lb_sum": st["fidelity_lb_sum"]}
+        s.close()
+    base = out["C only"]
+    return {"metric": METRIC, "value": out["network"]["amp_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": iters,
+            "warmup": 0, "ms_per_step": sum(out["network"]["ms_per_iteration"]) / iters, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Grover search {n} qubits, 8 iterations ({per_iter} gates each), eps {args.eps}, "
+                                   f"budget raw/4, chunks 2^{args.kc}; selectors compared",
+                       "n_qubits": n, "marked": marked},
+            "selector": {"train_rows": nrows, "train_loss": loss, "train_seconds": train_s},
+            "selectors": out,
+            "network_vs_c_only_peak_bytes": out["network"]["max_encoded_gb"] / base["max_encoded_gb"],
+            "network_vs_exhaustive_peak_bytes": out["network"]["max_encoded_gb"] / out["exhaustive C+D"]["max_encoded_gb"],
+            "network_vs_exhaustive_split_trials": out["network"]["split_trials"] / max(1, out["exhaustive C+D"]["split_trials"])}
+
+
 def cpu_sample(eps: float, n: int = 20, warm_layers: int = 3, timed_layers: int = 2, budget_s: float = 25.0):
     """The oracle on the host: same circuit family on a 4 x 5 grid (20 qubits), same
     bound and budget rule; times whole layers after a warm-up until budget_s."""
@@ -473,9 +553,10 @@ def main():
     ap.add_argument("--no-sv", action="store_true", help="skip the uncompressed comparator and fidelity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="also count SM cycles per phase of the fused kernel")
-    ap.add_argument("--workload", default="rcs30", choices=["rcs30", "batch", "qaoa34"],
+    ap.add_argument("--workload", default="rcs30", choices=["rcs30", "batch", "qaoa34", "grover"],
                     help="rcs30: the 30-qubit random circuit (default); batch: 256 circuits of 14-24 qubits; "
-                         "qaoa34: 34-qubit QAOA in a 180 GB pool")
+                         "qaoa34: 34-qubit QAOA in a 180 GB pool; grover: chunk-mode selectors on Grover search")
+    ap.add_argument("--grover-n", type=int, default=32)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)
@@ -491,6 +572,9 @@ def main():
         return
     if args.workload == "qaoa34" and args.impl == "gpu":
         print(json.dumps(run_qaoa34(args)), flush=True)
+        return
+    if args.workload == "grover" and args.impl == "gpu":
+        print(json.dumps(run_grover(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args)

@@ -216,6 +216,29 @@ sim_status sim_stats(sim_t* sim, sim_stats_t* out);
  * its length.  For checking images against a reference codec. */
 sim_status sim_chunk_image(sim_t* sim, uint64_t c, uint8_t* out, size_t cap, size_t* len);
 
+/* Checkpoint / resume (Section 3.5: save the compressed blocks, load them in a later
+ * job).  The checkpoint is one flat little-endian buffer: a 256-byte header (magic
+ * "QCSIMCK1", version 1, n, block_log2, chunk_log2, err_bound, budget, tau, ladder,
+ * mode set, controller level and bits, E, Emax, gates, switch gate, both fidelity-bound
+ * accumulators, amplitude updates, peak pages, chunk count, image bytes), then one
+ * uint32 image length per chunk, then the chunk images in chunk order (each a multiple
+ * of 16 bytes, the chunk image format).  Page ids are not saved; the selector network
+ * and timing switches are host settings and are not saved either.
+ * sim_checkpoint_size: bytes sim_checkpoint_save writes for the current state.
+ * sim_checkpoint_save: writes the checkpoint to out (cap bytes; out on the device if
+ *   out_on_device, else host memory); SIM_ERR_INVALID if cap is too small.  The state
+ *   is unchanged.
+ * sim_checkpoint_load: replaces the state of sim (created with the same n, block_log2,
+ *   chunk_log2, err_bound, budget, tau and ladder, else SIM_ERR_INVALID) with the saved
+ *   one: images, directory, page arena (pages reassigned in chunk order), controller and
+ *   counters, so later gates give the images an uninterrupted run gives.  Lengths and
+ *   header fields are checked (SIM_ERR_INVALID); an arena too small for the saved images
+ *   gives SIM_ERR_OOM.  Clears a poisoned handle on success.  The caller owns the
+ *   buffers; both calls synchronise the handle's stream. */
+sim_status sim_checkpoint_size(sim_t* sim, uint64_t* bytes);
+sim_status sim_checkpoint_save(sim_t* sim, void* out, uint64_t cap, int out_on_device);
+sim_status sim_checkpoint_load(sim_t* sim, const void* in, uint64_t in_len, int in_on_device);
+
 /* Number of chunks and chunk_log2 of the handle. */
 sim_status sim_layout(sim_t* sim, uint64_t* n_chunks, int* chunk_log2, int* block_log2);
 

@@ -238,3 +238,16 @@ def random_batch(count: int, n_lo: int, n_hi: int, d_lo: int, d_hi: int, seed: i
         d = int(rng.integers(d_lo, d_hi + 1))
         out.append((n, rcs_n(n, d, seed * 100003 + k)))
     return out
+
+
+def selector_init(seed: int) -> np.ndarray:
+    """Seeded starting parameters of the chunk-mode selector network (16 -> 32 -> 32 ->
+    8): He-normal weights and zero biases, float32, in the order W1 b1 W2 b2 W3 b3 with
+    row-major weight matrices (1864 numbers).  Random numbers only; the trainer rounds
+    them to bfloat16."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for rows, cols in ((32, 16), (32, 32), (8, 32)):
+        parts.append((rng.standard_normal((rows, cols)) * math.sqrt(2.0 / cols)).astype(np.float32).ravel())
+        parts.append(np.zeros(rows, dtype=np.float32))
+    return np.concatenate(parts)

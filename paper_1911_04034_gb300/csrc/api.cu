@@ -840,6 +840,196 @@ sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, co
   return SIM_OK;
 }
 
+// ----------------------------------------------------------- checkpoint -- //
+namespace {
+
+struct CkHeader {
+  char magic[8];  // "QCSIMCK1"
+  uint32_t version, n, b, kc;
+  double eps_max;
+  uint64_t budget;
+  double tau;
+  int32_t ladder;
+  uint32_t modes;
+  int32_t level, S_last;
+  uint64_t E, Emax, gates;
+  int64_t switch_gate;
+  double lb_sum, lb_prod;
+  uint64_t amp_updates, peak_pages, nchunks, image_bytes;
+};
+static_assert(sizeof(CkHeader) <= 256, "checkpoint header must fit 256 bytes");
+constexpr uint64_t kCkHead = 256;
+const char kCkMagic[8] = {'Q', 'C', 'S', 'I', 'M', 'C', 'K', '1'};
+
+// Image lengths of every chunk on the host, and their exclusive prefix sums.
+sim_status ck_lengths(sim* s, std::vector<uint32_t>& len, std::vector<unsigned long long>& off, uint64_t& total) {
+  uint32_t* d_len = nullptr;
+  CK(cudaMalloc(&d_len, s->nchunks * 4), "checkpoint lengths");
+  cudaError_t e = qc::launch_checkpoint_lengths(s->P, s->nchunks, d_len, s->st);
+  len.resize(s->nchunks);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(len.data(), d_len, s->nchunks * 4, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(d_len);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpoint lengths");
+  off.resize(s->nchunks);
+  total = 0;
+  for (uint64_t c = 0; c < s->nchunks; ++c) {
+    off[c] = total;
+    total += len[c];
+  }
+  return SIM_OK;
+}
+
+}  // namespace
+
+sim_status sim_checkpoint_size(sim_t* s, uint64_t* bytes) {
+  if (!s || !bytes) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  std::vector<uint32_t> len;
+  std::vector<unsigned long long> off;
+  uint64_t total = 0;
+  if (sim_status r = ck_lengths(s, len, off, total)) return r;
+  *bytes = kCkHead + 4 * s->nchunks + total;
+  return SIM_OK;
+}
+
+sim_status sim_checkpoint_save(sim_t* s, void* out, uint64_t cap, int out_on_device) {
+  if (!s || !out) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  std::vector<uint32_t> len;
+  std::vector<unsigned long long> off;
+  uint64_t total = 0;
+  if (sim_status r = ck_lengths(s, len, off, total)) return r;
+  const uint64_t need = kCkHead + 4 * s->nchunks + total;
+  if (cap < need) return fail(SIM_ERR_INVALID, "checkpoint buffer too small (see sim_checkpoint_size)");
+  DevCtl h{};
+  CK(cudaMemcpyAsync(&h, s->d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s->st), "copy counters");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  if (h.err) return s->check_device();
+  uint8_t head[kCkHead] = {0};
+  CkHeader k{};
+  std::memcpy(k.magic, kCkMagic, 8);
+  k.version = 1;
+  k.n = (uint32_t)s->n;
+  k.b = (uint32_t)s->b;
+  k.kc = (uint32_t)s->kc;
+  k.eps_max = s->eps_max;
+  k.budget = s->budget;
+  k.tau = s->tau;
+  k.ladder = s->ladder;
+  k.modes = s->modes;
+  k.level = h.level;
+  k.S_last = h.S_last;
+  k.E = h.E;
+  k.Emax = h.Emax;
+  k.gates = h.gates;
+  k.switch_gate = h.switch_gate;
+  k.lb_sum = h.lb_sum;
+  k.lb_prod = h.lb_prod;
+  k.amp_updates = s->amp_updates;
+  k.peak_pages = h.peak_pages;
+  k.nchunks = s->nchunks;
+  k.image_bytes = total;
+  std::memcpy(head, &k, sizeof(k));
+  // images: gathered on the device, straight into the caller's buffer when it is there
+  unsigned long long* d_off = nullptr;
+  uint8_t* d_img = nullptr;
+  CK(cudaMalloc(&d_off, s->nchunks * 8), "checkpoint offsets");
+  uint8_t* base = reinterpret_cast<uint8_t*>(out);
+  cudaError_t e = cudaMemcpyAsync(d_off, off.data(), s->nchunks * 8, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess && !out_on_device && total) e = cudaMalloc(&d_img, total);
+  uint8_t* dst = out_on_device ? base + kCkHead + 4 * s->nchunks : d_img;
+  if (e == cudaSuccess && total) e = qc::launch_checkpoint_gather(s->P, s->nchunks, d_off, dst, s->st);
+  const cudaMemcpyKind k_to = out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base, head, kCkHead, k_to, s->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(base + kCkHead, len.data(), 4 * s->nchunks, k_to, s->st);
+  if (e == cudaSuccess && !out_on_device && total)
+    e = cudaMemcpyAsync(base + kCkHead + 4 * s->nchunks, d_img, total, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(d_off);
+  cudaFree(d_img);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpoint save");
+  return SIM_OK;
+}
+
+sim_status sim_checkpoint_load(sim_t* s, const void* in, uint64_t in_len, int in_on_device) {
+  if (!s || !in) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (in_len < kCkHead) return fail(SIM_ERR_INVALID, "checkpoint shorter than its header");
+  const uint8_t* base = reinterpret_cast<const uint8_t*>(in);
+  const cudaMemcpyKind k_from = in_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  uint8_t head[kCkHead];
+  CK(cudaMemcpy(head, base, kCkHead, k_from), "checkpoint header");
+  CkHeader k{};
+  std::memcpy(&k, head, sizeof(k));
+  if (std::memcmp(k.magic, kCkMagic, 8) != 0 || k.version != 1) return fail(SIM_ERR_INVALID, "not a checkpoint");
+  if (k.n != (uint32_t)s->n || k.b != (uint32_t)s->b || k.kc != (uint32_t)s->kc || k.nchunks != s->nchunks ||
+      k.eps_max != s->eps_max || k.ladder != s->ladder || k.budget != s->budget || k.tau != s->tau)
+    return fail(SIM_ERR_INVALID, "checkpoint taken with other qubits, block/chunk sizes or controller settings");
+  if (k.level < 0 || k.level > s->cp.nlevels || (k.modes & qc::kDefaultModes) != qc::kDefaultModes ||
+      (k.modes >> qc::M_NMODES))
+    return fail(SIM_ERR_INVALID, "checkpoint controller state out of range");
+  if (in_len < kCkHead + 4 * s->nchunks + k.image_bytes) return fail(SIM_ERR_INVALID, "checkpoint truncated");
+  std::vector<uint32_t> len(s->nchunks);
+  CK(cudaMemcpy(len.data(), base + kCkHead, 4 * s->nchunks, k_from), "checkpoint lengths");
+  std::vector<unsigned long long> off(s->nchunks), pbase(s->nchunks);
+  uint64_t total = 0, used = 0;
+  const uint32_t cap = qc::round16(qc::max_image_bytes(s->kc));
+  for (uint64_t c = 0; c < s->nchunks; ++c) {
+    if (len[c] < 16 || len[c] > cap || (len[c] & 15u)) return fail(SIM_ERR_INVALID, "checkpoint image length out of range");
+    off[c] = total;
+    pbase[c] = used;
+    total += len[c];
+    used += qc::pages_for(len[c], s->kc);
+  }
+  if (total != k.image_bytes || total != k.E) return fail(SIM_ERR_INVALID, "checkpoint image bytes disagree");
+  if (used > s->npages) return fail(SIM_ERR_OOM, "checkpoint needs more pages than the arena holds");
+  unsigned long long *d_off = nullptr, *d_pb = nullptr;
+  uint32_t* d_len = nullptr;
+  uint8_t* d_img = nullptr;
+  cudaError_t e = cudaMalloc(&d_off, s->nchunks * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d_pb, s->nchunks * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d_len, s->nchunks * 4);
+  if (e == cudaSuccess && !in_on_device && total) e = cudaMalloc(&d_img, total);
+  const uint8_t* src = in_on_device ? base + kCkHead + 4 * s->nchunks : d_img;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), s->nchunks * 8, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_pb, pbase.data(), s->nchunks * 8, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, len.data(), s->nchunks * 4, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess && !in_on_device && total)
+    e = cudaMemcpyAsync(d_img, base + kCkHead + 4 * s->nchunks, total, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = qc::launch_checkpoint_scatter(s->P, s->nchunks, d_off, d_pb, d_len, src, used, s->st);
+  // controller and pool counters as they were, the page caches empty
+  DevCtl h{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, s->d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e == cudaSuccess) {
+    h.E = k.E;
+    h.dE = 0;
+    h.Emax = k.Emax;
+    h.top = (long long)(s->npages - used);
+    h.nfreed = 0;
+    h.gates = k.gates;
+    h.peak_pages = k.peak_pages > used ? k.peak_pages : used;
+    h.switch_gate = k.switch_gate;
+    h.lb_sum = k.lb_sum;
+    h.lb_prod = k.lb_prod;
+    h.level = k.level;
+    h.S_last = k.S_last;
+    h.err = 0;
+    e = cudaMemcpyAsync(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->P.cache_n, 0, (size_t)s->grid * sizeof(uint32_t), s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(d_off);
+  cudaFree(d_pb);
+  cudaFree(d_len);
+  cudaFree(d_img);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpoint load");
+  s->amp_updates = k.amp_updates;
+  s->modes = k.modes;
+  s->poisoned = SIM_OK;
+  return SIM_OK;
+}
+
 // ------------------------------------------------------------ codec ------ //
 sim_status sim_codec_encode(const double* in, uint64_t n_chunks, int chunk_log2, double eps, int force_mode,
                             uint8_t* out, uint64_t out_stride, uint32_t* out_len, int on_device) {

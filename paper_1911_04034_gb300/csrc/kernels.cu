@@ -745,6 +745,65 @@ __global__ void __launch_bounds__(256) k_sv_gate(double2* psi, unsigned long lon
   }
 }
 
+// ----------------------------------------------------------- checkpoint -- //
+// Section 3.5: the compressed state is saved as its chunk images and restored by
+// rebuilding the directory and the page arena around them.
+
+// Image length of every chunk (directory entry word 0).
+__global__ void k_ck_lengths(const Pool P, unsigned long long nchunks, uint32_t* len) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nchunks; c += stride)
+    len[c] = dir_entry(P, c)[0];
+}
+
+// Copies every chunk's image to out + off[c] (one warp per chunk; off multiples of 16).
+__global__ void k_ck_gather(const Pool P, unsigned long long nchunks, const unsigned long long* off, uint8_t* out) {
+  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / 32u);
+  const uint32_t lane = threadIdx.x & 31u;
+  constexpr uint32_t upp = kPage / 16;
+  for (unsigned long long c = blockIdx.x * (unsigned long long)(blockDim.x / 32u) + threadIdx.x / 32u; c < nchunks;
+       c += warps) {
+    const uint32_t* e = dir_entry(P, c);
+    const uint32_t units = e[0] >> 4, np = e[1];
+    uint4* dst = reinterpret_cast<uint4*>(out + off[c]);
+    for (uint32_t u = lane; u < units; u += 32u)
+      dst[u] = np == 0u ? reinterpret_cast<const uint4*>(e + 4)[u]
+                        : reinterpret_cast<const uint4*>(P.pages + (unsigned long long)e[4 + u / upp] * kPage)[u % upp];
+  }
+}
+
+// Writes chunk c's image from in + off[c] (len[c] bytes) back: inline in the directory
+// entry when it fits, else into pages pbase[c], pbase[c] + 1, ...
+__global__ void k_ck_scatter(const Pool P, unsigned long long nchunks, const unsigned long long* off,
+                             const unsigned long long* pbase, const uint32_t* len, const uint8_t* in) {
+  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / 32u);
+  const uint32_t lane = threadIdx.x & 31u;
+  constexpr uint32_t upp = kPage / 16;
+  for (unsigned long long c = blockIdx.x * (unsigned long long)(blockDim.x / 32u) + threadIdx.x / 32u; c < nchunks;
+       c += warps) {
+    uint32_t* e = dir_entry(P, c);
+    const uint32_t bytes = len[c], units = bytes >> 4, np = pages_for(bytes, P.kc);
+    const uint4* src = reinterpret_cast<const uint4*>(in + off[c]);
+    for (uint32_t u = lane; u < units; u += 32u) {
+      if (np == 0u) reinterpret_cast<uint4*>(e + 4)[u] = src[u];
+      else reinterpret_cast<uint4*>(P.pages + (pbase[c] + u / upp) * kPage)[u % upp] = src[u];
+    }
+    if (np) for (uint32_t k = lane; k < np; k += 32u) e[4 + k] = (uint32_t)(pbase[c] + k);
+    if (lane == 0) {
+      e[0] = bytes;
+      e[1] = np;
+      e[2] = e[3] = 0u;
+    }
+  }
+}
+
+// After a restore pages [0, used) hold images: the free stack lists the others.
+__global__ void k_ck_stack(const Pool P, unsigned long long used) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; used + i < P.npages; i += stride)
+    P.stack[i] = (uint32_t)(used + i);
+}
+
 // ------------------------------------------------------------- launchers -- //
 static int num_sms() {
   static int sms = 0;
@@ -926,6 +985,26 @@ cudaError_t launch_sv_gate(double* psi, int n, const GateCoef& g, int target, un
   const unsigned long long want = (npairs + 255ull) / 256ull;
   const unsigned grid = (unsigned)(want < (unsigned long long)num_sms() * 16 ? want : (unsigned long long)num_sms() * 16);
   k_sv_gate<<<grid, 256, 0, st>>>(reinterpret_cast<double2*>(psi), npairs, g, target, cmask, cvals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_checkpoint_lengths(const Pool& P, unsigned long long nchunks, uint32_t* len, cudaStream_t st) {
+  const unsigned long long g = (nchunks + 255) / 256;
+  k_ck_lengths<<<(unsigned)(g < 65535ull ? g : 65535ull), 256, 0, st>>>(P, nchunks, len);
+  return cudaGetLastError();
+}
+cudaError_t launch_checkpoint_gather(const Pool& P, unsigned long long nchunks, const unsigned long long* off,
+                                     uint8_t* out, cudaStream_t st) {
+  k_ck_gather<<<num_sms() * 8, 256, 0, st>>>(P, nchunks, off, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_checkpoint_scatter(const Pool& P, unsigned long long nchunks, const unsigned long long* off,
+                                      const unsigned long long* pbase, const uint32_t* len, const uint8_t* in,
+                                      unsigned long long used, cudaStream_t st) {
+  k_ck_scatter<<<num_sms() * 8, 256, 0, st>>>(P, nchunks, off, pbase, len, in);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ck_stack<<<num_sms() * 8, 256, 0, st>>>(P, used);
   return cudaGetLastError();
 }
 

@@ -79,4 +79,13 @@ cudaError_t launch_sv_init(double* psi, unsigned long long amps, cudaStream_t st
 cudaError_t launch_sv_gate(double* psi, int n, const GateCoef& g, int target, unsigned long long cmask,
                            unsigned long long cvals, cudaStream_t st);
 
+// Checkpoint: image lengths, gather of all images, and the rebuild of directory and
+// page arena from saved images (pages [0, used) in chunk order).
+cudaError_t launch_checkpoint_lengths(const Pool& P, unsigned long long nchunks, uint32_t* len, cudaStream_t st);
+cudaError_t launch_checkpoint_gather(const Pool& P, unsigned long long nchunks, const unsigned long long* off,
+                                     uint8_t* out, cudaStream_t st);
+cudaError_t launch_checkpoint_scatter(const Pool& P, unsigned long long nchunks, const unsigned long long* off,
+                                      const unsigned long long* pbase, const uint32_t* len, const uint8_t* in,
+                                      unsigned long long used, cudaStream_t st);
+
 }  // namespace qc

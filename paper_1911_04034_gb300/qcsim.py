@@ -67,6 +67,9 @@ def lib():
             "sim_create": [i32, i32, dbl, pp],
             "sim_create_ex": [i32, i32, i32, dbl, u64, dbl, i32, u64, pp],
             "sim_destroy": [vp],
+            "sim_checkpoint_size": [vp, C.POINTER(C.c_uint64)],
+            "sim_checkpoint_save": [vp, vp, u64, i32],
+            "sim_checkpoint_load": [vp, vp, u64, i32],
             "sim_set_stream": [vp, vp],
             "sim_apply_gate": [vp, vp],
             "sim_apply_circuit": [vp, vp, sz],
@@ -201,6 +204,26 @@ class Sim:
             assert p.size == 1864
         _check(lib().sim_set_selector(self._h, int(selector), C.c_void_p(_ptr(p)) if p is not None else None),
                "sim_set_selector")
+
+    def checkpoint(self, out=None):
+        """The compressed state as a checkpoint (Section 3.5): a numpy uint8 array, or
+        written into `out` (a torch CUDA uint8 tensor large enough) and returned."""
+        n = C.c_uint64()
+        _check(lib().sim_checkpoint_size(self._h, C.byref(n)), "sim_checkpoint_size")
+        if out is None:
+            out = np.zeros(n.value, dtype=np.uint8)
+        _check(lib().sim_checkpoint_save(self._h, C.c_void_p(_ptr(out)), int(n.value), int(_is_device(out))),
+               "sim_checkpoint_save")
+        return out
+
+    def restore(self, ck) -> None:
+        """Replaces the state with a checkpoint (numpy uint8 array / bytes, or a torch
+        CUDA uint8 tensor)."""
+        if isinstance(ck, (bytes, bytearray)):
+            ck = np.frombuffer(bytes(ck), dtype=np.uint8).copy()
+        size = ck.numel() if _is_device(ck) else ck.size
+        _check(lib().sim_checkpoint_load(self._h, C.c_void_p(_ptr(ck)), int(size), int(_is_device(ck))),
+               "sim_checkpoint_load")
 
     def trace(self, capacity: int) -> None:
         _check(lib().sim_trace(self._h, int(capacity)), "sim_trace")
