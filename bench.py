@@ -437,18 +437,23 @@ def run_grover(args) -> dict:
     gates, marked = Cc.grover(n, iters, seed=SEED)
     per_iter = 4 * n + 2
     raw = 16 << n
-    t0 = time.perf_counter()
-    wb, nrows, loss = train_selector(qcsim, args.eps, SEED)
-    train_s = time.perf_counter() - t0
+    runs = [r for r in (("C only", 0), ("exhaustive C+D", 1), ("network", 2)) if str(r[1]) in args.selectors.split(",")]
+    wb, nrows, loss, train_s = None, 0, None, 0.0
+    if any(sel == 2 for _, sel in runs):
+        t0 = time.perf_counter()
+        wb, nrows, loss = train_selector(qcsim, args.eps, SEED)
+        train_s = time.perf_counter() - t0
     theta = math.asin(2.0 ** (-n / 2))
     out = {}
-    for name, sel in (("C only", 0), ("exhaustive C+D", 1), ("network", 2)):
+    for name, sel in runs:
         stream = torch.cuda.Stream()
         s = qcsim.Sim(n, 20, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=raw + raw // 8, stream=stream)
         if sel == 2:
             s.set_selector(2, wb)
         else:
             s.set_selector(sel)
+        if args.cache:
+            s.set_block_cache(True)
         s.apply_circuit(gates[:n])
         st0 = s.stats()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
@@ -464,20 +469,24 @@ def run_grover(args) -> dict:
                      "max_encoded_gb": st["max_encoded_bytes"] / 1e9, "min_compression_ratio": st["min_ratio"],
                      "split_trials": st["split_trials"], "eps_switch_gate": st["eps_switch_gate"],
                      "p_marked": abs(a) ** 2, "p_closed_form": math.sin((2 * iters + 1) * theta) ** 2,
-                     "fidelity_lb_sum": st["fidelity_lb_sum"]}
+                     "fidelity_lb_sum": st["fidelity_lb_sum"], "cache_lookups": st["cache_lookups"],
+                     "cache_hits": st["cache_hits"]}
         s.close()
-    base = out["C only"]
-    return {"metric": METRIC, "value": out["network"]["amp_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": iters,
-            "warmup": 0, "ms_per_step": sum(out["network"]["ms_per_iteration"]) / iters, "higher_is_better": True,
+    head = out[runs[-1][0]]
+    ratios = {}
+    if len(out) == 3:
+        ratios = {"network_vs_c_only_peak_bytes": out["network"]["max_encoded_gb"] / out["C only"]["max_encoded_gb"],
+                  "network_vs_exhaustive_peak_bytes": out["network"]["max_encoded_gb"] / out["exhaustive C+D"]["max_encoded_gb"],
+                  "network_vs_exhaustive_split_trials": out["network"]["split_trials"] / max(1, out["exhaustive C+D"]["split_trials"])}
+    return {"metric": METRIC, "value": head["amp_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": iters,
+            "warmup": 0, "ms_per_step": sum(head["ms_per_iteration"]) / iters, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"Grover search {n} qubits, 8 iterations ({per_iter} gates each), eps {args.eps}, "
-                                   f"budget raw/4, chunks 2^{args.kc}; selectors compared",
-                       "n_qubits": n, "marked": marked},
+                                   f"budget raw/4, chunks 2^{args.kc}; selectors compared"
+                                   + ("; block cache on" if args.cache else ""),
+                       "n_qubits": n, "marked": marked, "block_cache": bool(args.cache)},
             "selector": {"train_rows": nrows, "train_loss": loss, "train_seconds": train_s},
-            "selectors": out,
-            "network_vs_c_only_peak_bytes": out["network"]["max_encoded_gb"] / base["max_encoded_gb"],
-            "network_vs_exhaustive_peak_bytes": out["network"]["max_encoded_gb"] / out["exhaustive C+D"]["max_encoded_gb"],
-            "network_vs_exhaustive_split_trials": out["network"]["split_trials"] / max(1, out["exhaustive C+D"]["split_trials"])}
+            "selectors": out, **ratios}
 
 
 def cpu_sample(eps: float, n: int = 20, warm_layers: int = 3, timed_layers: int = 2, budget_s: float = 25.0):
@@ -562,6 +571,8 @@ def main():
                     help="rcs30: the 30-qubit random circuit (default); batch: 256 circuits of 14-24 qubits; "
                          "qaoa34: 34-qubit QAOA in a 180 GB pool; grover: chunk-mode selectors on Grover search")
     ap.add_argument("--grover-n", type=int, default=32)
+    ap.add_argument("--selectors", default="0,1,2", help="grover: which selectors to run (0 C only, 1 exhaustive, 2 network)")
+    ap.add_argument("--cache", action="store_true", help="grover: switch the compressed block cache on")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)

@@ -92,6 +92,8 @@ typedef struct sim_stats_t {
   uint64_t phase_cycles[6];   /* with sim_set_timing(sim, 2): SM cycles of the fused kernel's CTAs in
                                  stage / decode / apply / encode / commit / constant fast paths */
   uint64_t split_trials;      /* chunk encodes that ran the Solution D trial */
+  uint64_t cache_lookups;     /* block-cache lookups (work items that consulted it) */
+  uint64_t cache_hits;        /* ... that took a cached result */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
@@ -154,6 +156,17 @@ sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const*
  * updates per second of kernel time, rates[i] (if not NULL) each candidate's rate. */
 sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,
                               const int* candidates, int n_candidates, int* best, double* rates);
+
+/* Compressed block cache (Section 3.4): on = 1 allocates 256 lines (each 64 bytes plus
+ * room for four images of the largest size, 16.8 MB at chunk_log2 10) and makes later
+ * gates look up every work item of two chunks: a line holds the item's two input
+ * images and the two images the running gate made of them, so another item of the same
+ * gate with byte-identical inputs takes those images instead of decoding, applying and
+ * encoding (the result is the same bytes).  Lines are valid for one gate; when 16 gates
+ * in a row look up without a hit the cache sits out 64 gates, then probes again.  No
+ * lookups while selector training records are being written.  on = 0 frees the lines.
+ * Counts in sim_stats_t.cache_lookups / cache_hits. */
+sim_status sim_set_block_cache(sim_t* sim, int on);
 
 /* Chunk modes the encoder chooses from for later gates (bit m = mode m).  The default
  * 0x1F is Solution C (Section 4.2) with its Zstd stand-in modes ZERO..RAW; 0x3F adds

@@ -145,6 +145,7 @@ struct sim {
   int selector = 0;                  // 0 mode set, 2 selector network
   unsigned short* d_mlp = nullptr;   // bfloat16 parameters of the selector network
   float* d_trace = nullptr;          // selector training records
+  uint8_t* d_bc = nullptr;           // block cache lines (Section 3.4) or nullptr
   uint64_t trace_cap = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -155,6 +156,7 @@ struct sim {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     cudaFree(d_mlp);
     cudaFree(d_trace);
+    cudaFree(d_bc);
     cudaFree(P.pages);
     cudaFree(P.dir);
     cudaFree(P.stack);
@@ -375,6 +377,7 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
     const bool perm = u[0] == 0 && u[1] == 0 && u[6] == 0 && u[7] == 0;
     L.gfeat = (real ? 1u : 0u) | (diag ? 2u : 0u) | (perm ? 4u : 0u) | (t < kc ? 8u : 0u);
   }
+  L.bc = s->d_trace ? nullptr : s->d_bc;
   L.trace = s->d_trace;
   L.trace_n = s->d_trace ? &s->d_ctl->trace_n : nullptr;
   L.trace_cap = s->trace_cap;
@@ -502,6 +505,28 @@ sim_status sim_timing(sim_t* s, double* ms, uint64_t* launches, uint64_t* bytes_
   s->t_bytes_out0 = out;
   s->ev_pending.clear();
   s->ev_next = 0;
+  return SIM_OK;
+}
+
+sim_status sim_set_block_cache(sim_t* s, int on) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  CK(cudaStreamSynchronize(s->st), "sync");
+  if (!on) {
+    cudaFree(s->d_bc);
+    s->d_bc = nullptr;
+    return SIM_OK;
+  }
+  if (s->d_bc) return SIM_OK;
+  const size_t bytes = (size_t)qc::kBcLines * qc::bc_line_bytes(qc::round16(qc::max_image_bytes(s->kc)));
+  CK(cudaMalloc(&s->d_bc, bytes), "block cache");
+  CK(cudaMemset(s->d_bc, 0, bytes), "block cache");  // every line empty, tag 0
+  // a fresh cache starts switched on
+  DevCtl h{};
+  CK(cudaMemcpy(&h, s->d_ctl, sizeof(h), cudaMemcpyDeviceToHost), "copy counters");
+  h.bc_off = 0;
+  h.bc_zero_streak = 0;
+  CK(cudaMemcpy(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice), "copy counters");
   return SIM_OK;
 }
 
@@ -695,6 +720,8 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->block_log2 = s->b;
   for (int k = 0; k < 6; ++k) o->phase_cycles[k] = h.phase_cycles[k];
   o->split_trials = h.split_trials;
+  o->cache_lookups = h.bc_lookups;
+  o->cache_hits = h.bc_hits;
   if (h.err) return s->check_device();
   return SIM_OK;
 }

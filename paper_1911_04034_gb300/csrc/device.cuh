@@ -69,6 +69,12 @@ struct DevCtl {
   unsigned long long phase_cycles[6];  // SM cycles of CTA thread 0 per phase when profiling
   unsigned long long split_trials;     // chunk encodes that ran the Solution D trial
   unsigned long long trace_n;          // selector training records written
+  unsigned long long bc_lookups;       // block-cache lookups (cumulative)
+  unsigned long long bc_hits;          // block-cache hits (cumulative)
+  unsigned long long bc_gate_lookups;  // ... during the running gate
+  unsigned long long bc_gate_hits;
+  unsigned int bc_zero_streak;         // gates in a row with lookups and no hit
+  unsigned int bc_off;                 // gates the cache still sits out (0 = on)
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -126,6 +132,23 @@ struct Pool {
   int kc;
 };
 
+// ------------------------------------------------------- block cache ---- //
+// Section 3.4: a line holds the two compressed input blocks of a work item and the two
+// output blocks the running gate made of them; another item of the same gate with the
+// same inputs takes the outputs instead of decoding, applying and encoding.  Lines are
+// valid for one gate (tag = gate serial << 2 | state; states 0 empty, 1 being written,
+// 2 ready); a hit is confirmed byte by byte.
+constexpr int kBcLines = 256;
+constexpr uint32_t kBcHead = 64;
+constexpr unsigned int kBcZeroGates = 16;  // gates with lookups and no hit before the cache pauses
+constexpr unsigned int kBcPause = 64;      // gates it then sits out before probing again
+struct BcLine {
+  unsigned long long tag;
+  unsigned long long key;
+  uint32_t len[4];  // input 0, input 1, output 0, output 1
+};
+__host__ __device__ __forceinline__ uint64_t bc_line_bytes(uint32_t img_cap) { return kBcHead + 4ull * img_cap; }
+
 // -------------------------------------------------------------- scans ----- //
 __device__ __forceinline__ uint32_t warp_incl_add(uint32_t v) {
   const int lane = threadIdx.x & 31;
@@ -159,6 +182,8 @@ struct ScanSmem {
   uint32_t bits_period;
   int split_pick;  // the selector network's decision for the chunk being encoded
   uint32_t zcnt[2];  // selector inputs: amplitude groups with all-zero real / imaginary parts
+  unsigned long long bc_part[kWarps];  // block cache: per-warp partial hashes
+  int bc_flag;                         // block cache: 0 miss, 1 candidate line, 2 line claimed
 };
 
 // Exclusive prefix sum over the CTA with one barrier; also ORs `fo` and ANDs `fa`
@@ -262,6 +287,32 @@ __device__ __forceinline__ uint32_t block_lead_scan(uint32_t M, uint32_t V, Scan
   }
   pp ^= 1;
   return (pv & ~em) | ev;
+}
+
+// Block cache key of a work item: a hash of its two staged images (every 16-byte
+// unit mixed with its position, summed).  All threads; one barrier.
+__device__ __forceinline__ unsigned long long bc_mix(uint4 v, uint32_t pos) {
+  unsigned long long z = (((unsigned long long)v.y << 32) | v.x) + 0x9E3779B97F4A7C15ull * (pos + 1u);
+  z ^= (((unsigned long long)v.w << 32) | v.z) * 0xD1B54A32D192ED03ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long bc_key(const uint8_t* img0, uint32_t b0, const uint8_t* img1, uint32_t b1,
+                                                     ScanSmem& s) {
+  const uint32_t u0 = b0 >> 4, u1 = b1 >> 4;
+  unsigned long long h = 0ull;
+  for (uint32_t u = threadIdx.x; u < u0 + u1; u += kThreads)
+    h += bc_mix(u < u0 ? reinterpret_cast<const uint4*>(img0)[u] : reinterpret_cast<const uint4*>(img1)[u - u0],
+                u < u0 ? u : 0x80000000u + (u - u0));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31u) == 0) s.bc_part[threadIdx.x >> 5] = h;
+  __syncthreads();
+  unsigned long long k = (unsigned long long)b0 * 0x100000001B3ull + b1;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) k += s.bc_part[i];
+  return k;
 }
 
 // ---------------------------------------------------------- bit helpers --- //

@@ -148,7 +148,7 @@ __device__ __forceinline__ unsigned long long item_chunk(const GateLaunch& L, un
 // entries are fetched asynchronously during this item and its pages pulled into L2.
 template <int VPT, bool PREF>
 __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long long item, uint32_t S,
-                                          const GateSmem& m, GateCta& st) {
+                                          unsigned long long serial, bool bc_on, const GateSmem& m, GateCta& st) {
   const int kc = L.P.kc;
   const uint32_t A = 1u << kc;
   const uint32_t cap = imgcap(kc);
@@ -287,20 +287,82 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   __syncthreads();
   if (threadIdx.x < 32u) free_pages_warp(P, st.cc, ent0 + 4, np0, ent1 + 4, has1 ? np1 : 0u);
   QC_PHASE(0);
-  const bool ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
-  const bool ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
   // the next item's pages into L2: warp 0 for its first chunk, warp 1 for its second
   // (each warp waits only for the entry copies it issued itself)
-  if (PREF && st.next_item != ~0ull && threadIdx.x < 64u && (threadIdx.x < 32u || nhas1)) {
-    cp_async_wait_all();
-    __syncwarp();
-    const uint32_t* e = m.ent[st.cur ^ 1][threadIdx.x >> 5];
-    const uint32_t q = min(e[1], max_pages(kc));
-    for (uint32_t k = threadIdx.x & 31u; k < q; k += 32u) {
-      const uint32_t pid = e[4 + k];
-      if (pid < P.npages) prefetch_l2_page(P.pages + (unsigned long long)pid * kPage);
+  auto prefetch_next = [&]() {
+    if (PREF && st.next_item != ~0ull && threadIdx.x < 64u && (threadIdx.x < 32u || nhas1)) {
+      cp_async_wait_all();
+      __syncwarp();
+      const uint32_t* e = m.ent[st.cur ^ 1][threadIdx.x >> 5];
+      const uint32_t q = min(e[1], max_pages(kc));
+      for (uint32_t k = threadIdx.x & 31u; k < q; k += 32u) {
+        const uint32_t pid = e[4 + k];
+        if (pid < P.npages) prefetch_l2_page(P.pages + (unsigned long long)pid * kPage);
+      }
+    }
+  };
+  // Section 3.4: an earlier item of this gate with the same two input blocks left its
+  // outputs in the block cache (confirmed byte by byte); otherwise claim the line
+  bool bc_hit = false, bc_claim = false;
+  BcLine* line = nullptr;
+  uint8_t* ldat = nullptr;
+  unsigned long long key = 0;
+  uint32_t n0 = 0, n1 = 1;
+  if (L.bc && bc_on && has1) {
+    key = bc_key(m.img0, b0, m.img1, b1, *m.s);
+    line = reinterpret_cast<BcLine*>(L.bc + (key % (unsigned long long)kBcLines) * bc_line_bytes(cap));
+    ldat = reinterpret_cast<uint8_t*>(line) + kBcHead;
+    if (threadIdx.x == 0) {
+      const unsigned long long t = atomicAdd(&line->tag, 0ull);
+      int flag = 0;
+      if (t == ((serial << 2) | 2ull)) {
+        __threadfence();
+        if (__ldcg(&line->key) == key && __ldcg(&line->len[0]) == b0 && __ldcg(&line->len[1]) == b1) flag = 1;
+      } else if ((t >> 2) != serial && atomicCAS(&line->tag, t, (serial << 2) | 1ull) == t) {
+        flag = 2;
+      }
+      m.s->bc_flag = flag;
+      atomicAdd(&ctl->bc_gate_lookups, 1ull);
+    }
+    __syncthreads();
+    const int flag = m.s->bc_flag;
+    const uint4* lin = reinterpret_cast<const uint4*>(ldat);
+    if (flag == 1) {
+      const uint32_t u0 = b0 >> 4, u1 = b1 >> 4, c16 = cap >> 4;
+      bool eq = true;
+      for (uint32_t u = threadIdx.x; u < u0 + u1; u += kThreads) {
+        const uint4 a = u < u0 ? reinterpret_cast<const uint4*>(m.img0)[u] : reinterpret_cast<const uint4*>(m.img1)[u - u0];
+        const uint4 b = __ldcg(lin + (u < u0 ? u : c16 + (u - u0)));
+        eq &= a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
+      }
+      if (__syncthreads_and(eq)) {
+        n0 = __ldcg(&line->len[2]);
+        n1 = __ldcg(&line->len[3]);
+        const uint32_t v0 = n0 >> 4, v1 = n1 >> 4;
+        for (uint32_t u = threadIdx.x; u < v0 + v1; u += kThreads) {
+          if (u < v0) reinterpret_cast<uint4*>(m.img0)[u] = __ldcg(lin + 2u * c16 + u);
+          else reinterpret_cast<uint4*>(m.img1)[u - v0] = __ldcg(lin + 3u * c16 + (u - v0));
+        }
+        __syncthreads();
+        bc_hit = true;
+        if (threadIdx.x == 0) atomicAdd(&ctl->bc_gate_hits, 1ull);
+      }
+    } else if (flag == 2) {
+      const uint32_t u0 = b0 >> 4, u1 = b1 >> 4, c16 = cap >> 4;
+      uint4* lout = reinterpret_cast<uint4*>(ldat);
+      for (uint32_t u = threadIdx.x; u < u0 + u1; u += kThreads) {
+        if (u < u0) lout[u] = reinterpret_cast<const uint4*>(m.img0)[u];
+        else lout[c16 + (u - u0)] = reinterpret_cast<const uint4*>(m.img1)[u - u0];
+      }
+      bc_claim = true;
     }
   }
+  if (bc_hit) {
+    prefetch_next();
+  } else {
+  const bool ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
+  const bool ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
+  prefetch_next();
   QC_PHASE(1);
   if (!ok0 || !ok1) {
     if (threadIdx.x == 0) atomicOr(&ctl->err, (unsigned)E_CORRUPT);
@@ -349,8 +411,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
     sel.prev_len = b0;
   }
-  const uint32_t n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
-  uint32_t n1 = 1u;
+  n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
   if (has1) {
     const uint4 h = reinterpret_cast<const uint4*>(m.img1)[0];
     sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
@@ -358,6 +419,26 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     n1 = encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
   }
   QC_PHASE(3);
+  // a claimed cache line receives the outputs and is published for the rest of the gate
+  if (bc_claim && n0 != 0u && n1 != 0u) {
+    const uint32_t v0 = n0 >> 4, v1 = n1 >> 4, c16 = cap >> 4;
+    uint4* lout = reinterpret_cast<uint4*>(ldat);
+    for (uint32_t u = threadIdx.x; u < v0 + v1; u += kThreads) {
+      if (u < v0) lout[2u * c16 + u] = reinterpret_cast<const uint4*>(m.img0)[u];
+      else lout[3u * c16 + (u - v0)] = reinterpret_cast<const uint4*>(m.img1)[u - v0];
+    }
+    if (threadIdx.x == 0) {
+      line->key = key;
+      line->len[0] = b0;
+      line->len[1] = b1;
+      line->len[2] = n0;
+      line->len[3] = n1;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicExch(&line->tag, (serial << 2) | 2ull);
+  }
+  }
   if (n0 == 0u || n1 == 0u) return false;
   if (threadIdx.x < 32u) {
     const uint32_t q0 = pages_for(n0, kc), q1 = has1 ? pages_for(n1, kc) : 0u;
@@ -396,8 +477,10 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_
   st.cc.n = &s_cache_n;
   cta_begin(L.P, st, L.prof, s_ph);
   const uint32_t S = gate_bits(L);
+  const unsigned long long serial = L.P.ctl->gates + 1ull;
+  const bool bc_on = L.bc != nullptr && L.P.ctl->bc_off == 0u;
   for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x)
-    if (!gate_item<VPT, true>(L, item, S, m, st)) break;
+    if (!gate_item<VPT, true>(L, item, S, serial, bc_on, m, st)) break;
   cp_async_wait_all();  // no copy may still target shared memory at exit
   cta_end(L, st, s_ph);
 }
@@ -419,6 +502,8 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
   st.cc.n = &s_cache_n;
   int cur = -1;
   uint32_t S = 64;
+  unsigned long long serial = 0;
+  bool bc_on = false;
   for (unsigned long long g = blockIdx.x; g < total; g += gridDim.x) {
     int lo = 0, hi = njobs - 1;  // last job whose first item is <= g
     while (lo < hi) {
@@ -431,8 +516,10 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
       cur = lo;
       cta_begin(jobs[cur].L.P, st, jobs[cur].L.prof, s_ph);
       S = gate_bits(jobs[cur].L);
+      serial = jobs[cur].L.P.ctl->gates + 1ull;
+      bc_on = jobs[cur].L.bc != nullptr && jobs[cur].L.P.ctl->bc_off == 0u;
     }
-    gate_item<VPT, false>(jobs[cur].L, g - jobs[cur].begin, S, m, st);
+    gate_item<VPT, false>(jobs[cur].L, g - jobs[cur].begin, S, serial, bc_on, m, st);
   }
   if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
 }
@@ -475,6 +562,21 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
     ctl->dE = 0;
     if (ctl->E > ctl->Emax) ctl->Emax = ctl->E;
     ctl->gates += 1;
+    // block cache: pause it after kBcZeroGates gates in a row with lookups and no hit
+    // (Section 3.4 switches it off when the hit rate stays zero), probe again later
+    const unsigned long long lk = ctl->bc_gate_lookups, hit = ctl->bc_gate_hits;
+    ctl->bc_lookups += lk;
+    ctl->bc_hits += hit;
+    ctl->bc_gate_lookups = ctl->bc_gate_hits = 0;
+    if (ctl->bc_off) {
+      ctl->bc_off -= 1u;
+    } else if (lk) {
+      ctl->bc_zero_streak = hit ? 0u : ctl->bc_zero_streak + 1u;
+      if (ctl->bc_zero_streak >= kBcZeroGates) {
+        ctl->bc_off = kBcPause;
+        ctl->bc_zero_streak = 0u;
+      }
+    }
     const unsigned long long in_use = P.npages - s_top;
     if (in_use > ctl->peak_pages) ctl->peak_pages = in_use;
   }

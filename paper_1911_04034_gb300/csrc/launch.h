@@ -33,6 +33,7 @@ struct GateLaunch {
   float* trace;                  // selector training records (device) or nullptr
   unsigned long long* trace_n;
   unsigned long long trace_cap;
+  uint8_t* bc;                   // block cache lines (kBcLines of bc_line_bytes) or nullptr
 };
 
 // One gate of one simulator inside a batched launch; its work items are the global

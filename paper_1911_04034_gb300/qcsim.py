@@ -41,6 +41,7 @@ class Stats(C.Structure):
         ("sig_bits_current", C.c_int32), ("level", C.c_int32), ("chunk_log2", C.c_int32), ("block_log2", C.c_int32),
         ("phase_cycles", C.c_uint64 * 6),
         ("split_trials", C.c_uint64),
+        ("cache_lookups", C.c_uint64), ("cache_hits", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -68,6 +69,7 @@ def lib():
             "sim_create_ex": [i32, i32, i32, dbl, u64, dbl, i32, u64, pp],
             "sim_destroy": [vp],
             "sim_checkpoint_size": [vp, C.POINTER(C.c_uint64)],
+            "sim_set_block_cache": [vp, i32],
             "sim_checkpoint_save": [vp, vp, u64, i32],
             "sim_checkpoint_load": [vp, vp, u64, i32],
             "sim_set_stream": [vp, vp],
@@ -204,6 +206,10 @@ class Sim:
             assert p.size == 1864
         _check(lib().sim_set_selector(self._h, int(selector), C.c_void_p(_ptr(p)) if p is not None else None),
                "sim_set_selector")
+
+    def set_block_cache(self, on: bool = True) -> None:
+        """Section 3.4 compressed block cache for later gates (see sim_set_block_cache)."""
+        _check(lib().sim_set_block_cache(self._h, int(bool(on))), "sim_set_block_cache")
 
     def checkpoint(self, out=None):
         """The compressed state as a checkpoint (Section 3.5): a numpy uint8 array, or
