@@ -136,6 +136,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(ms: float, updates: float, dist, device: str) -> tuple[float, float]:
+    """Replicas: the job's time is the slowest rank's, its work the sum of all ranks'."""
+    import torch
+
+    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
+def replica_seed(rank: int) -> int:
+    """Each replica simulates its own random circuit of the same family and size."""
+    return SEED + rank
+
+
 def run_gpu(args) -> dict | None:
     import torch
 
@@ -152,7 +168,7 @@ def run_gpu(args) -> dict | None:
         dist.init_process_group("nccl")
     n = ROWS * COLS
     depth = max(20, 1 + args.warmup + 2 * args.steps)
-    gates = Cc.rcs(ROWS, COLS, depth, seed=SEED + rank)
+    gates = Cc.rcs(ROWS, COLS, depth, seed=replica_seed(rank))
     layers = layers_of(gates, n, depth)
     raw = 16 << n
     stream = torch.cuda.Stream()
@@ -221,15 +237,9 @@ def run_gpu(args) -> dict | None:
                      "sim_fidelity")
         fid = float(F.value)
         sv.close()
-    ms_max = ms
-    upd_total = updates
+    ms_max, upd_total = ms, updates
     if dist is not None:
-        t = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max = float(tmax[0])
-        upd_total = float(t[1])
+        ms_max, upd_total = reduce_over_ranks(ms, updates, dist, "cuda")
         dist.destroy_process_group()
     if rank != 0:
         return None

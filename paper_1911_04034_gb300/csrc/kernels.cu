@@ -68,6 +68,58 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// Bulk asynchronous shared -> global copy (one page of a new image); the issuing thread
+// later waits until the source has been read before the buffer is reused.
+__device__ __forceinline__ void bulk_store(void* gmem, const void* smem, uint32_t bytes) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gmem), "r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// Makes this thread's earlier shared-memory writes visible to bulk copies.
+__device__ __forceinline__ void fence_to_bulk() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Writes the two new images of a work item: pages by bulk copies (a lane of warp 0 per
+// page), inline images and the directory entries by plain stores (warp 1).  All threads
+// call it; the images in shared memory must stay untouched until bulk_wait_read.
+__device__ __forceinline__ void commit_images(const Pool& P, unsigned long long c0, const uint8_t* img0, uint32_t n0,
+                                              const uint32_t* pg0, uint32_t np0, bool has1, unsigned long long c1,
+                                              const uint8_t* img1, uint32_t n1, const uint32_t* pg1, uint32_t np1) {
+  if (threadIdx.x < 32u) {
+    const uint32_t tot = np0 + (has1 ? np1 : 0u);
+    bool issued = false;
+    for (uint32_t k = threadIdx.x; k < tot; k += 32u) {
+      const bool second = k >= np0;
+      const uint32_t q = second ? k - np0 : k, bytes = second ? n1 : n0;
+      const uint32_t len = min((uint32_t)kPage, bytes - q * kPage);
+      if (!issued) fence_to_bulk();
+      bulk_store(P.pages + (unsigned long long)(second ? pg1[q] : pg0[q]) * kPage,
+                 (second ? img1 : img0) + q * kPage, len);
+      issued = true;
+    }
+    if (issued) bulk_commit();
+  } else if (threadIdx.x < 64u) {
+    const uint32_t lane = threadIdx.x - 32u;
+    for (int w = 0; w < (has1 ? 2 : 1); ++w) {
+      uint32_t* e = dir_entry(P, w ? c1 : c0);
+      const uint32_t bytes = w ? n1 : n0, np = w ? np1 : np0;
+      const uint32_t* pg = w ? pg1 : pg0;
+      if (np == 0u) {
+        const uint4* src = reinterpret_cast<const uint4*>(w ? img1 : img0);
+        for (uint32_t u = lane; u < bytes / 16u; u += 32u) reinterpret_cast<uint4*>(e + 4)[u] = src[u];
+      } else {
+        for (uint32_t q = lane; q < np; q += 32u) e[4 + q] = pg[q];
+      }
+      if (lane == 0) {
+        e[0] = bytes;
+        e[1] = np;
+      }
+    }
+  }
+}
+
 // Pulls one page of a later item's image into L2 (no data returned to the SM).
 __device__ __forceinline__ void prefetch_l2_page(const void* gmem) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"((uint32_t)kPage) : "memory");
@@ -162,7 +214,9 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     m.ph[6] = now_;                     \
   }
   // one barrier that also broadcasts thread 0's view of the error word (and publishes
-  // the entries prefetched during the previous item)
+  // the entries prefetched during the previous item); the previous item's bulk page
+  // stores must have read the image buffers before they are refilled
+  bulk_wait_read();
   if (PREF) cp_async_wait_all();
   if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned int*)&ctl->err) != 0u)) return false;
   const bool have_entries = PREF && st.next_item == item;
@@ -440,6 +494,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   }
   if (n0 == 0u || n1 == 0u) return false;
+  fence_to_bulk();  // every thread's image writes, before the barrier below, for the bulk page stores
   if (threadIdx.x < 32u) {
     const uint32_t q0 = pages_for(n0, kc), q1 = has1 ? pages_for(n1, kc) : 0u;
     const bool ok = alloc_pages_warp(P, st.cc, ent0 + 4, q0, ent1 + 4, q1);
@@ -452,8 +507,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   __syncthreads();
   if (m.oom[0]) return false;
-  store_image_block(P, c0, m.img0, n0, ent0 + 4, m.np[0]);
-  if (has1) store_image_block(P, c1, m.img1, n1, ent1 + 4, m.np[1]);
+  commit_images(P, c0, m.img0, n0, ent0 + 4, m.np[0], has1, c1, m.img1, n1, ent1 + 4, m.np[1]);
   st.dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
   st.wr += n0 + (has1 ? n1 : 0u);
   __syncthreads();
@@ -482,6 +536,7 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_
   for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x)
     if (!gate_item<VPT, true>(L, item, S, serial, bc_on, m, st)) break;
   cp_async_wait_all();  // no copy may still target shared memory at exit
+  bulk_wait_all();      // nor read from it
   cta_end(L, st, s_ph);
 }
 
@@ -521,6 +576,7 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
     }
     gate_item<VPT, false>(jobs[cur].L, g - jobs[cur].begin, S, serial, bc_on, m, st);
   }
+  bulk_wait_all();  // no bulk page store may still read shared memory at exit
   if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
 }
 
