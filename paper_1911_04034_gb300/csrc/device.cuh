@@ -559,7 +559,7 @@ constexpr int kTraceFloats = 20;  // features[16], best mode, STREAM and SPLIT s
 
 struct SelCtx {
   int selector;                    // 0: the mode set decides; 2: the network decides SPLIT trials
-  const unsigned short* mlp;       // bfloat16 parameters (device), selector 2
+  const unsigned short* mlp;       // bfloat16 parameters (16-byte aligned; a shared-memory copy in k_gate), selector 2
   uint32_t gfeat;                  // gate features: bit0 real, 1 diagonal, 2 permutation, 3 target in chunk
   uint32_t S_gate;                 // significant bits the controller chose for this gate
   uint32_t prev_hdr[4];            // header of the chunk's previous image
@@ -611,24 +611,40 @@ __device__ __forceinline__ void zero_group_counts(const uint64_t* tile, uint32_t
 
 // Warp-level inference; every lane of the warp must call it.  Returns (to all lanes)
 // whether SPLIT has the largest of the six mode logits (first maximum wins).
+// bfloat16 pair (one 32-bit word: element 2i in the low half) to two floats.
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// One unit's float32 sum over n inputs (n a multiple of 8) in input order, with its
+// weights read as 16-byte vectors from w (16-byte aligned) and input i broadcast from
+// lane i of v.
+template <int NIN>
+__device__ __forceinline__ float sel_unit(const unsigned short* w, float v) {
+  const uint4* wv = reinterpret_cast<const uint4*>(w);
+  float acc = 0.0f;
+#pragma unroll
+  for (int q = 0; q < NIN / 8; ++q) {
+    const uint4 p = wv[q];
+    const uint32_t u[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc = __fadd_rn(acc, __fmul_rn(bf16_lo(u[k]), __shfl_sync(0xffffffffu, v, 8 * q + 2 * k)));
+      acc = __fadd_rn(acc, __fmul_rn(bf16_hi(u[k]), __shfl_sync(0xffffffffu, v, 8 * q + 2 * k + 1)));
+    }
+  }
+  return acc;
+}
+
 __device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint32_t zre, uint32_t zim) {
   const int lane = threadIdx.x & 31;
-  const unsigned short* w = sel.mlp;
+  const unsigned short* w = sel.mlp;  // W1 (512) b1 (32) W2 (1024) b2 (32) W3 (256) b3 (8)
   const float x = lane < 16 ? sel_feature(sel, kc, lane, zre, zim) : 0.0f;
-  float acc = 0.0f;
-  for (int i = 0; i < 16; ++i) acc = __fadd_rn(acc, __fmul_rn(bf16_at(w, 16 * lane + i), __shfl_sync(0xffffffffu, x, i)));
-  acc = __fadd_rn(acc, bf16_at(w, 512 + lane));
+  float acc = __fadd_rn(sel_unit<16>(w + 16 * lane, x), bf16_at(w, 512 + lane));
   const float h1 = acc > 0.0f ? acc : 0.0f;
-  acc = 0.0f;
-  for (int i = 0; i < 32; ++i)
-    acc = __fadd_rn(acc, __fmul_rn(bf16_at(w, 544 + 32 * lane + i), __shfl_sync(0xffffffffu, h1, i)));
-  acc = __fadd_rn(acc, bf16_at(w, 1568 + lane));
+  acc = __fadd_rn(sel_unit<32>(w + 544 + 32 * lane, h1), bf16_at(w, 1568 + lane));
   const float h2 = acc > 0.0f ? acc : 0.0f;
   const int o = lane & 7;
-  acc = 0.0f;
-  for (int i = 0; i < 32; ++i)
-    acc = __fadd_rn(acc, __fmul_rn(bf16_at(w, 1600 + 32 * o + i), __shfl_sync(0xffffffffu, h2, i)));
-  acc = __fadd_rn(acc, bf16_at(w, 1856 + o));
+  acc = __fadd_rn(sel_unit<32>(w + 1600 + 32 * o, h2), bf16_at(w, 1856 + o));
   float mx = __shfl_sync(0xffffffffu, acc, 0);
   for (int m = 1; m < 6; ++m) {
     const float v = __shfl_sync(0xffffffffu, acc, m);

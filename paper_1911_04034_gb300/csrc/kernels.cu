@@ -33,7 +33,7 @@ __host__ __device__ __forceinline__ uint32_t pagelist_words(int kc) { return (ma
 __host__ __device__ __forceinline__ uint32_t imgbuf(int kc) { return imgcap(kc) + 16u; }
 size_t gate_smem_bytes(int kc) {
   return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgbuf(kc)) + 4 * size_t(dir_stride(kc)) +
-         round16(sizeof(ScanSmem));
+         round16(sizeof(ScanSmem)) + round16(2 * kMlpParams);
 }
 size_t codec_smem_bytes(int kc) {
   return size_t(tile_words(kc)) * 8 + size_t(codedcap(kc)) + 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
@@ -48,6 +48,7 @@ struct GateSmem {
   uint32_t* ent[2][2];    // two sets of copies of the two directory entries (header, page
                           // ids or image): the current item's and the next item's
   ScanSmem* s;
+  unsigned short* mlp;    // the selector network's parameters, copied once per launch
   long long* ph;          // per-phase cycles, [6] = last clock (profiling)
   int* oom;
   uint32_t* np;
@@ -137,6 +138,7 @@ __device__ __forceinline__ GateSmem gate_smem(uint8_t* smem, int kc, uint32_t di
   m.ent[1][0] = m.ent[0][1] + dir_words;
   m.ent[1][1] = m.ent[1][0] + dir_words;
   m.s = reinterpret_cast<ScanSmem*>(m.ent[1][1] + dir_words);
+  m.mlp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint8_t*>(m.s) + round16(sizeof(ScanSmem)));
   m.ph = ph;
   m.oom = oom;
   m.np = np;
@@ -161,6 +163,17 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
     for (int k = 0; k < 6; ++k) ph[k] = 0;
     ph[6] = clock64();
   }
+}
+
+// The selector network's parameters into shared memory (all threads; the next barrier
+// publishes them).
+__device__ __forceinline__ void load_selector(const GateLaunch& L, const GateSmem& m) {
+  if (L.selector != 2 || !L.mlp) return;
+  const uint4* src = reinterpret_cast<const uint4*>(L.mlp);
+  for (uint32_t u = threadIdx.x; u < (uint32_t)(2 * kMlpParams) / 16u; u += kThreads)
+    reinterpret_cast<uint4*>(m.mlp)[u] = src[u];
+  if (threadIdx.x < (uint32_t)((2 * kMlpParams) % 16) / 2u)
+    m.mlp[(2 * kMlpParams) / 16 * 8 + threadIdx.x] = L.mlp[(2 * kMlpParams) / 16 * 8 + threadIdx.x];
 }
 
 // Warp 0: hands the CTA's page cache and counters back to the simulator.
@@ -453,7 +466,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   QC_PHASE(2);
   SelCtx sel;
   sel.selector = L.selector;
-  sel.mlp = L.mlp;
+  sel.mlp = m.mlp;
   sel.gfeat = L.gfeat;
   sel.S_gate = S;
   sel.trace = L.trace;
@@ -530,6 +543,7 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_
   st.cc.ids = s_cache;
   st.cc.n = &s_cache_n;
   cta_begin(L.P, st, L.prof, s_ph);
+  load_selector(L, m);
   const uint32_t S = gate_bits(L);
   const unsigned long long serial = L.P.ctl->gates + 1ull;
   const bool bc_on = L.bc != nullptr && L.P.ctl->bc_off == 0u;
@@ -569,7 +583,9 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
     if (lo != cur) {
       if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
       cur = lo;
+      __syncthreads();  // the previous job's items are done with the shared parameters
       cta_begin(jobs[cur].L.P, st, jobs[cur].L.prof, s_ph);
+      load_selector(jobs[cur].L, m);
       S = gate_bits(jobs[cur].L);
       serial = jobs[cur].L.P.ctl->gates + 1ull;
       bc_on = jobs[cur].L.bc != nullptr && jobs[cur].L.P.ctl->bc_off == 0u;
