@@ -53,10 +53,17 @@ struct GateSmem {
   int* oom;
   uint32_t* np;
 };
-struct GateCta {
-  CtaCache cc;
+// Per-CTA counters that only thread 0 updates (kept in shared memory so that they
+// hold no registers during the codec phases).
+struct CtaAcc {
   long long dE;
   unsigned long long rd, wr;
+  unsigned long long key;  // block-cache key of the running item
+};
+struct GateCta {
+  CtaCache cc;
+  CtaAcc* acc;
+  unsigned int err;        // thread 0: the error word as read during the previous item
   int pp;
   int cur;                        // directory-entry buffer set of the current item
   unsigned long long next_item;   // item whose entries were prefetched into set cur ^ 1
@@ -154,8 +161,11 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
     if (threadIdx.x == 0) *st.cc.n = n;
     __syncwarp();
   }
-  st.dE = 0;
-  st.rd = st.wr = 0;
+  if (threadIdx.x == 0) {
+    st.acc->dE = 0;
+    st.acc->rd = st.acc->wr = 0;
+  }
+  st.err = 0u;
   st.pp = 0;
   st.cur = 0;
   st.next_item = ~0ull;
@@ -187,9 +197,9 @@ __device__ __forceinline__ void cta_end(const GateLaunch& L, GateCta& st, const 
     for (int k = 0; k < 6; ++k)
       if (ph[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)ph[k]);
   L.P.cache_n[blockIdx.x] = n;
-  if (st.dE) atomicAdd(&ctl->dE, (unsigned long long)st.dE);
-  if (st.rd) atomicAdd(&ctl->bytes_in, st.rd);
-  if (st.wr) atomicAdd(&ctl->bytes_out, st.wr);
+  if (st.acc->dE) atomicAdd(&ctl->dE, (unsigned long long)st.acc->dE);
+  if (st.acc->rd) atomicAdd(&ctl->bytes_in, st.acc->rd);
+  if (st.acc->wr) atomicAdd(&ctl->bytes_out, st.acc->wr);
 }
 
 // Section 3.7: the bound of the running gate, from E after the previous gate.  Every
@@ -231,24 +241,25 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   // stores must have read the image buffers before they are refilled
   bulk_wait_read();
   if (PREF) cp_async_wait_all();
-  if (__syncthreads_or(threadIdx.x == 0 && (*(volatile unsigned int*)&ctl->err) != 0u)) return false;
+  if (__syncthreads_or(threadIdx.x == 0 && st.err != 0u)) return false;
   const bool have_entries = PREF && st.next_item == item;
   if (PREF && st.next_item != ~0ull) st.cur ^= 1;
   st.next_item = ~0ull;
   uint32_t* const ent0 = m.ent[st.cur][0];
   uint32_t* const ent1 = m.ent[st.cur][1];
+  // the item's chunks (recomputed at commit rather than kept through the codec)
+  auto chunks_of = [&](unsigned long long& x0, unsigned long long& x1) {
+    if (L.pair) {
+      x0 = item_chunk(L, item) | L.hi_vals;
+      x1 = x0 | L.pair_bit;
+    } else {
+      x0 = item_chunk(L, 2ull * item) | L.hi_vals;
+      x1 = 2ull * item + 1 < L.nact ? (item_chunk(L, 2ull * item + 1) | L.hi_vals) : 0ull;
+    }
+  };
   unsigned long long c0, c1;
-  bool has1;
-  if (L.pair) {
-    c0 = item_chunk(L, item) | L.hi_vals;
-    c1 = c0 | L.pair_bit;
-    has1 = true;
-  } else {
-    const unsigned long long k0 = 2ull * item;
-    c0 = item_chunk(L, k0) | L.hi_vals;
-    has1 = k0 + 1 < L.nact;
-    c1 = has1 ? (item_chunk(L, k0 + 1) | L.hi_vals) : 0ull;
-  }
+  chunks_of(c0, c1);
+  const bool has1 = L.pair || 2ull * item + 1 < L.nact;
   // stage 1: both directory entries (warp 0 and warp 1), unless prefetched
   if (!have_entries) {
     if (threadIdx.x < 32u) {
@@ -297,7 +308,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   // stored as +0), and its image does not depend on the bound: skip it.
   const bool z0 = np0 == 0 && b0 == 16u && ent0[4] == 0u;
   const bool z1 = !has1 || (np1 == 0 && b1 == 16u && ent1[4] == 0u);
-  st.rd += b0 + b1;
+  if (threadIdx.x == 0) st.acc->rd += b0 + b1;
   if (z0 && z1) {
     QC_PHASE(5);
     return true;
@@ -328,8 +339,8 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
         }
         w0[0] = n0;
         w1[0] = n1;
-        st.dE += (long long)n0 + (long long)n1 - (long long)b0 - (long long)b1;
-        st.wr += n0 + n1;
+        st.acc->dE += (long long)n0 + (long long)n1 - (long long)b0 - (long long)b1;
+        st.acc->wr += n0 + n1;
       }
     }
     QC_PHASE(5);
@@ -371,14 +382,12 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   // Section 3.4: an earlier item of this gate with the same two input blocks left its
   // outputs in the block cache (confirmed byte by byte); otherwise claim the line
   bool bc_hit = false, bc_claim = false;
-  BcLine* line = nullptr;
-  uint8_t* ldat = nullptr;
-  unsigned long long key = 0;
   uint32_t n0 = 0, n1 = 1;
   if (L.bc && bc_on && has1) {
-    key = bc_key(m.img0, b0, m.img1, b1, *m.s);
-    line = reinterpret_cast<BcLine*>(L.bc + (key % (unsigned long long)kBcLines) * bc_line_bytes(cap));
-    ldat = reinterpret_cast<uint8_t*>(line) + kBcHead;
+    const unsigned long long key = bc_key(m.img0, b0, m.img1, b1, *m.s);
+    if (threadIdx.x == 0) st.acc->key = key;
+    BcLine* line = reinterpret_cast<BcLine*>(L.bc + (key % (unsigned long long)kBcLines) * bc_line_bytes(cap));
+    uint8_t* ldat = reinterpret_cast<uint8_t*>(line) + kBcHead;
     if (threadIdx.x == 0) {
       const unsigned long long t = atomicAdd(&line->tag, 0ull);
       int flag = 0;
@@ -486,8 +495,13 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     n1 = encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
   }
   QC_PHASE(3);
+  // the error word for the next item's check (the load completes while this one ends)
+  if (threadIdx.x == 0) st.err = *(volatile unsigned int*)&ctl->err;
   // a claimed cache line receives the outputs and is published for the rest of the gate
   if (bc_claim && n0 != 0u && n1 != 0u) {
+    const unsigned long long key = st.acc->key;
+    BcLine* line = reinterpret_cast<BcLine*>(L.bc + (key % (unsigned long long)kBcLines) * bc_line_bytes(cap));
+    uint8_t* ldat = reinterpret_cast<uint8_t*>(line) + kBcHead;
     const uint32_t v0 = n0 >> 4, v1 = n1 >> 4, c16 = cap >> 4;
     uint4* lout = reinterpret_cast<uint4*>(ldat);
     for (uint32_t u = threadIdx.x; u < v0 + v1; u += kThreads) {
@@ -520,9 +534,16 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   __syncthreads();
   if (m.oom[0]) return false;
-  commit_images(P, c0, m.img0, n0, ent0 + 4, m.np[0], has1, c1, m.img1, n1, ent1 + 4, m.np[1]);
-  st.dE += (long long)n0 - (long long)b0 + (has1 ? (long long)n1 - (long long)b1 : 0ll);
-  st.wr += n0 + (has1 ? n1 : 0u);
+  {
+    unsigned long long x0, x1;
+    chunks_of(x0, x1);
+    commit_images(P, x0, m.img0, n0, ent0 + 4, m.np[0], has1, x1, m.img1, n1, ent1 + 4, m.np[1]);
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t i0 = ent0[0], i1 = has1 ? ent1[0] : 0u;  // the old image lengths (entry copies)
+    st.acc->dE += (long long)n0 - (long long)i0 + (has1 ? (long long)n1 - (long long)i1 : 0ll);
+    st.acc->wr += n0 + (has1 ? n1 : 0u);
+  }
   __syncthreads();
   QC_PHASE(4);
 
@@ -538,10 +559,12 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_
   __shared__ uint32_t s_np[2];
   __shared__ uint32_t s_cache[kCacheCap];
   __shared__ uint32_t s_cache_n;
+  __shared__ CtaAcc s_acc;
   const GateSmem m = gate_smem(smem, L.P.kc, L.P.dir_words, s_ph, &s_oom, s_np);
   GateCta st;
   st.cc.ids = s_cache;
   st.cc.n = &s_cache_n;
+  st.acc = &s_acc;
   cta_begin(L.P, st, L.prof, s_ph);
   load_selector(L, m);
   const uint32_t S = gate_bits(L);
@@ -565,10 +588,12 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
   __shared__ uint32_t s_np[2];
   __shared__ uint32_t s_cache[kCacheCap];
   __shared__ uint32_t s_cache_n;
+  __shared__ CtaAcc s_acc;
   const GateSmem m = gate_smem(smem, jobs[0].L.P.kc, jobs[0].L.P.dir_words, s_ph, &s_oom, s_np);
   GateCta st;
   st.cc.ids = s_cache;
   st.cc.n = &s_cache_n;
+  st.acc = &s_acc;
   int cur = -1;
   uint32_t S = 64;
   unsigned long long serial = 0;
