@@ -200,19 +200,15 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t fo, uint32_t
     s.wand[pp][w] = wa;
   }
   __syncthreads();
-  uint32_t base = 0, tot = 0, o = 0, a = 0xffffffffu;
-#pragma unroll
-  for (int i = 0; i < kWarps; ++i) {
-    const uint32_t x = s.wsum[pp][i];
-    base += i < w ? x : 0u;
-    tot += x;
-    o |= s.wor[pp][i];
-    a &= s.wand[pp][i];
-  }
+  // lane i < kWarps reads warp i's totals; warp reductions combine them
+  const uint32_t x = lane < kWarps ? s.wsum[pp][lane] : 0u;
+  const uint32_t xo = lane < kWarps ? s.wor[pp][lane] : 0u;
+  const uint32_t xa = lane < kWarps ? s.wand[pp][lane] : 0xffffffffu;
+  const uint32_t base = __reduce_add_sync(0xffffffffu, lane < w ? x : 0u);
   pp ^= 1;
-  *total = tot;
-  *all_or = o;
-  *all_and = a;
+  *total = __reduce_add_sync(0xffffffffu, x);
+  *all_or = __reduce_or_sync(0xffffffffu, xo);
+  *all_and = __reduce_and_sync(0xffffffffu, xa);
   return base + inc - v;
 }
 
@@ -232,24 +228,18 @@ __device__ __forceinline__ void block_scan2(uint32_t v, uint32_t v2, uint32_t fo
     s.wand[pp][w] = wa;
   }
   __syncthreads();
-  uint32_t base = 0, tot = 0, base2 = 0, tot2 = 0, o = 0, a = 0xffffffffu;
-#pragma unroll
-  for (int i = 0; i < kWarps; ++i) {
-    const uint32_t x = s.wsum[pp][i], x2 = s.wsum2[pp][i];
-    base += i < w ? x : 0u;
-    base2 += i < w ? x2 : 0u;
-    tot += x;
-    tot2 += x2;
-    o |= s.wor[pp][i];
-    a &= s.wand[pp][i];
-  }
+  const uint32_t x = lane < kWarps ? s.wsum[pp][lane] : 0u, x2 = lane < kWarps ? s.wsum2[pp][lane] : 0u;
+  const uint32_t xo = lane < kWarps ? s.wor[pp][lane] : 0u;
+  const uint32_t xa = lane < kWarps ? s.wand[pp][lane] : 0xffffffffu;
+  const uint32_t base = __reduce_add_sync(0xffffffffu, lane < w ? x : 0u);
+  const uint32_t base2 = __reduce_add_sync(0xffffffffu, lane < w ? x2 : 0u);
   pp ^= 1;
   *ex = base + inc - v;
   *ex2 = base2 + inc2 - v2;
-  *total = tot;
-  *total2 = tot2;
-  *all_or = o;
-  *all_and = a;
+  *total = __reduce_add_sync(0xffffffffu, x);
+  *total2 = __reduce_add_sync(0xffffffffu, x2);
+  *all_or = __reduce_or_sync(0xffffffffu, xo);
+  *all_and = __reduce_and_sync(0xffffffffu, xa);
 }
 
 // The leading three bytes of a value that a thread's run of coded values leaves for its
