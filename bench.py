@@ -443,7 +443,7 @@ def run_grover(args) -> dict:
     from paper_1911_04034_gb300 import qcsim
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    n, iters = args.grover_n, 8
+    n, iters = args.grover_n, args.grover_iters
     gates, marked = Cc.grover(n, iters, seed=SEED)
     per_iter = 4 * n + 2
     raw = 16 << n
@@ -457,7 +457,10 @@ def run_grover(args) -> dict:
     out = {}
     for name, sel in runs:
         stream = torch.cuda.Stream()
-        s = qcsim.Sim(n, 20, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=raw + raw // 8, stream=stream)
+        pool = int(args.pool_gb * 1e9) if args.pool_gb else raw + raw // 8
+        budget = pool if args.ladder == 2 else raw // 4
+        s = qcsim.Sim(n, 20, args.eps, chunk_log2=args.kc, budget=budget, ladder=args.ladder, pool_bytes=pool,
+                      stream=stream)
         if sel == 2:
             s.set_selector(2, wb)
         else:
@@ -480,7 +483,8 @@ def run_grover(args) -> dict:
                      "split_trials": st["split_trials"], "eps_switch_gate": st["eps_switch_gate"],
                      "p_marked": abs(a) ** 2, "p_closed_form": math.sin((2 * iters + 1) * theta) ** 2,
                      "fidelity_lb_sum": st["fidelity_lb_sum"], "cache_lookups": st["cache_lookups"],
-                     "cache_hits": st["cache_hits"]}
+                     "cache_hits": st["cache_hits"], "peak_pages_gb": st["peak_pages_bytes"] / 1e9,
+                     "device_gb": st["device_bytes"] / 1e9, "eps_final": st["eps_current"]}
         s.close()
     head = out[runs[-1][0]]
     ratios = {}
@@ -491,8 +495,9 @@ def run_grover(args) -> dict:
     return {"metric": METRIC, "value": head["amp_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": iters,
             "warmup": 0, "ms_per_step": sum(head["ms_per_iteration"]) / iters, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"Grover search {n} qubits, 8 iterations ({per_iter} gates each), eps {args.eps}, "
-                                   f"budget raw/4, chunks 2^{args.kc}; selectors compared"
+            "config": {"workload": f"Grover search {n} qubits, {iters} iterations ({per_iter} gates each), eps {args.eps}, "
+                                   + (f"guarded ladder in a {args.pool_gb:g} GB pool" if args.ladder == 2 else "budget raw/4")
+                                   + f", chunks 2^{args.kc}; selectors compared"
                                    + ("; block cache on" if args.cache else ""),
                        "n_qubits": n, "marked": marked, "block_cache": bool(args.cache)},
             "selector": {"train_rows": nrows, "train_loss": loss, "train_seconds": train_s},
@@ -581,6 +586,9 @@ def main():
                     help="rcs30: the 30-qubit random circuit (default); batch: 256 circuits of 14-24 qubits; "
                          "qaoa34: 34-qubit QAOA in a 180 GB pool; grover: chunk-mode selectors on Grover search")
     ap.add_argument("--grover-n", type=int, default=32)
+    ap.add_argument("--grover-iters", type=int, default=8)
+    ap.add_argument("--pool-gb", type=float, default=0.0, help="grover: page pool in GB (default raw x 9/8)")
+    ap.add_argument("--ladder", type=int, default=0, help="grover: controller ladder (2 = guarded, budget = pool)")
     ap.add_argument("--selectors", default="0,1,2", help="grover: which selectors to run (0 C only, 1 exhaustive, 2 network)")
     ap.add_argument("--cache", action="store_true", help="grover: switch the compressed block cache on")
     ap.add_argument("--batch", type=int, default=256)
