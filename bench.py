@@ -172,7 +172,8 @@ def run_gpu(args) -> dict | None:
     layers = layers_of(gates, n, depth)
     raw = 16 << n
     stream = torch.cuda.Stream()
-    sim = qcsim.Sim(n, BLOCK_LOG2, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=raw + raw // 8,
+    pool = raw + raw // 8 + (64 << 20)  # page rounding + per-CTA page caches
+    sim = qcsim.Sim(n, BLOCK_LOG2, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=pool,
                     stream=stream)
     kc = sim.chunk_log2
 
@@ -267,7 +268,7 @@ def run_gpu(args) -> dict | None:
             "workload": f"random circuit {ROWS}x{COLS} grid, {n} qubits, layers {1 + args.warmup}-{args.warmup + args.steps} "
                         f"timed; eps {args.eps}; blocks 2^{BLOCK_LOG2}, chunks 2^{kc}",
             "n_qubits": n, "block_log2": BLOCK_LOG2, "chunk_log2": kc, "eps": args.eps,
-            "budget_bytes": raw // 4, "pool_bytes": raw + raw // 8, "gates_timed": int(sum(len(x) for x in timed)),
+            "budget_bytes": raw // 4, "pool_bytes": pool, "gates_timed": int(sum(len(x) for x in timed)),
             "l2": "no flush: compressed state larger than L2",
             "parallelism": "replicas" if world > 1 else "1 gpu",
         },

@@ -74,7 +74,7 @@ typedef struct sim_stats_t {
   uint64_t max_encoded_bytes; /* largest encoded_bytes seen after any gate */
   uint64_t raw_bytes;         /* 2^(n+4) */
   uint64_t inflight_bytes;    /* two decompressed blocks, 2 * 2^(block_log2 + 4) */
-  uint64_t chunks_by_mode[8]; /* chunk images by mode: ZERO CONST PERIOD STREAM RAW */
+  uint64_t chunks_by_mode[8]; /* chunk images by mode: ZERO CONST PERIOD STREAM RAW SPLIT */
   uint64_t pool_bytes;        /* page arena size */
   uint64_t pages_in_use_bytes;/* pages holding images now */
   uint64_t peak_pages_bytes;  /* most pages in use after any gate */
