@@ -184,6 +184,7 @@ struct ScanSmem {
   uint32_t zcnt[2];  // selector inputs: amplitude groups with all-zero real / imaginary parts
   unsigned long long bc_part[kWarps];  // block cache: per-warp partial hashes
   int bc_flag;                         // block cache: 0 miss, 1 candidate line, 2 line claimed
+  __align__(16) float sel_x[32];       // selector: the current layer's inputs (warp 0)
 };
 
 // Exclusive prefix sum over the CTA with one barrier; also ORs `fo` and ANDs `fa`
@@ -605,36 +606,50 @@ __device__ __forceinline__ void zero_group_counts(const uint64_t* tile, uint32_t
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-// One unit's float32 sum over n inputs (n a multiple of 8) in input order, with its
-// weights read as 16-byte vectors from w (16-byte aligned) and input i broadcast from
-// lane i of v.
+// One unit's float32 sum over NIN inputs (a multiple of 8) in input order: weights read
+// as 16-byte vectors from w (16-byte aligned), inputs as 16-byte vectors from xs (the
+// layer's inputs in shared memory), so the chain of sums waits on no shuffle.
 template <int NIN>
-__device__ __forceinline__ float sel_unit(const unsigned short* w, float v) {
+__device__ __forceinline__ float sel_unit(const unsigned short* w, const float* xs) {
   const uint4* wv = reinterpret_cast<const uint4*>(w);
+  const float4* xv = reinterpret_cast<const float4*>(xs);
   float acc = 0.0f;
 #pragma unroll
   for (int q = 0; q < NIN / 8; ++q) {
     const uint4 p = wv[q];
-    const uint32_t u[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      acc = __fadd_rn(acc, __fmul_rn(bf16_lo(u[k]), __shfl_sync(0xffffffffu, v, 8 * q + 2 * k)));
-      acc = __fadd_rn(acc, __fmul_rn(bf16_hi(u[k]), __shfl_sync(0xffffffffu, v, 8 * q + 2 * k + 1)));
-    }
+    const float4 a = xv[2 * q], b = xv[2 * q + 1];
+    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.x), a.x));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.x), a.y));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.y), a.z));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.y), a.w));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.z), b.x));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.z), b.y));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.w), b.z));
+    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.w), b.w));
   }
   return acc;
 }
 
-__device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint32_t zre, uint32_t zim) {
+// Warp-level inference (every lane of the warp calls it; xs: 32 floats of shared
+// memory, 16-byte aligned, private to the warp).  Returns to all lanes whether the
+// Solution D trial runs (SPLIT logit + 2 >= the largest mode logit).
+__device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint32_t zre, uint32_t zim, float* xs) {
   const int lane = threadIdx.x & 31;
   const unsigned short* w = sel.mlp;  // W1 (512) b1 (32) W2 (1024) b2 (32) W3 (256) b3 (8)
-  const float x = lane < 16 ? sel_feature(sel, kc, lane, zre, zim) : 0.0f;
-  float acc = __fadd_rn(sel_unit<16>(w + 16 * lane, x), bf16_at(w, 512 + lane));
+  xs[lane] = lane < 16 ? sel_feature(sel, kc, lane, zre, zim) : 0.0f;
+  __syncwarp();
+  float acc = __fadd_rn(sel_unit<16>(w + 16 * lane, xs), bf16_at(w, 512 + lane));
   const float h1 = acc > 0.0f ? acc : 0.0f;
-  acc = __fadd_rn(sel_unit<32>(w + 544 + 32 * lane, h1), bf16_at(w, 1568 + lane));
+  __syncwarp();
+  xs[lane] = h1;
+  __syncwarp();
+  acc = __fadd_rn(sel_unit<32>(w + 544 + 32 * lane, xs), bf16_at(w, 1568 + lane));
   const float h2 = acc > 0.0f ? acc : 0.0f;
+  __syncwarp();
+  xs[lane] = h2;
+  __syncwarp();
   const int o = lane & 7;
-  acc = __fadd_rn(sel_unit<32>(w + 1600 + 32 * o, h2), bf16_at(w, 1856 + o));
+  acc = __fadd_rn(sel_unit<32>(w + 1600 + 32 * o, xs), bf16_at(w, 1856 + o));
   float mx = __shfl_sync(0xffffffffu, acc, 0);
   for (int m = 1; m < 6; ++m) {
     const float v = __shfl_sync(0xffffffffu, acc, m);
@@ -1003,7 +1018,7 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
       s.zcnt[1] = zim;
     }
     if (sel->selector == 2 && threadIdx.x < 32u) {
-      const bool pick = sel_wants_split(*sel, kc, zre, zim);
+      const bool pick = sel_wants_split(*sel, kc, zre, zim, s.sel_x);
       if (threadIdx.x == 0) s.split_pick = pick ? 1 : 0;
     }
   }
