@@ -82,6 +82,30 @@ def amp_updates(gates: np.ndarray, n: int, kc: int) -> int:
     return tot
 
 
+def fp64_flops(gates: np.ndarray, n: int, kc: int) -> float:
+    """Algorithmic FP64 flops of the gate arithmetic: per amplitude pair, each output
+    component is a chain over its nonzero coefficients (the first a product, unless it
+    is +-1 and needs no arithmetic, each later one a fused multiply-add = 2 flops);
+    pairs = amplitudes in touched chunks / 2, thinned by controls inside a chunk."""
+    tot = 0.0
+    for g in gates:
+        u = [float(x) for x in g["u"]]
+        rows = ((u[0], -u[1], u[2], -u[3]), (u[0], u[1], u[2], u[3]), (u[4], -u[5], u[6], -u[7]), (u[4], u[5], u[6], u[7]))
+        per_pair = 0
+        for r in rows:
+            kept = [c for c in r if c != 0.0]
+            if kept:
+                per_pair += (0 if kept[0] in (1.0, -1.0) else 1) + 2 * (len(kept) - 1)
+        mask = int(g["ctrl_mask"])
+        amps = (1 << n) >> bin(mask >> kc).count("1")
+        tot += per_pair * (amps / 2) / (1 << bin(mask & ((1 << kc) - 1)).count("1"))
+    return tot
+
+
+# GB300 FP64 (vector pipe): 1.25 TFLOP/s nominal; a DFMA loop measured 1.2 TFLOP/s here.
+FP64_PEAK_TFLOPS = 1.25
+
+
 def peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -291,6 +315,16 @@ def run_gpu(args) -> dict | None:
             "kernel_ms_avg": kernel_ms_avg,
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else None,
+        },
+        "roofline_fp64": {
+            "bound": "alu",
+            "achieved": fp64_flops(np.concatenate(timed), n, kc) / (tm["gate_kernel_ms"] * 1e-3) / 1e12,
+            "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": fp64_flops(np.concatenate(timed), n, kc) / (tm["gate_kernel_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "kernel": "k_gate",
+            "peak_source": "nominal GB300 FP64 (vector) rate; a DFMA loop measured 1.2 TFLOP/s",
+            "note": "the fused kernel's arithmetic ceiling: dense gates cost 28 flops per amplitude pair",
         },
         "gpu_launches": 2 * tm["launches"],
         "phase_share": ({k: round(v / max(1, sum(st1["phase_cycles"])), 4) for k, v in
