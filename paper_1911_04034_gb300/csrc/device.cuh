@@ -664,18 +664,19 @@ __device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint3
 template <int VPT>
 __device__ __forceinline__ uint32_t code_word(const uint32_t c[VPT], uint32_t j0, uint32_t nv) {
   uint32_t cw = 0;
-  if (VPT >= 4) {  // j0 is a multiple of 4: the layout within the thread's bytes is fixed
+  if constexpr (VPT >= 4) {  // j0 is a multiple of 4: the layout within the thread's bytes is fixed
 #pragma unroll
     for (int k = 0; k < VPT; ++k)
       if (j0 + k < nv) cw |= c[k] << (8 * (k >> 2) + 6 - 2 * (k & 3));
     return cw << (8u * ((j0 >> 2) & 3u));
-  }
+  } else {
 #pragma unroll
-  for (int k = 0; k < VPT; ++k) {
-    const uint32_t j = j0 + k;
-    if (j < nv) cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
+    for (int k = 0; k < VPT; ++k) {
+      const uint32_t j = j0 + k;
+      if (j < nv) cw |= c[k] << (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u));
+    }
+    return cw;
   }
-  return cw;
 }
 
 // Writes the 2-bit codes and the residual stream of coded values [j0, j0 + VPT) of this

@@ -179,11 +179,10 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
 // publishes them).
 __device__ __forceinline__ void load_selector(const GateLaunch& L, const GateSmem& m) {
   if (L.selector != 2 || !L.mlp) return;
+  static_assert((2 * kMlpParams) % 16 == 0, "the parameters copy as whole 16-byte units");
   const uint4* src = reinterpret_cast<const uint4*>(L.mlp);
   for (uint32_t u = threadIdx.x; u < (uint32_t)(2 * kMlpParams) / 16u; u += kThreads)
     reinterpret_cast<uint4*>(m.mlp)[u] = src[u];
-  if (threadIdx.x < (uint32_t)((2 * kMlpParams) % 16) / 2u)
-    m.mlp[(2 * kMlpParams) / 16 * 8 + threadIdx.x] = L.mlp[(2 * kMlpParams) / 16 * 8 + threadIdx.x];
 }
 
 // Warp 0: hands the CTA's page cache and counters back to the simulator.
