@@ -150,12 +150,35 @@ sim_status sim_apply_circuit(sim_t* sim, const sim_gate* gates, size_t n_gates);
 sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const* circuits, const size_t* n_gates,
                            int use_graph);
 
+/* Runs n_circ independent circuits (n_qubits[k] qubits, circ[k][0..n_gates[k]) each)
+ * through the batched path and writes each one's statistics to out[k]: one chunk size
+ * for the batch (autotuned among 8..10 on the largest circuit when it has at least 4
+ * gates and every circuit has at least 8 qubits; else min(10, smallest n)), blocks of
+ * 2^min(n, 20), bound err_bound reached after the lossless stage at budget raw/4, page
+ * pool raw + 1/8 + 8 MiB, the gates advanced one step at a time across all circuits in
+ * one persistent launch replayed from a CUDA graph (sim_batch_apply).  The handles are
+ * created and destroyed inside the call.  Errors as sim_create_ex / sim_batch_apply. */
+sim_status sim_batch_run(int n_circ, const int* n_qubits, const sim_gate* const* circ, const size_t* n_gates,
+                         double err_bound, sim_stats_t* out);
+
 /* Chunk-size autotuner: for each candidate chunk_log2, creates a handle (budget raw/4,
  * pool raw + 1/8), applies the first half of the probe circuit, then times the fused
  * kernel over the second half; *best receives the candidate with the most amplitude
  * updates per second of kernel time, rates[i] (if not NULL) each candidate's rate. */
 sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,
                               const int* candidates, int n_candidates, int* best, double* rates);
+
+/* Changes the budget the controller compares with (Section 3.7; threshold floor(tau *
+ * bytes)) from the next gate on; the page arena keeps the size it was created with.
+ * bytes > 0, else SIM_ERR_INVALID. */
+sim_status sim_set_budget(sim_t* sim, uint64_t bytes);
+
+/* Named settings, from the next gate on: "modes" (as sim_set_modes), "selector" (0 or
+ * 1; the network needs sim_set_selector), "block_cache" (0/1, as sim_set_block_cache),
+ * "timing" (0/1/2, as sim_set_timing), "tau_ppm" (tau in millionths, (0, 1e6]),
+ * "ladder" (0/1/2; only before the first gate).  "chunk_log2" and "block_log2" are fixed
+ * at creation.  Unknown keys or values out of range: SIM_ERR_INVALID. */
+sim_status sim_set_option(sim_t* sim, const char* key, int64_t value);
 
 /* Compressed block cache (Section 3.4): on = 1 allocates 256 lines (each 64 bytes plus
  * room for four images of the largest size, 16.8 MB at chunk_log2 10) and makes later

@@ -508,6 +508,63 @@ sim_status sim_timing(sim_t* s, double* ms, uint64_t* launches, uint64_t* bytes_
   return SIM_OK;
 }
 
+sim_status sim_set_budget(sim_t* s, uint64_t bytes) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  if (bytes == 0) return fail(SIM_ERR_INVALID, "budget must be > 0");
+  if (sim_status r = s->guard()) return r;
+  CK(cudaStreamSynchronize(s->st), "sync");
+  s->budget = bytes;
+  s->cp.thresh = (unsigned long long)std::floor(s->tau * (double)bytes);
+  return SIM_OK;
+}
+
+sim_status sim_set_option(sim_t* s, const char* key, int64_t value) {
+  if (!s || !key) return fail(SIM_ERR_INVALID, "NULL argument");
+  if (sim_status r = s->guard()) return r;
+  const std::string k(key);
+  if (k == "modes") return sim_set_modes(s, (uint32_t)value);
+  if (k == "selector") {
+    if (value != 0 && value != 1) return fail(SIM_ERR_INVALID, "selector 2 needs its parameters: sim_set_selector");
+    return sim_set_selector(s, (int)value, nullptr);
+  }
+  if (k == "block_cache") return sim_set_block_cache(s, value != 0);
+  if (k == "timing") return sim_set_timing(s, (int)value);
+  if (k == "tau_ppm") {
+    if (value <= 0 || value > 1000000) return fail(SIM_ERR_INVALID, "tau_ppm must be in (0, 1000000]");
+    CK(cudaStreamSynchronize(s->st), "sync");
+    s->tau = (double)value * 1e-6;
+    s->cp.thresh = (unsigned long long)std::floor(s->tau * (double)s->budget);
+    return SIM_OK;
+  }
+  if (k == "ladder") {
+    if (value < 0 || value > 2) return fail(SIM_ERR_INVALID, "ladder must be 0, 1 or 2");
+    DevCtl h{};
+    CK(cudaMemcpyAsync(&h, s->d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s->st), "copy counters");
+    CK(cudaStreamSynchronize(s->st), "sync");
+    if (h.gates != 0) return fail(SIM_ERR_INVALID, "the ladder can only change before the first gate");
+    CtlParams& cp = s->cp;
+    cp.ladder = (int)value;
+    s->ladder = (int)value;
+    cp.nlevels = 0;
+    if (s->eps_max > 0.0) {
+      static const double paper[5] = {1e-5, 1e-4, 1e-3, 1e-2, 1e-1};
+      if (value >= 1)
+        for (double e : paper)
+          if (e < s->eps_max) s->level_eps[cp.nlevels++] = e;
+      s->level_eps[cp.nlevels++] = s->eps_max;
+    }
+    for (int l = 0; l < cp.nlevels; ++l) {
+      cp.S[l] = sig_bits_of(s->level_eps[l]);
+      cp.delta[l] = std::ldexp(1.0, 12 - cp.S[l]);
+    }
+    for (int l = 0; l <= cp.nlevels; ++l) cp.maxb[l] = qc::max_level_image(s->kc, l == 0 ? 64 : cp.S[l - 1]);
+    return SIM_OK;
+  }
+  if (k == "chunk_log2" || k == "block_log2")
+    return fail(SIM_ERR_INVALID, "%s is fixed when the handle is created (sim_create_ex)", key);
+  return fail(SIM_ERR_INVALID, "unknown option '%s'", key);
+}
+
 sim_status sim_set_block_cache(sim_t* s, int on) {
   if (!s) return fail(SIM_ERR_INVALID, "NULL argument");
   if (sim_status r = s->guard()) return r;
@@ -834,6 +891,40 @@ sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const*
     if (r != SIM_OK && worst == SIM_OK) worst = r;
   }
   return worst;
+}
+
+sim_status sim_batch_run(int n_circ, const int* n_qubits, const sim_gate* const* circ, const size_t* n_gates,
+                         double err_bound, sim_stats_t* out) {
+  if (n_circ < 1 || !n_qubits || !circ || !n_gates || !out) return fail(SIM_ERR_INVALID, "bad batch arguments");
+  int nmin = 64, big = 0;
+  for (int k = 0; k < n_circ; ++k) {
+    if (n_qubits[k] < 1 || n_qubits[k] > 40) return fail(SIM_ERR_INVALID, "n_qubits must be in [1, 40]");
+    if (n_qubits[k] < nmin) nmin = n_qubits[k];
+    if (n_qubits[k] > n_qubits[big] || (n_qubits[k] == n_qubits[big] && n_gates[k] > n_gates[big])) big = k;
+  }
+  // one chunk size for the whole batch, autotuned on the largest circuit when it is long enough
+  int kc = nmin < 10 ? nmin : 10;
+  if (n_gates[big] >= 4 && nmin >= 8) {
+    int cand[3], nc = 0;
+    for (int c = 8; c <= 10 && c <= nmin; ++c) cand[nc++] = c;
+    if (nc > 1) {
+      const int nb = n_qubits[big] < 20 ? n_qubits[big] : 20;
+      if (sim_status r = sim_autotune_chunk(n_qubits[big], nb, err_bound, circ[big], n_gates[big], cand, nc, &kc, nullptr))
+        return r;
+    }
+  }
+  std::vector<sim_t*> sims(n_circ, nullptr);
+  sim_status r = SIM_OK;
+  for (int k = 0; k < n_circ && r == SIM_OK; ++k) {
+    const uint64_t raw = 16ull << n_qubits[k];
+    const int b = n_qubits[k] < 20 ? n_qubits[k] : 20;
+    r = sim_create_ex(n_qubits[k], b, kc, err_bound, raw / 4 ? raw / 4 : 1, 0.9, 0, raw + raw / 8 + (8ull << 20), &sims[k]);
+  }
+  if (r == SIM_OK) r = sim_batch_apply(sims.data(), n_circ, circ, n_gates, 1);
+  for (int k = 0; k < n_circ && r == SIM_OK; ++k) r = sim_stats(sims[k], &out[k]);
+  for (sim_t* s : sims)
+    if (s) sim_destroy(s);
+  return r;
 }
 
 sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,

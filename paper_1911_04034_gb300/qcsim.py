@@ -70,6 +70,9 @@ def lib():
             "sim_destroy": [vp],
             "sim_checkpoint_size": [vp, C.POINTER(C.c_uint64)],
             "sim_set_block_cache": [vp, i32],
+            "sim_set_budget": [vp, u64],
+            "sim_set_option": [vp, C.c_char_p, C.c_int64],
+            "sim_batch_run": [i32, vp, vp, vp, dbl, vp],
             "sim_checkpoint_save": [vp, vp, u64, i32],
             "sim_checkpoint_load": [vp, vp, u64, i32],
             "sim_set_stream": [vp, vp],
@@ -207,6 +210,14 @@ class Sim:
         _check(lib().sim_set_selector(self._h, int(selector), C.c_void_p(_ptr(p)) if p is not None else None),
                "sim_set_selector")
 
+    def set_budget(self, nbytes: int) -> None:
+        """The controller's budget from the next gate on (see sim_set_budget)."""
+        _check(lib().sim_set_budget(self._h, int(nbytes)), "sim_set_budget")
+
+    def set_option(self, key: str, value: int) -> None:
+        """A named setting (see sim_set_option)."""
+        _check(lib().sim_set_option(self._h, key.encode(), int(value)), "sim_set_option")
+
     def set_block_cache(self, on: bool = True) -> None:
         """Section 3.4 compressed block cache for later gates (see sim_set_block_cache)."""
         _check(lib().sim_set_block_cache(self._h, int(bool(on))), "sim_set_block_cache")
@@ -306,6 +317,20 @@ def batch_apply(sims: list, circuits: list, use_graph: bool = True) -> None:
     counts = (C.c_size_t * n)(*[a.shape[0] for a in arrs])
     _check(lib().sim_batch_apply(C.cast(handles, C.c_void_p), n, C.cast(ptrs, C.c_void_p), C.cast(counts, C.c_void_p),
                                  int(bool(use_graph))), "sim_batch_apply")
+
+
+def batch_run(circuits: list, n_qubits: list, err_bound: float) -> list[dict]:
+    """Runs independent circuits through the batched path (see sim_batch_run); returns
+    each circuit's statistics."""
+    arrs = [gates_array(g) for g in circuits]
+    k = len(arrs)
+    ptrs = (C.c_void_p * k)(*[_ptr(a) for a in arrs])
+    ns = (C.c_size_t * k)(*[a.shape[0] for a in arrs])
+    qs = (C.c_int * k)(*[int(n) for n in n_qubits])
+    out = (Stats * k)()
+    _check(lib().sim_batch_run(k, C.cast(qs, C.c_void_p), C.cast(ptrs, C.c_void_p), C.cast(ns, C.c_void_p),
+                               float(err_bound), C.cast(out, C.c_void_p)), "sim_batch_run")
+    return [out[i].as_dict() for i in range(k)]
 
 
 def autotune_chunk(n_qubits: int, block_log2: int, err_bound: float, probe, candidates=(8, 9, 10, 11)):
