@@ -95,6 +95,23 @@ def test_random_circuit_bit_exact(eps, kc):
     assert np.array_equal(gpu.amplitudes().view(np.uint64), orc.amplitudes().view(np.uint64))
 
 
+@pytest.mark.parametrize("kc,n", [(0, 8), (1, 9), (2, 10), (11, 14), (11, 16)])
+def test_extreme_chunk_sizes_bit_exact(kc, n):
+    """One- to four-amplitude chunks (one value per thread, most threads idle) and the
+    largest chunks (16 values per thread, one CTA per SM), over a circuit with both
+    in-chunk and cross-chunk targets and a lossy switch."""
+    gates = Cc.rcs_n(n, 6, seed=40 + kc)
+    budget = (16 << n) // 4
+    b = min(n, max(kc, 6))
+    orc = O.CSim(n, b, kc, 1e-4, budget)
+    gpu = qc().Sim(n, b, 1e-4, chunk_log2=kc, budget=budget, pool_bytes=4 * (16 << n) + (64 << 20))
+    gpu.apply_circuit(gates)
+    orc.apply(gates)
+    assert images_equal(gpu, orc) == []
+    stats_match(gpu.stats(), orc.stats())
+    assert gpu.stats()["eps_switch_gate"] >= 0
+
+
 @pytest.mark.parametrize("ladder", [0, 1, 2])
 def test_qaoa_and_qft_bit_exact(ladder):
     n = 12
