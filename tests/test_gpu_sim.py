@@ -112,6 +112,24 @@ def test_extreme_chunk_sizes_bit_exact(kc, n):
     assert gpu.stats()["eps_switch_gate"] >= 0
 
 
+def test_subnormal_amplitudes_in_the_fused_kernel():
+    """Chunks holding subnormal amplitudes are coded at 64 bits in a lossy run, the
+    others at the bound; the images equal the oracle's."""
+    from test_oracle_sim import subnormal_circuit
+
+    n, kc = 10, 4
+    gates = subnormal_circuit()
+    orc = O.CSim(n, n, kc, 1e-4, 1)
+    gpu = qc().Sim(n, n, 1e-4, chunk_log2=kc, budget=1, pool_bytes=4 * (16 << n) + (16 << 20))
+    for k in range(len(gates)):
+        gpu.apply_circuit(gates[k:k + 1])
+        orc.apply(gates[k:k + 1])
+        assert images_equal(gpu, orc) == [], k
+    stats_match(gpu.stats(), orc.stats())
+    widths = {gpu.chunk_image(q)[1] for q in range(gpu.n_chunks)}
+    assert widths == {0, 26, 64}  # 0: ZERO chunks (qubit 9 is never touched)
+
+
 @pytest.mark.parametrize("ladder", [0, 1, 2])
 def test_qaoa_and_qft_bit_exact(ladder):
     n = 12

@@ -317,6 +317,37 @@ def test_guarded_ladder_keeps_the_state_under_the_threshold():
     assert levels[0] == 0 and levels[-1] > 0
 
 
+def subnormal_circuit():
+    """A real rotation with cos = 1e-310 (subnormal; cos^2 underflows, so the matrix is
+    unitary to the last bit) applied under a control on qubit 8 puts subnormal amplitudes
+    into the half of the state with bit 8 set; later gates stay on qubits below 8, so the
+    other half never meets them."""
+    c = 1e-310
+    U = np.array([[c, -1.0], [1.0, c]], dtype=np.complex128)
+    g = [Cc.gate(8, Cc.H), Cc.gate(0, U, {8: 1}), Cc.gate(1, Cc.H), Cc.gate(4, Cc.H), Cc.gate(5, Cc.H),
+         Cc.gate(2, Cc.SX), Cc.gate(6, Cc.H), Cc.gate(3, Cc.T), Cc.gate(7, Cc.H), Cc.gate(1, Cc.SY)]
+    return Cc.to_array(g)
+
+
+def test_chunks_with_subnormals_are_coded_at_full_width():
+    n, kc = 10, 4
+    cs = O.CSim(n, n, kc, 1e-4, 1)  # lossy from the first gate
+    cs.apply(subnormal_circuit())
+    assert cs.stats()["S_current"] == O.sig_bits(1e-4)
+    for q in range(cs.nchunks):
+        img = cs.image(q)
+        if (q >> 5) & 1:  # qubit 9 is never touched: those chunks stay ZERO
+            assert img[0] == 0
+            continue
+        vals = O.decode_chunk(img, kc)
+        bits = np.concatenate([vals.real, vals.imag]).view(np.uint64)
+        has_sub = bool(np.any(((bits >> 52) & 0x7FF == 0) & ((bits << 12) != 0)))
+        if (q >> 4) & 1:  # bit 8 of the amplitude index = bit 4 of the chunk index
+            assert has_sub and img[1] == 64
+        else:
+            assert not has_sub and img[1] == O.sig_bits(1e-4)
+
+
 def test_error_statistics_section_4_2():
     """All relative errors below the bound; errors normalised by the last kept
     mantissa unit are spread over [0, 1); lag-1 autocorrelation near zero."""
