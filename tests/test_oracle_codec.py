@@ -117,6 +117,34 @@ def test_truncation_float32_sweep():
         assert np.all(rel < eps) and np.all(np.abs(t) <= np.abs(x))
 
 
+@pytest.mark.parametrize("eps", LEVELS)
+def test_truncation_every_float32_mantissa(eps):
+    """Every float32 mantissa, with both signs, in the smallest, the unit and the largest
+    float32 binade, widened to binary64 and sent through the oracle's whole codec
+    (encode, then decode).  Truncation toward zero to m = S - 12 mantissa bits has
+    exactly one result: the value t with |t| a multiple of 2^(E-m) (E the binade of x,
+    from frexp) and |x| - 2^(E-m) < |t| <= |x|, sign kept.  Checked without the oracle's
+    formula for every value."""
+    kc = 11
+    S = O.sig_bits(eps)
+    m = S - 12
+    mant = np.arange(1 << 23, dtype=np.uint32)
+    for e32 in (1, 127, 254):
+        f = ((np.uint32(e32) << np.uint32(23)) | mant).view(np.float32).astype(np.float64)
+        x = np.concatenate([f, -f])
+        t = np.empty_like(x)
+        step = 2 << kc
+        for i in range(0, x.size, step):
+            t[i:i + step] = O.decode_chunk(O.encode_chunk(x[i:i + step], kc, S), kc).view(np.float64)
+        ax, at = np.abs(x), np.abs(t)
+        _, ex = np.frexp(ax)
+        ulp = np.ldexp(1.0, ex - 1 - m)
+        assert np.array_equal(np.signbit(t), np.signbit(x)), e32
+        assert np.all(at <= ax) and np.all(ax - at < ulp), e32
+        q = at / ulp
+        assert np.array_equal(q, np.floor(q)), e32
+
+
 def test_zero_and_negative_zero():
     for S in (16, 26, 64):
         assert O.truncate(0, S) == 0
