@@ -179,6 +179,8 @@ struct ScanSmem {
   uint32_t wand[2][kWarps];
   uint32_t wlm[2][kWarps];  // lead-byte scan: bytes set, and their values
   uint32_t wlv[2][kWarps];
+  uint32_t wlm2[2][kWarps];  // the second chunk's lead-byte scan (decode_stream32_pair)
+  uint32_t wlv2[2][kWarps];
   uint32_t bits_period;
   int split_pick;  // the selector network's decision for the chunk being encoded
   uint32_t zcnt[2];  // selector inputs: amplitude groups with all-zero real / imaginary parts
@@ -248,36 +250,70 @@ __device__ __forceinline__ void block_scan2(uint32_t v, uint32_t v2, uint32_t fo
 // keep them.  A run is summarised as (M, V): the bits of the top three bytes (of the
 // value's high word) that it sets, and their values.  Composition (earlier, later) =
 // (M1 | M2, (V1 & ~M2) | V2) is associative; this is its exclusive scan over the CTA
-// (identity (0, 0): the first value's predecessor is 0), one barrier.  Returns V.
-__device__ __forceinline__ uint32_t block_lead_scan(uint32_t M, uint32_t V, ScanSmem& s, int& pp) {
-  constexpr uint32_t kFull = 0xFFFFFF00u;  // all three leading bytes set: earlier runs no longer matter
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t im = M, iv = V;
+// (identity (0, 0): the first value's predecessor is 0), one barrier
+// (block_lead_scan returns V).
+constexpr uint32_t kLeadFull = 0xFFFFFF00u;  // all three leading bytes set: earlier runs no longer matter
+
+// The warp part: inclusive (im, iv) and exclusive (em, ev) composition within the warp.
+__device__ __forceinline__ void warp_lead_scan(uint32_t M, uint32_t V, uint32_t& im, uint32_t& iv, uint32_t& em,
+                                               uint32_t& ev) {
+  const int lane = threadIdx.x & 31;
+  im = M;
+  iv = V;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     // lanes below d already cover the whole warp prefix; full lanes cannot change
-    if (__all_sync(0xffffffffu, im == kFull || lane < d)) break;
+    if (__all_sync(0xffffffffu, im == kLeadFull || lane < d)) break;
     const uint32_t um = __shfl_up_sync(0xffffffffu, im, d), uv = __shfl_up_sync(0xffffffffu, iv, d);
     if (lane >= d) {
       iv = (uv & ~im) | iv;
       im |= um;
     }
   }
-  uint32_t em = __shfl_up_sync(0xffffffffu, im, 1), ev = __shfl_up_sync(0xffffffffu, iv, 1);
+  em = __shfl_up_sync(0xffffffffu, im, 1);
+  ev = __shfl_up_sync(0xffffffffu, iv, 1);
   if (lane == 0) em = ev = 0u;
+}
+// Earlier warps' totals, nearest first, until every leading byte is set; then the
+// thread's exclusive prefix.
+__device__ __forceinline__ uint32_t lead_prefix(const uint32_t* wlm, const uint32_t* wlv, uint32_t em, uint32_t ev) {
+  uint32_t pm = 0u, pv = 0u;
+  for (int i = (int)(threadIdx.x >> 5) - 1; i >= 0 && pm != kLeadFull; --i) {
+    pv |= wlv[i] & ~pm;
+    pm |= wlm[i];
+  }
+  return (pv & ~em) | ev;
+}
+__device__ __forceinline__ uint32_t block_lead_scan(uint32_t M, uint32_t V, ScanSmem& s, int& pp) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t im, iv, em, ev;
+  warp_lead_scan(M, V, im, iv, em, ev);
   if (lane == 31) {
     s.wlm[pp][w] = im;
     s.wlv[pp][w] = iv;
   }
   __syncthreads();
-  // earlier warps, nearest first, until every leading byte is set
-  uint32_t pm = 0u, pv = 0u;
-  for (int i = w - 1; i >= 0 && pm != kFull; --i) {
-    pv |= s.wlv[pp][i] & ~pm;
-    pm |= s.wlm[pp][i];
-  }
+  const uint32_t P = lead_prefix(s.wlm[pp], s.wlv[pp], em, ev);
   pp ^= 1;
-  return (pv & ~em) | ev;
+  return P;
+}
+// The same scan for two independent runs (two chunks), one barrier.
+__device__ __forceinline__ void block_lead_scan2(uint32_t M0, uint32_t V0, uint32_t M1, uint32_t V1, ScanSmem& s,
+                                                 int& pp, uint32_t& P0, uint32_t& P1) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t im0, iv0, em0, ev0, im1, iv1, em1, ev1;
+  warp_lead_scan(M0, V0, im0, iv0, em0, ev0);
+  warp_lead_scan(M1, V1, im1, iv1, em1, ev1);
+  if (lane == 31) {
+    s.wlm[pp][w] = im0;
+    s.wlv[pp][w] = iv0;
+    s.wlm2[pp][w] = im1;
+    s.wlv2[pp][w] = iv1;
+  }
+  __syncthreads();
+  P0 = lead_prefix(s.wlm[pp], s.wlv[pp], em0, ev0);
+  P1 = lead_prefix(s.wlm2[pp], s.wlv2[pp], em1, ev1);
+  pp ^= 1;
 }
 
 // Block cache key of a work item: a hash of its two staged images (every 16-byte
@@ -535,6 +571,92 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
   }
   __syncthreads();
   return ok;
+}
+
+// True if a staged image is a STREAM image of width S <= 32 that passes decode_block's
+// header checks: the case decode_stream32_pair takes.
+__device__ __forceinline__ bool stream32_image(const uint8_t* img, uint32_t img_bytes, int kc) {
+  const uint32_t* h = reinterpret_cast<const uint32_t*>(img);
+  const uint32_t mode = h[0] & 0xffu, S = (h[0] >> 8) & 0xffu, lp = (h[0] >> 16) & 0xffu, flags = h[0] >> 24;
+  return mode == M_STREAM && flags == 0 && lp == 0 && S >= 13u && S <= 32u && img_bytes >= 16u &&
+         h[1] + 16u == img_bytes && (h[1] & 15u) == 0 && img_bytes <= max_coded_bytes(kc) && h[2] == (2u << kc);
+}
+
+// The 2-bit code of value j0 + k from the 32-bit code word holding values j0 .. j0 + VPT - 1.
+template <int VPT>
+__device__ __forceinline__ uint32_t code_in_word(uint32_t cword, uint32_t j0, int k) {
+  if (VPT >= 4) return (cword >> (8u * ((j0 >> 2) & 3u) + 8 * (k >> 2) + 6 - 2 * (k & 3))) & 3u;
+  const uint32_t j = j0 + (uint32_t)k;
+  return (cword >> (8u * ((j >> 2) & 3u) + 6u - 2u * (j & 3u))) & 3u;
+}
+
+// Decodes the two STREAM images of a work item (both stream32_image) into their tiles
+// in one pass: decode_xor_block's steps for each chunk, the two chunks sharing every
+// barrier.  Every thread holds VPT values of each chunk (kThreads * VPT = 2^(kc+1)).
+// Returns false if either image's residual lengths disagree with its header.
+template <int VPT>
+__device__ bool decode_stream32_pair(const uint8_t* img0, const uint8_t* img1, uint32_t N, uint64_t* tile0,
+                                     uint64_t* tile1, ScanSmem& s, int& pp) {
+  const uint32_t* hd0 = reinterpret_cast<const uint32_t*>(img0);
+  const uint32_t* hd1 = reinterpret_cast<const uint32_t*>(img1);
+  const uint32_t S0 = (hd0[0] >> 8) & 0xffu, S1 = (hd1[0] >> 8) & 0xffu;
+  const uint32_t cb = code_bytes(N);
+  const uint32_t j0 = threadIdx.x * VPT;
+  const uint32_t cw0 = reinterpret_cast<const uint32_t*>(img0 + 16)[j0 >> 4];
+  const uint32_t cw1 = reinterpret_cast<const uint32_t*>(img1 + 16)[j0 >> 4];
+  uint32_t sum0 = 0u, sum1 = 0u;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    sum0 += resid_len(code_in_word<VPT>(cw0, j0, k), S0);
+    sum1 += resid_len(code_in_word<VPT>(cw1, j0, k), S1);
+  }
+  uint32_t o0, o1, total0, total1, fo, fa;
+  block_scan2(sum0, sum1, 0u, 0u, s, pp, &o0, &o1, &total0, &total1, &fo, &fa);
+  if (total0 != hd0[3] || total1 != hd1[3] || cb + resid_bytes(total0) != hd0[1] || cb + resid_bytes(total1) != hd1[1])
+    return false;
+  // explicit parts (the residual placed at [8c, S) of the high word) and each run's
+  // effect on the leading bytes
+  const uint32_t* m0 = reinterpret_cast<const uint32_t*>(img0 + 16 + cb);
+  const uint32_t* m1 = reinterpret_cast<const uint32_t*>(img1 + 16 + cb);
+  const uint32_t mh0 = (uint32_t)(trunc_mask(S0) >> 32), mh1 = (uint32_t)(trunc_mask(S1) >> 32);
+  uint32_t e0[VPT], e1[VPT];
+  uint32_t M0 = 0u, V0 = 0u, M1 = 0u, V1 = 0u;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    {
+      const uint32_t c = code_in_word<VPT>(cw0, j0, k), q = o0 >> 5, sh = o0 & 31u;
+      e0[k] = (__funnelshift_l(m0[(q + 1u) ^ 1u], m0[q ^ 1u], sh) >> (8u * c)) & mh0;
+      o0 += resid_len(c, S0);
+      const uint32_t ex = lead_explicit(c);
+      V0 = (V0 & ~ex) | (e0[k] & 0xFFFFFF00u);
+      M0 |= ex;
+    }
+    {
+      const uint32_t c = code_in_word<VPT>(cw1, j0, k), q = o1 >> 5, sh = o1 & 31u;
+      e1[k] = (__funnelshift_l(m1[(q + 1u) ^ 1u], m1[q ^ 1u], sh) >> (8u * c)) & mh1;
+      o1 += resid_len(c, S1);
+      const uint32_t ex = lead_explicit(c);
+      V1 = (V1 & ~ex) | (e1[k] & 0xFFFFFF00u);
+      M1 |= ex;
+    }
+  }
+  uint32_t P0, P1;
+  block_lead_scan2(M0, V0, M1, V1, s, pp, P0, P1);
+  uint64_t v[VPT];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    P0 = e0[k] | (P0 & lead_copied(code_in_word<VPT>(cw0, j0, k)));
+    v[k] = (uint64_t)P0 << 32;
+  }
+  store_vals<VPT>(tile0, j0, N, v);
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    P1 = e1[k] | (P1 & lead_copied(code_in_word<VPT>(cw1, j0, k)));
+    v[k] = (uint64_t)P1 << 32;
+  }
+  store_vals<VPT>(tile1, j0, N, v);
+  __syncthreads();
+  return true;
 }
 
 // ------------------------------------------------------- learned selector -- //
@@ -1055,6 +1177,206 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
   const uint32_t S = anysub ? 64u : S_req;
   if (S <= 32u) return encode_core<VPT, true>(tile, kc, S, force_mode, modes, img, img_cap, s, pp, err, sel, t);
   return encode_core<VPT, false>(tile, kc, S, force_mode, modes, img, img_cap, s, pp, err, sel, t);
+}
+
+// Step 3 of encode_core (W32) for one chunk of a pair: the codes of this thread's
+// values packed two bits each (value k at bits 2k), their residual bits, and the CONST
+// and top-level PERIOD tests.  All values of the thread exist (kThreads * VPT = N).
+template <int VPT>
+__device__ __forceinline__ void codes32_pair_part(const uint64_t* tile, uint32_t j0, const uint32_t h[VPT], uint32_t S,
+                                                  uint32_t Ptop, uint32_t& cc, uint32_t& sum, bool& cst, bool& gtop) {
+  const uint32_t* t32 = reinterpret_cast<const uint32_t*>(tile);
+  uint32_t ph = j0 > 0 ? t32[2u * tile_val(j0 - 1u) + 1u] : 0u;
+  const uint32_t a0xh = t32[2u * tile_val(0) + 1u], a0yh = t32[2u * tile_val(1) + 1u];
+  cc = 0u;
+  sum = 0u;
+  cst = true;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const uint32_t c = xor_code32(h[k], ph);
+    cc |= c << (2 * k);
+    sum += resid_len(c, S);
+    ph = h[k];
+    cst &= h[k] == (((j0 + k) & 1u) ? a0yh : a0xh);
+  }
+  gtop = true;
+  if ((j0 >> 1) & Ptop) gtop = h[0] == t32[2u * tile_val(j0 ^ (2u * Ptop)) + 1u];
+}
+
+// Steps 4-6 of encode_core (W32, smallest image, no Solution D trial) for one chunk of
+// a pair, once the shared scan has given its stream offset o0, its residual total and
+// its chunk-wide flags.  Returns the image length, or 0 with *err set.
+template <int VPT>
+__device__ __forceinline__ uint32_t finish32_pair_part(const uint64_t* tile, int kc, uint32_t S, uint32_t modes,
+                                                       uint8_t* img, uint32_t img_cap, ScanSmem& s, unsigned int* err,
+                                                       const uint32_t h[VPT], uint32_t cc, uint32_t o0, uint32_t total,
+                                                       bool allzero, bool allconst, bool gtop) {
+  const uint32_t N = 2u << kc, A = 1u << kc;
+  const uint32_t j0 = threadIdx.x * VPT;
+  const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(tile);
+  // 4. smallest power-of-two period (as in encode_core)
+  int period = -1;
+  if (kc >= 2 && gtop && !allconst) {
+    int p = kc - 1;
+    for (; p >= 1; --p) {
+      const uint32_t P = 1u << p;
+      bool ok = true;
+      for (uint32_t i = threadIdx.x; i < A; i += kThreads) {
+        if (i & P) {
+          const ulonglong2 q = t2[tile_amp(i)], w = t2[tile_amp(i ^ P)];
+          ok &= (q.x == w.x) && (q.y == w.y);
+        }
+      }
+      if (!__syncthreads_and(ok)) break;
+    }
+    period = p + 1 < kc ? p + 1 : -1;
+  }
+  uint32_t bits_p = 0;
+  if (period > 0) {
+    if (threadIdx.x == 0) s.bits_period = 0;
+    __syncthreads();
+    const uint32_t nvp = 2u << period;
+    uint32_t o = o0;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (j0 + k == nvp) s.bits_period = o;
+      o += resid_len((cc >> (2 * k)) & 3u, S);
+    }
+    __syncthreads();
+    bits_p = s.bits_period;
+    __syncthreads();
+  }
+  // 5. sizes and the choice
+  uint32_t size[M_NMODES];
+  size[M_ZERO] = allzero ? 16u : 0u;
+  size[M_CONST] = allconst ? 32u : 0u;
+  size[M_PERIOD] = period > 0 ? 16u + code_bytes(2u << period) + resid_bytes(bits_p) : 0u;
+  size[M_STREAM] = 16u + code_bytes(N) + resid_bytes(total);
+  size[M_RAW] = 16u + 8u * N;
+  size[M_SPLIT] = 0u;
+  uint32_t mode = 0, best = 0xffffffffu;
+#pragma unroll
+  for (uint32_t m = 0; m < M_NMODES; ++m)
+    if (((modes >> m) & 1u) && size[m] != 0 && size[m] < best) {
+      best = size[m];
+      mode = m;
+    }
+  if (best > img_cap) {  // cannot happen: RAW always fits a buffer of max_image_bytes
+    if (threadIdx.x == 0) atomicOr(err, (unsigned)E_MODE);
+    return 0;
+  }
+  // 6. the image
+  uint32_t nv = 0, rbits = 0;
+  if (mode == M_CONST) nv = 2;
+  if (mode == M_PERIOD) { nv = 2u << period; rbits = bits_p; }
+  if (mode == M_STREAM) { nv = N; rbits = total; }
+  if (mode == M_RAW) nv = N;
+  if (threadIdx.x == 0) {
+    uint32_t* hd = reinterpret_cast<uint32_t*>(img);
+    hd[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | ((mode == M_PERIOD ? (uint32_t)period : 0u) << 16);
+    hd[1] = best - 16u;
+    hd[2] = nv;
+    hd[3] = rbits;
+  }
+  uint64_t* pay64 = reinterpret_cast<uint64_t*>(img + 16);
+  if (mode == M_CONST) {
+    if (threadIdx.x == 0) {
+      pay64[0] = tile[tile_val(0)];
+      pay64[1] = tile[tile_val(1)];
+    }
+  } else if (mode == M_RAW) {
+    ulonglong2* p2 = reinterpret_cast<ulonglong2*>(pay64);
+    for (uint32_t a = threadIdx.x; a < A; a += kThreads) p2[a] = t2[tile_amp(a)];
+  } else if (mode == M_PERIOD || mode == M_STREAM) {
+    uint32_t c[VPT], r[VPT];
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      c[k] = (cc >> (2 * k)) & 3u;
+      r[k] = resid_len(c[k], S);
+    }
+    pack_xor32<VPT>(img, nv, j0, o0, h, c, r);
+  }
+  return best;
+}
+
+// Encodes both tiles of a work item in one pass: encode_core's steps for each chunk,
+// the two chunks sharing every barrier.  Taken for the common case only: width
+// S <= 32, the smallest image among modes without SPLIT, no selector network, and every
+// thread holding VPT values of each chunk (kThreads * VPT = 2^(kc+1)).  Returns false,
+// with both tiles untouched, if either chunk holds a subnormal or non-finite value (the
+// caller then runs encode_block on each); otherwise true with the image lengths in
+// n0 / n1 (0 with *err set on error).
+template <int VPT>
+__device__ bool encode_pair32(uint64_t* tile0, uint64_t* tile1, int kc, uint32_t S, uint32_t modes, uint8_t* img0,
+                              uint8_t* img1, uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err, uint32_t& n0,
+                              uint32_t& n1) {
+  const uint32_t N = 2u << kc;
+  const uint32_t j0 = threadIdx.x * VPT;
+  // 0. clear both payload areas the packers OR into
+  {
+    const uint32_t span = (min(img_cap, max_coded_bytes(kc)) - 16u) / 16u;
+    uint4* z0 = reinterpret_cast<uint4*>(img0 + 16);
+    uint4* z1 = reinterpret_cast<uint4*>(img1 + 16);
+    for (uint32_t u = threadIdx.x; u < 2u * span; u += kThreads) {
+      if (u < span) z0[u] = make_uint4(0u, 0u, 0u, 0u);
+      else z1[u - span] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  // 1. truncated high words (-0 stored as +0); a subnormal or non-finite value anywhere
+  //    sends both chunks to the general path
+  const uint32_t mh = (uint32_t)(trunc_mask(S) >> 32);
+  uint32_t h0[VPT], h1[VPT];
+  bool bad = false, nz0 = false, nz1 = false;
+  {
+    uint64_t t[VPT];
+    load_vals<VPT>(tile0, j0, N, t);
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const uint32_t hi = (uint32_t)(t[k] >> 32), ahi = hi & 0x7fffffffu;
+      bad |= ahi >= 0x7ff00000u || (ahi < 0x00100000u && (ahi | (uint32_t)t[k]) != 0u);
+      const uint32_t v = hi & mh;
+      h0[k] = v == 0x80000000u ? 0u : v;
+      nz0 |= h0[k] != 0u;
+    }
+    load_vals<VPT>(tile1, j0, N, t);
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const uint32_t hi = (uint32_t)(t[k] >> 32), ahi = hi & 0x7fffffffu;
+      bad |= ahi >= 0x7ff00000u || (ahi < 0x00100000u && (ahi | (uint32_t)t[k]) != 0u);
+      const uint32_t v = hi & mh;
+      h1[k] = v == 0x80000000u ? 0u : v;
+      nz1 |= h1[k] != 0u;
+    }
+  }
+  if (__syncthreads_or(bad)) return false;
+  // 2. the truncated values back into the tiles
+  {
+    uint64_t t[VPT];
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) t[k] = (uint64_t)h0[k] << 32;
+    store_vals<VPT>(tile0, j0, N, t);
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) t[k] = (uint64_t)h1[k] << 32;
+    store_vals<VPT>(tile1, j0, N, t);
+  }
+  __syncthreads();
+  // 3. codes, residual lengths and flags of both chunks; one scan for both
+  const uint32_t Ptop = kc >= 2 ? (1u << (kc - 1)) : 0u;
+  uint32_t cc0, cc1, sum0, sum1;
+  bool cst0, cst1, gt0, gt1;
+  codes32_pair_part<VPT>(tile0, j0, h0, S, Ptop, cc0, sum0, cst0, gt0);
+  codes32_pair_part<VPT>(tile1, j0, h1, S, Ptop, cc1, sum1, cst1, gt1);
+  uint32_t o0, o1, total0, total1, f_or, f_and;
+  block_scan2(sum0, sum1, (nz0 ? 1u : 0u) | (nz1 ? 2u : 0u),
+              (cst0 ? 1u : 0u) | (gt0 ? 2u : 0u) | (cst1 ? 4u : 0u) | (gt1 ? 8u : 0u), s, pp, &o0, &o1, &total0,
+              &total1, &f_or, &f_and);
+  // 4-6. period, choice and image of each chunk
+  n0 = finish32_pair_part<VPT>(tile0, kc, S, modes, img0, img_cap, s, err, h0, cc0, o0, total0, (f_or & 1u) == 0u,
+                               (f_and & 1u) != 0u, (f_and & 2u) != 0u);
+  n1 = finish32_pair_part<VPT>(tile1, kc, S, modes, img1, img_cap, s, err, h1, cc1, o1, total1, (f_or & 2u) == 0u,
+                               (f_and & 4u) != 0u, (f_and & 8u) != 0u);
+  __syncthreads();
+  return true;
 }
 
 // -------------------------------------------------------- gate arithmetic -- //

@@ -435,8 +435,16 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   if (bc_hit) {
     prefetch_next();
   } else {
-  const bool ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
-  const bool ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
+  // two STREAM images of 32-bit width (the common case once the run is lossy) decode
+  // together, sharing barriers; anything else chunk by chunk
+  const bool paired = has1 && kThreads * VPT == 2u * A;
+  bool ok0, ok1;
+  if (paired && stream32_image(m.img0, b0, kc) && stream32_image(m.img1, b1, kc)) {
+    ok0 = ok1 = decode_stream32_pair<VPT>(m.img0, m.img1, 2u * A, m.tile0, m.tile1, *m.s, st.pp);
+  } else {
+    ok0 = decode_block<VPT>(m.img0, b0, kc, m.tile0, *m.s, st.pp);
+    ok1 = has1 ? decode_block<VPT>(m.img1, b1, kc, m.tile1, *m.s, st.pp) : true;
+  }
   prefetch_next();
   QC_PHASE(1);
   if (!ok0 || !ok1) {
@@ -486,12 +494,19 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
     sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
     sel.prev_len = b0;
   }
-  n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
-  if (has1) {
-    const uint4 h = reinterpret_cast<const uint4*>(m.img1)[0];
-    sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
-    sel.prev_len = b1;
-    n1 = encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
+  // both chunks in one pass when neither needs the Solution D trial, the network or
+  // 64-bit widths; otherwise (or if a chunk holds a subnormal) chunk by chunk
+  const bool enc_paired = paired && S <= 32u && L.selector != 2 && !L.trace && !((L.modes >> M_SPLIT) & 1u) &&
+                          encode_pair32<VPT>(m.tile0, m.tile1, kc, S, L.modes, m.img0, m.img1, cap, *m.s, st.pp,
+                                             &ctl->err, n0, n1);
+  if (!enc_paired) {
+    n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
+    if (has1) {
+      const uint4 h = reinterpret_cast<const uint4*>(m.img1)[0];
+      sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
+      sel.prev_len = b1;
+      n1 = encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
+    }
   }
   QC_PHASE(3);
   // the error word for the next item's check (the load completes while this one ends)

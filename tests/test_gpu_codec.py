@@ -66,6 +66,25 @@ def test_encode_bytes_match_oracle(kc, modes):
             assert imgs[k] == ref, (kc, eps, k, imgs[k][:16].hex(), ref[:16].hex())
 
 
+@pytest.mark.parametrize("e32", [1, 127, 254])
+def test_every_float32_mantissa_matches_oracle(e32):
+    """All 2^23 float32 mantissas of one binade with both signs (the smallest, the unit
+    and the largest float32 binade), widened to binary64, in index order and in a seeded
+    shuffle: 4096 chunks of 2^11 amplitudes per bound, the device's images byte for byte
+    the oracle's."""
+    kc = 11
+    mant = np.arange(1 << 23, dtype=np.uint32)
+    f = ((np.uint32(e32) << np.uint32(23)) | mant).view(np.float32).astype(np.float64)
+    x = np.concatenate([f, -np.random.default_rng(e32).permutation(f)])
+    step = 2 << kc
+    for eps in EPS:
+        S = O.sig_bits(eps)
+        imgs, _ = qc().codec_encode(x.view(np.complex128), kc, eps)
+        assert len(imgs) == x.size // step
+        for k in range(len(imgs)):
+            assert imgs[k] == O.encode_chunk(x[k * step:(k + 1) * step], kc, S), (eps, k)
+
+
 @pytest.mark.parametrize("kc", [1, 4, 8, 10])
 def test_forced_modes_match_oracle(kc):
     rng = np.random.default_rng(kc)
