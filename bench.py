@@ -47,10 +47,11 @@ ROWS, COLS, BLOCK_LOG2, CHUNK_LOG2, SEED = 5, 6, 20, 10, 2024  # defaults; --row
 # DRAM traffic of k_gate from the last ncu capture, with the hash of the kernel sources
 # it was taken on.  The 30-qubit launch is too large to capture, so the capture ran the
 # 26-qubit 2 x 13 grid (launches 151-152): dram__bytes_read.sum + dram__bytes_write.sum
-# = 901.9 MB per launch against 864.3 MB of image bytes per launch, a ratio of 1.044
-# (the rest is directory entries and pool bookkeeping); traffic scales with the image
-# bytes, so a 30-qubit launch's traffic is that ratio times its image bytes.
-NCU_TRAFFIC = {"ratio_to_image_bytes": 1.044, "source_sha": "a1635ec286167906"}
+# = 961.5 MB per launch against 864.3 MB of image bytes per launch, a ratio of 1.113
+# (reads 465 MB: the images plus directory entries and pool bookkeeping; writes 496 MB,
+# 60 MB above the images written); traffic scales with the image bytes, so a 30-qubit
+# launch's traffic is that ratio times its image bytes.
+NCU_TRAFFIC = {"ratio_to_image_bytes": 1.113, "source_sha": "f6df44bc141445fb"}
 
 
 def kernel_sha() -> str:
