@@ -130,6 +130,64 @@ def test_subnormal_amplitudes_in_the_fused_kernel():
     assert widths == {0, 26, 64}  # 0: ZERO chunks (qubit 9 is never touched)
 
 
+def paired_subnormal_circuit():
+    """Like test_oracle_sim.subnormal_circuit, for chunks of 2^7 amplitudes: the rotation
+    with cos = 1e-310 runs under a control on qubit 7 (bit 0 of the chunk index), so in a
+    work item of an in-chunk gate one chunk holds subnormal amplitudes and its partner
+    none, while a cross-chunk gate on qubits 8-11 pairs two chunks of the same kind.
+    Qubit 0 is not touched again, so the subnormals survive."""
+    c = 1e-310
+    U = np.array([[c, -1.0], [1.0, c]], dtype=np.complex128)
+    g = [Cc.gate(7, Cc.H), Cc.gate(0, U, {7: 1}), Cc.gate(1, Cc.H), Cc.gate(8, Cc.H), Cc.gate(2, Cc.H),
+         Cc.gate(9, Cc.SX), Cc.gate(3, Cc.H), Cc.gate(4, Cc.SX), Cc.gate(10, Cc.H), Cc.gate(5, Cc.T),
+         Cc.gate(6, Cc.SY), Cc.gate(11, Cc.H), Cc.gate(2, Cc.SY), Cc.gate(9, Cc.T)]
+    return Cc.to_array(g)
+
+
+def test_subnormal_chunk_beside_a_normal_one_in_a_work_item():
+    """Chunks of 2^7 amplitudes, where both chunks of a work item decode and encode in one
+    pass: an item holding a subnormal chunk falls back to chunk-by-chunk coding (the
+    subnormal chunk at 64 bits, its partner at the bound), and every image equals the
+    oracle's after every gate."""
+    n, kc = 12, 7
+    gates = paired_subnormal_circuit()
+    orc = O.CSim(n, n, kc, 1e-4, 1)
+    gpu = qc().Sim(n, n, 1e-4, chunk_log2=kc, budget=1, pool_bytes=4 * (16 << n) + (16 << 20))
+    for k in range(len(gates)):
+        gpu.apply_circuit(gates[k:k + 1])
+        orc.apply(gates[k:k + 1])
+        assert images_equal(gpu, orc) == [], k
+    stats_match(gpu.stats(), orc.stats())
+    widths = [gpu.chunk_image(q)[1] for q in range(gpu.n_chunks)]
+    assert {w for q, w in enumerate(widths) if q & 1} == {64}
+    assert {w for q, w in enumerate(widths) if not q & 1} == {O.sig_bits(1e-4)}
+
+
+@pytest.mark.parametrize("kc", [8, 10])
+def test_paired_and_chunk_by_chunk_coding_agree(kc):
+    """Tracing selector records switches the fused kernel to chunk-by-chunk encoding (with
+    the Solution C modes only it records nothing); the images must not change.  Random
+    circuit, Grover and QAOA states (STREAM, CONST, PERIOD, ZERO chunks side by side)."""
+    n, eps = 14, 1e-4
+    circuits = [Cc.rcs_n(n, 6, seed=70 + kc), Cc.grover(n, 1, seed=71)[0], Cc.qaoa_maxcut(n, 1, 3, seed=72)[0]]
+    for gates in circuits:
+        sims = []
+        for tracing in (False, True):
+            s = qc().Sim(n, n, eps, chunk_log2=kc, budget=(16 << n) // 4, pool_bytes=2 * (16 << n) + (32 << 20))
+            if tracing:
+                s.trace(1 << 10)
+            sims.append(s)
+        for k in range(0, len(gates), 25):
+            for s in sims:
+                s.apply_circuit(gates[k:k + 25])
+            a, b = sims
+            assert [a.chunk_image(c) for c in range(a.n_chunks)] == [b.chunk_image(c) for c in range(b.n_chunks)], k
+        assert sims[1].trace_read().shape[0] == 0
+        orc = O.CSim(n, n, kc, eps, (16 << n) // 4)
+        orc.apply(gates)
+        assert images_equal(sims[0], orc) == []
+
+
 @pytest.mark.parametrize("ladder", [0, 1, 2])
 def test_qaoa_and_qft_bit_exact(ladder):
     n = 12
