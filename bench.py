@@ -429,6 +429,15 @@ def run_qaoa34(args) -> dict:
     kernel_ms = tm["gate_kernel_ms"] / max(1, tm["launches"])
     bpl = (tm["bytes_read"] + tm["bytes_written"]) / max(1, tm["launches"])
     pk = peaks().get("hbm_gbs")
+    echo = None
+    if args.echo:
+        # Loschmidt echo (untimed): the inverse circuit run compressed after the forward one;
+        # |<0...0|state>| >= 1 - sum(delta) over both halves (the fidelity bound)
+        sim.apply_circuit(Cc.inverse(gates))
+        a0 = complex(sim.amplitudes(0, 1)[0])
+        st2 = sim.stats()
+        echo = {"amp0_abs": abs(a0), "bound": st2["fidelity_lb_sum"], "gates": 2 * len(gates),
+                "max_encoded_gb": st2["max_encoded_bytes"] / 1e9, "eps_final": st2["eps_current"]}
     return {"metric": METRIC, "value": updates / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": len(timed),
             "warmup": args.warmup, "ms_per_step": ms / len(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -443,7 +452,7 @@ def run_qaoa34(args) -> dict:
             "roofline": {"bound": "hbm", "achieved": bpl / (kernel_ms * 1e-3) / 1e9 if kernel_ms else None, "peak": pk,
                          "unit": "GB/s", "frac": (bpl / (kernel_ms * 1e-3) / 1e9 / pk) if (pk and kernel_ms) else None,
                          "traffic": None, "kernel": "k_gate", "kernel_ms_avg": kernel_ms},
-            "gpu_launches": 2 * tm["launches"], "clocks": clk}
+            "gpu_launches": 2 * tm["launches"], "clocks": clk, "echo": echo}
 
 
 def train_selector(qcsim, eps: float, seed: int):
@@ -644,6 +653,8 @@ def main():
     ap.add_argument("--ladder", type=int, default=0, help="grover: controller ladder (2 = guarded, budget = pool)")
     ap.add_argument("--selectors", default="0,1,2", help="grover: which selectors to run (0 C only, 1 exhaustive, 2 network)")
     ap.add_argument("--cache", action="store_true", help="grover: switch the compressed block cache on")
+    ap.add_argument("--echo", action="store_true",
+                    help="qaoa34: after the timed run, run the inverse circuit (untimed) and report |<0|state>|")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)

@@ -95,6 +95,21 @@ def matrix_of(rec) -> np.ndarray:
     return np.array([[u[0] + 1j * u[1], u[2] + 1j * u[3]], [u[4] + 1j * u[5], u[6] + 1j * u[7]]])
 
 
+def inverse(gates: np.ndarray) -> np.ndarray:
+    """The inverse circuit: the gates in reverse order, each unitary replaced by its
+    conjugate transpose (exact in floating point; zero parts stay +0).  Run after
+    ``gates`` it returns every state to itself up to rounding: a Loschmidt echo, whose
+    overlap with the starting state measures what the compression lost."""
+    g = np.asarray(gates, dtype=GATE_DTYPE)
+    out = np.array(g[::-1], dtype=GATE_DTYPE, copy=True)
+    u = np.array(out["u"], dtype=np.float64, copy=True)
+    re = (0, 4, 2, 6)  # u00, u10 -> u01, u01 -> u10, u11
+    for k, src in enumerate(re):
+        out["u"][:, 2 * k] = u[:, src]
+        out["u"][:, 2 * k + 1] = 0.0 - u[:, src + 1]
+    return out
+
+
 # --------------------------------------------------------------------------- #
 # Circuit families                                                             #
 # --------------------------------------------------------------------------- #

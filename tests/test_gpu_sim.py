@@ -188,6 +188,24 @@ def test_paired_and_chunk_by_chunk_coding_agree(kc):
         assert images_equal(sims[0], orc) == []
 
 
+def test_loschmidt_echo_matches_oracle_and_bound():
+    """QAOA then its inverse, compressed at 1e-4 (guarded ladder, budget raw/4): the
+    images equal the oracle's, and the amplitude of |0...0> is at least 1 - sum(delta)
+    (Section 3.8 reading) but below 1.  The benchmark runs the same check at 34 qubits."""
+    n, kc, eps = 16, 8, 1e-4
+    gates, _ = Cc.qaoa_maxcut(n, 2, 3, seed=12)
+    echo = np.concatenate([gates, Cc.inverse(gates)])
+    budget = (16 << n) // 4
+    gpu = qc().Sim(n, n, eps, chunk_log2=kc, budget=budget, ladder=2, pool_bytes=2 * (16 << n) + (32 << 20))
+    gpu.apply_circuit(echo)
+    orc = O.CSim(n, n, kc, eps, budget, ladder=2)
+    orc.apply(echo)
+    assert images_equal(gpu, orc) == []
+    stats_match(gpu.stats(), orc.stats())
+    a0 = abs(gpu.amplitudes(0, 1)[0])
+    assert gpu.stats()["fidelity_lb_sum"] - 1e-12 <= a0 < 1.0
+
+
 @pytest.mark.parametrize("ladder", [0, 1, 2])
 def test_qaoa_and_qft_bit_exact(ladder):
     n = 12

@@ -126,6 +126,38 @@ def test_norm_conservation_rcs():
     assert abs(O.sv_norm2(psi, n) - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("family", ["rcs", "qaoa", "qft"])
+def test_inverse_circuit_returns_to_the_start(family):
+    """circuits.inverse: U then U^dagger on the exact state vector gives back |0...0>
+    (Loschmidt echo without compression) up to rounding."""
+    n = 10
+    gates = {"rcs": lambda: Cc.rcs(2, 5, 8, seed=3), "qaoa": lambda: Cc.qaoa_maxcut(n, 2, 3, seed=3)[0],
+             "qft": lambda: Cc.qft(n, seed=3)[0]}[family]()
+    psi = O.sv_init(n)
+    O.sv_run(psi, n, gates)
+    assert abs(psi[0]) < 0.5  # the forward circuit leaves |0...0>
+    O.sv_run(psi, n, Cc.inverse(gates))
+    assert abs(psi[0] - 1.0) < 1e-12
+    assert np.max(np.abs(psi[1:])) < 1e-12
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-3])
+def test_compressed_echo_bound(eps):
+    """Section 3.8 reading: each lossy encode moves the state by at most delta, and the
+    inverse circuit is unitary, so after U and U^dagger run compressed the amplitude of
+    |0...0> is at least 1 - sum(delta) over both halves; it is below 1 because the
+    compression did lose something."""
+    n, kc = 12, 6
+    gates, _ = Cc.qaoa_maxcut(n, 2, 3, seed=5)
+    cs = O.CSim(n, n, kc, eps, budget=1)
+    cs.apply(gates)
+    cs.apply(Cc.inverse(gates))
+    a0 = abs(cs.amplitudes()[0])
+    st = cs.stats()
+    assert st["fid_lb_sum"] == pytest.approx(1.0 - 2 * len(gates) * 2.0 ** O.exp_of(eps), rel=1e-12)
+    assert st["fid_lb_sum"] - 1e-12 <= a0 < 1.0
+
+
 def test_qaoa_gate_counts_table2():
     # Table 2: QAOA with 42 and 43 qubits uses 336 and 344 gates; one round (p = 1)
     # on a 4-regular graph with CNOT-RZ-CNOT cost terms gives n + 3 (2n) + n.
