@@ -103,6 +103,43 @@ def fp64_flops(gates: np.ndarray, n: int, kc: int) -> float:
     return tot
 
 
+def gate_class(g) -> str:
+    """dense: all four entries of the 2x2 matrix nonzero (sqrt(X), sqrt(Y), H);
+    diagonal: zero off-diagonal (T, CZ, phases); permutation: zero diagonal (X, CNOT);
+    other: one zero entry."""
+    u = [float(x) for x in g["u"]]
+    z = [u[2 * k] == 0.0 and u[2 * k + 1] == 0.0 for k in range(4)]
+    if not any(z):
+        return "dense"
+    if z[1] and z[2]:
+        return "diagonal"
+    if z[0] and z[3]:
+        return "permutation"
+    return "other"
+
+
+def per_class(gates: np.ndarray, tl: dict, n: int, kc: int, hbm: float | None) -> dict:
+    """Kernel time, image bytes and the two roofline fractions per gate class, from the
+    per-launch CUDA-event times and traffic counters of the timed gates."""
+    out = {}
+    cls = [gate_class(g) for g in gates]
+    assert len(cls) == len(tl["ms"])
+    for c in ("dense", "diagonal", "permutation", "other"):
+        idx = [i for i, x in enumerate(cls) if x == c]
+        if not idx:
+            continue
+        ms = float(np.sum(tl["ms"][idx]))
+        by = float(np.sum(tl["bytes_read"][idx]) + np.sum(tl["bytes_written"][idx]))
+        fl = fp64_flops(gates[idx], n, kc)
+        ach = by / (ms * 1e-3) / 1e9
+        out[c] = {"launches": len(idx), "kernel_ms_per_launch": ms / len(idx),
+                  "image_bytes_per_launch": by / len(idx), "hbm_gbs": ach,
+                  "hbm_frac": ach / hbm if hbm else None,
+                  "fp64_tflops": fl / (ms * 1e-3) / 1e12, "fp64_frac": fl / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                  "amp_updates_per_s": amp_updates(gates[idx], n, kc) / (ms * 1e-3)}
+    return out
+
+
 # GB300 FP64 (vector pipe): 1.25 TFLOP/s nominal; a DFMA loop measured 1.2 TFLOP/s here.
 FP64_PEAK_TFLOPS = 1.25
 
@@ -200,6 +237,8 @@ def run_gpu(args) -> dict | None:
     pool = raw + raw // 8 + (64 << 20)  # page rounding + per-CTA page caches
     sim = qcsim.Sim(n, BLOCK_LOG2, args.eps, chunk_log2=args.kc, budget=raw // 4, pool_bytes=pool,
                     stream=stream)
+    if args.no_fast:
+        sim.set_option("fast_path", 0)
     kc = sim.chunk_log2
 
     def barrier():
@@ -227,6 +266,7 @@ def run_gpu(args) -> dict | None:
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    tl = sim.timing_launches()
     tm = sim.timing()
     sim.set_timing(False)
     st1 = sim.stats()
@@ -327,6 +367,7 @@ def run_gpu(args) -> dict | None:
             "peak_source": "nominal GB300 FP64 (vector) rate; a DFMA loop measured 1.2 TFLOP/s",
             "note": "the fused kernel's arithmetic ceiling: dense gates cost 28 flops per amplitude pair",
         },
+        "roofline_by_class": per_class(np.concatenate(timed), tl, n, kc, hbm),
         "gpu_launches": 2 * tm["launches"],
         "phase_share": ({k: round(v / max(1, sum(st1["phase_cycles"])), 4) for k, v in
                          zip(("stage", "decode", "apply", "encode", "commit", "const"), st1["phase_cycles"])}
@@ -659,6 +700,7 @@ def main():
     ap.add_argument("--rows", type=int, default=5, help="grid rows (profiling cases use smaller grids)")
     ap.add_argument("--cols", type=int, default=6)
     ap.add_argument("--kc", type=int, default=CHUNK_LOG2, help="chunk_log2 (amplitudes per coded chunk = 2^kc)")
+    ap.add_argument("--no-fast", action="store_true", help="every work item through the general gate kernel")
     args = ap.parse_args()
     global ROWS, COLS, BLOCK_LOG2
     ROWS, COLS = args.rows, args.cols

@@ -94,6 +94,9 @@ typedef struct sim_stats_t {
   uint64_t split_trials;      /* chunk encodes that ran the Solution D trial */
   uint64_t cache_lookups;     /* block-cache lookups (work items that consulted it) */
   uint64_t cache_hits;        /* ... that took a cached result */
+  uint64_t fast_items;        /* work items the streaming gate kernel wrote (cumulative) */
+  uint64_t fast_deferred;     /* work items it left to the general gate kernel (cumulative) */
+  uint64_t kernel_launches;   /* kernels the gates enqueued (streaming, general and post kernels) */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
@@ -176,6 +179,8 @@ sim_status sim_set_budget(sim_t* sim, uint64_t bytes);
 /* Named settings, from the next gate on: "modes" (as sim_set_modes), "selector" (0 or
  * 1; the network needs sim_set_selector), "block_cache" (0/1, as sim_set_block_cache),
  * "timing" (0/1/2, as sim_set_timing), "tau_ppm" (tau in millionths, (0, 1e6]),
+ * "fast_path" (1 default: gates run the streaming kernel first where it applies, see
+ * sim_apply_gate; 0: every item through the general kernel -- same bytes, slower),
  * "ladder" (0/1/2; only before the first gate).  "chunk_log2" and "block_log2" are fixed
  * at creation.  Unknown keys or values out of range: SIM_ERR_INVALID. */
 sim_status sim_set_option(sim_t* sim, const char* key, int64_t value);
@@ -288,6 +293,17 @@ sim_status sim_set_timing(sim_t* sim, int on);
 sim_status sim_timing(sim_t* sim, double* gate_kernel_ms, uint64_t* launches, uint64_t* bytes_read,
                       uint64_t* bytes_written);
 
+/* The same figures launch by launch, for the launches sim_timing would sum next (call
+ * it before sim_timing, which starts counting anew): *n receives their number; the
+ * first min(*n, cap) entries of ms, bytes_read and bytes_written (caller-owned arrays of
+ * cap entries) receive each gate-kernel launch's CUDA-event time and the chunk-image
+ * bytes it read and wrote, in launch order.  Synchronises the handle's stream.  With
+ * timing on, every gate also copies the two traffic counters into a device log that
+ * grows by stream-ordered allocation.  Errors: SIM_ERR_INVALID (NULL pointers with
+ * cap > 0), SIM_ERR_CUDA. */
+sim_status sim_timing_launches(sim_t* sim, uint64_t cap, float* ms, uint64_t* bytes_read, uint64_t* bytes_written,
+                               uint64_t* n);
+
 /* Message for the last failure on the calling thread ("" if none). */
 const char* sim_last_error(void);
 
@@ -333,7 +349,9 @@ sim_status sim_codec_decode(const uint8_t* in, uint64_t in_stride, const uint32_
  *    SIM_ERR_INVALID ("request larger than the 8 MiB scratch"): n_chunks *
  *    (16 * 2^chunk_log2 + out_stride) + 4 * n_chunks + 768 bytes must fit in 8 MiB.
  *  - The first call on each device looks up the array's device address (with that
- *    device current); make that first call before any stream capture.
+ *    device current, under a lock, so first calls from several host threads are
+ *    safe); make that first call before any stream capture.  The address is kept for
+ *    the process: after a cudaDeviceReset of a device the call must not be used there.
  *  - All calls on a device share the array: calls that overlap on the same device
  *    (other host threads or streams) race and must be serialised by the caller.
  *    Each call resets the parts it uses, so results never depend on earlier calls.

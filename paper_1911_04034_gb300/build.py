@@ -12,8 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqcsim.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "mlp.cu"]
-HEADERS = ["device.cuh", "launch.h"]
+SOURCES = ["kernels.cu", "fast.cu", "api.cu", "noalloc.cu", "mlp.cu"]
+HEADERS = ["device.cuh", "launch.h", "gate_common.cuh"]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

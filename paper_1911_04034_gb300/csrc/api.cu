@@ -47,9 +47,11 @@ sim_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+}  // namespace
+
 // Eq. sigbits: S = 12 - EXP(eps) for binary64 (EXP = the IEEE exponent of eps);
 // eps = 0 is the lossless stage (64 bits).  -1 for a bound outside {0} U [2^-52, 1).
-int sig_bits_of(double eps) {
+int qc::sig_bits_of(double eps) {
   if (eps == 0.0) return 64;
   if (!(eps > 0.0) || !(eps < 1.0)) return -1;
   int e2 = 0;
@@ -59,6 +61,10 @@ int sig_bits_of(double eps) {
   const int S = 12 - ex;
   return S > 64 ? 64 : S;
 }
+
+namespace {
+
+using qc::sig_bits_of;
 
 bool gate_ok(const sim_gate* g, int n, std::string* why) {
   if (g->target < 0 || g->target >= n) { *why = "target outside the register"; return false; }
@@ -146,14 +152,22 @@ struct sim {
   unsigned short* d_mlp = nullptr;   // bfloat16 parameters of the selector network
   float* d_trace = nullptr;          // selector training records
   uint8_t* d_bc = nullptr;           // block cache lines (Section 3.4) or nullptr
+  uint32_t* d_defer = nullptr;       // items the streaming kernel leaves to the general one
+  int fast_grid = 0;                 // CTAs of the streaming kernel (0: chunk size outside its range)
+  bool fast = true;                  // gates try the streaming kernel first
+  uint64_t kernel_launches = 0;      // gate, streaming and post kernels enqueued
   uint64_t trace_cap = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   size_t ev_next = 0;
+  unsigned long long* d_tlog = nullptr;  // per timed launch: cumulative image bytes read, written after it
+  size_t tlog_cap = 0;
   unsigned long long t_bytes_in0 = 0, t_bytes_out0 = 0;
 
   ~sim() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    cudaFree(d_tlog);
+    cudaFree(d_defer);
     cudaFree(d_mlp);
     cudaFree(d_trace);
     cudaFree(d_bc);
@@ -192,6 +206,12 @@ struct sim {
     if (err & qc::E_OOM) {
       poisoned = SIM_ERR_OOM;
       return fail(SIM_ERR_OOM, "the page pool ran out of pages (budget too small for the state)");
+    }
+    if (err & qc::E_TIMEOUT) {
+      unsigned int site = 0;
+      cudaMemcpy(&site, &d_ctl->timeout_site, sizeof(site), cudaMemcpyDeviceToHost);
+      poisoned = SIM_ERR_TIMEOUT;
+      return fail(SIM_ERR_TIMEOUT, "a bounded wait in the streaming gate kernel gave up (site %u)", site);
     }
     poisoned = SIM_ERR_CORRUPT;
     return fail(SIM_ERR_CORRUPT, "a chunk image failed its checks or held a non-finite value (flags 0x%x)", err);
@@ -260,7 +280,11 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
   // page arena: the budget, 1/8 more for page rounding, and the pages that the
   // per-CTA caches may hold while a gate runs
   s->grid = device_sms() * qc::gate_ctas_per_sm(s->kc);
-  const uint64_t slack_pages = (uint64_t)s->grid * (qc::kCacheCap + 2 * qc::max_pages(s->kc));
+  s->fast_grid = s->kc >= qc::kFastMinKC ? device_sms() * qc::fast_ctas_per_sm(s->kc) : 0;
+  // pages the per-CTA caches of the general kernel, and the per-warp caches and items in
+  // flight of the streaming kernel, may hold while a gate runs
+  const uint64_t slack_pages = (uint64_t)s->grid * (qc::kCacheCap + 2 * qc::max_pages(s->kc)) +
+                               (uint64_t)s->fast_grid * qc::fast_warps() * (qc::fast_warp_cache() + 2 * qc::max_pages(s->kc));
   if (pool_bytes) {
     s->npages = (pool_bytes + qc::kPage - 1) / qc::kPage;
   } else {
@@ -288,6 +312,7 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
       {(void**)&P.cache_n, (size_t)s->grid * 4, "page cache counts"},
       {(void**)&s->d_ctl, sizeof(DevCtl), "counters"},
       {(void**)&s->d_counts, 8 * sizeof(unsigned long long), "mode counts"},
+      {(void**)&s->d_defer, (size_t)(s->nchunks / 2 + 1) * sizeof(uint32_t), "deferred-item list"},
   };
   for (auto& a : allocs) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -418,9 +443,43 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
   return L;
 }
 
+// True if the streaming kernel can take the gate's items (see kernels.cu): chunk sizes
+// 2^7..2^11, the plain mode set and selector, no block cache or training records, and a
+// partner amplitude within a warp's pass unless the gate is diagonal.  Sets L.fast_kind.
+static bool fast_applies(const sim* s, const sim_gate* g, GateLaunch& L) {
+  if (!s->fast || s->fast_grid == 0 || L.bc || L.trace || L.selector != 0 || L.modes != qc::kDefaultModes) return false;
+  const double* u = g->u;
+  const bool diag = u[2] == 0.0 && u[3] == 0.0 && u[4] == 0.0 && u[5] == 0.0;
+  const bool anti = u[0] == 0.0 && u[1] == 0.0 && u[6] == 0.0 && u[7] == 0.0;
+  if (L.pair) L.fast_kind = 0;
+  else if (diag) L.fast_kind = 3;
+  else if (L.target < 2) L.fast_kind = 1;
+  else if (L.target < 7) L.fast_kind = 2;
+  else return false;
+  // Eq. matrix1 / matrix2 with the coefficient order of GateCoef: a term with a zero
+  // coefficient contributes an exact zero, so summing every term gives the kept-term
+  // sums' value (a zero result may differ in sign, and the encoder stores +0 for both)
+  const double cf[16] = {u[0], -u[1], u[2], -u[3], u[0], u[1], u[2], u[3],
+                         u[4], -u[5], u[6], -u[7], u[4], u[5], u[6], u[7]};
+  for (int k = 0; k < 16; ++k) L.cf[k] = cf[k];
+  L.arith = diag ? 1 : (anti ? 2 : 0);
+  if (L.arith) {
+    // the one nonzero entry of each row: a' = d0 x, b' = d1 y (x, y = a, b or b, a)
+    const double d[4] = {diag ? u[0] : u[2], diag ? u[1] : u[3], diag ? u[6] : u[4], diag ? u[7] : u[5]};
+    for (int r = 0; r < 2; ++r) {
+      L.du[2 * r] = d[2 * r];
+      L.du[2 * r + 1] = d[2 * r + 1];
+      L.rop[r] = d[2 * r + 1] != 0.0 ? 0 : (d[2 * r] == 1.0 ? 1 : (d[2 * r] == -1.0 ? 2 : 0));
+    }
+  }
+  return true;
+}
+
 static sim_status enqueue_gate(sim* s, const sim_gate* g) {
-  const GateLaunch L = make_launch(s, g);
+  GateLaunch L = make_launch(s, g);
   const int grid = (uint64_t)s->grid < L.items ? s->grid : (int)L.items;
+  const bool fast = fast_applies(s, g, L);
+  L.defer = s->d_defer;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (s->timing) {
     while (s->ev_pool.size() < s->ev_next + 2) {
@@ -432,12 +491,38 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
     e1 = s->ev_pool[s->ev_next++];
     CK(cudaEventRecord(e0, s->st), "event record");
   }
+  if (fast) {
+    // the streaming kernel first; the general kernel then runs the items it left
+    const unsigned long long want = (L.items + qc::fast_pairs() - 1) / qc::fast_pairs();
+    const int fg = (unsigned long long)s->fast_grid < want ? s->fast_grid : (int)want;
+    CK(qc::launch_gate_fast(L, fg, s->st), "streaming gate kernel launch");
+    L.list = 1;
+    s->kernel_launches += 1;
+  }
   CK(qc::launch_gate(L, grid, s->st), "gate kernel launch");
+  s->kernel_launches += 2;  // with the post kernel below
   if (s->timing) {
     CK(cudaEventRecord(e1, s->st), "event record");
     s->ev_pending.emplace_back(e0, e1);
   }
   CK(qc::launch_post(s->P, L.ctl, s->grid, s->st), "post kernel launch");
+  if (s->timing) {
+    // the traffic counters after this gate, for the per-launch figures of sim_timing_launches
+    const size_t k = s->ev_pending.size() - 1;
+    if (k >= s->tlog_cap) {
+      const size_t cap = s->tlog_cap ? 2 * s->tlog_cap : 4096;
+      unsigned long long* p = nullptr;
+      CK(cudaMallocAsync(&p, cap * 2 * sizeof(unsigned long long), s->st), "timing log");
+      if (s->tlog_cap)
+        CK(cudaMemcpyAsync(p, s->d_tlog, s->tlog_cap * 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                           s->st), "timing log copy");
+      if (s->d_tlog) CK(cudaFreeAsync(s->d_tlog, s->st), "timing log");
+      s->d_tlog = p;
+      s->tlog_cap = cap;
+    }
+    CK(cudaMemcpyAsync(s->d_tlog + 2 * k, &s->d_ctl->bytes_in, 2 * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToDevice, s->st), "timing log");
+  }
   s->amp_updates += L.nact << s->kc;
   return SIM_OK;
 }
@@ -481,9 +566,35 @@ sim_status sim_set_timing(sim_t* s, int on) {
   CK(cudaStreamSynchronize(s->st), "sync");
   s->timing = on != 0;
   s->phases = on >= 2;
+  if (s->timing && !s->d_tlog) {  // room for the per-launch log of 8192 gates before it has to grow
+    CK(cudaMalloc(&s->d_tlog, 8192 * 2 * sizeof(unsigned long long)), "timing log");
+    s->tlog_cap = 8192;
+  }
   s->ev_pending.clear();
   s->ev_next = 0;
   return read_traffic(s, &s->t_bytes_in0, &s->t_bytes_out0);
+}
+
+sim_status sim_timing_launches(sim_t* s, uint64_t cap, float* ms, uint64_t* bytes_read, uint64_t* bytes_written,
+                               uint64_t* n) {
+  if (!s || !n || (cap && (!ms || !bytes_read || !bytes_written))) return fail(SIM_ERR_INVALID, "NULL argument");
+  CK(cudaStreamSynchronize(s->st), "sync");
+  const size_t k = s->ev_pending.size();
+  *n = k;
+  if (k == 0 || cap == 0) return SIM_OK;
+  std::vector<unsigned long long> log(2 * k);
+  CK(cudaMemcpy(log.data(), s->d_tlog, 2 * k * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "timing log");
+  unsigned long long in0 = s->t_bytes_in0, out0 = s->t_bytes_out0;
+  for (size_t i = 0; i < k && i < cap; ++i) {
+    float m = 0.f;
+    CK(cudaEventElapsedTime(&m, s->ev_pending[i].first, s->ev_pending[i].second), "event elapsed");
+    ms[i] = m;
+    bytes_read[i] = log[2 * i] - in0;
+    bytes_written[i] = log[2 * i + 1] - out0;
+    in0 = log[2 * i];
+    out0 = log[2 * i + 1];
+  }
+  return SIM_OK;
 }
 
 sim_status sim_timing(sim_t* s, double* ms, uint64_t* launches, uint64_t* bytes_read, uint64_t* bytes_written) {
@@ -529,6 +640,11 @@ sim_status sim_set_option(sim_t* s, const char* key, int64_t value) {
   }
   if (k == "block_cache") return sim_set_block_cache(s, value != 0);
   if (k == "timing") return sim_set_timing(s, (int)value);
+  if (k == "fast_path") {
+    if (value != 0 && value != 1) return fail(SIM_ERR_INVALID, "fast_path must be 0 or 1");
+    s->fast = value != 0;
+    return SIM_OK;
+  }
   if (k == "tau_ppm") {
     if (value <= 0 || value > 1000000) return fail(SIM_ERR_INVALID, "tau_ppm must be in (0, 1000000]");
     CK(cudaStreamSynchronize(s->st), "sync");
@@ -779,6 +895,9 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->split_trials = h.split_trials;
   o->cache_lookups = h.bc_lookups;
   o->cache_hits = h.bc_hits;
+  o->fast_items = h.fast_items;
+  o->fast_deferred = h.fast_deferred;
+  o->kernel_launches = s->kernel_launches;
   if (h.err) return s->check_device();
   return SIM_OK;
 }
@@ -1167,6 +1286,9 @@ sim_status sim_codec_encode_ex(const double* in, uint64_t n_chunks, int chunk_lo
   const uint64_t need = 16 + (16ull << chunk_log2) + (1ull << chunk_log2) / 2 + 32;
   if (out_stride < need || (out_stride & 15)) return fail(SIM_ERR_INVALID, "out_stride too small or not a multiple of 16");
   if (n_chunks == 0) return SIM_OK;
+  // every size below is a product with n_chunks: bound it first so that none wraps
+  if (out_stride > (1ull << 40) || n_chunks > (1ull << 62) / (out_stride + (16ull << chunk_log2) + 4))
+    return fail(SIM_ERR_INVALID, "n_chunks or out_stride too large");
   const size_t in_bytes = (size_t)n_chunks * (16ull << chunk_log2);
   const double* din = in;
   uint8_t* dout = out;
@@ -1206,6 +1328,9 @@ sim_status sim_codec_decode(const uint8_t* in, uint64_t in_stride, const uint32_
   if (chunk_log2 < 0 || chunk_log2 > qc::kMaxKC) return fail(SIM_ERR_INVALID, "chunk_log2 must be in [0, 11]");
   if (in_stride & 15) return fail(SIM_ERR_INVALID, "in_stride must be a multiple of 16");
   if (n_chunks == 0) return SIM_OK;
+  // every size below is a product with n_chunks: bound it first so that none wraps
+  if (in_stride > (1ull << 40) || n_chunks > (1ull << 62) / (in_stride + (16ull << chunk_log2) + 4))
+    return fail(SIM_ERR_INVALID, "n_chunks or in_stride too large");
   const size_t out_bytes = (size_t)n_chunks * (16ull << chunk_log2);
   const uint8_t* din = in;
   const uint32_t* dlen = in_len;

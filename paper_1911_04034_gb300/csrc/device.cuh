@@ -27,7 +27,7 @@ enum : uint32_t { M_ZERO = 0, M_CONST = 1, M_PERIOD = 2, M_STREAM = 3, M_RAW = 4
 // Solution C's modes; SPLIT (Solution D, re parts then im parts) only on request
 constexpr uint32_t kDefaultModes = 0x1Fu;
 
-enum : uint32_t { E_OK = 0, E_OOM = 1, E_CORRUPT = 2, E_NONFINITE = 4, E_MODE = 8 };
+enum : uint32_t { E_OK = 0, E_OOM = 1, E_CORRUPT = 2, E_NONFINITE = 4, E_MODE = 8, E_TIMEOUT = 16 };
 
 // ---------------------------------------------------------------- sizes ---- //
 __host__ __device__ __forceinline__ uint32_t round16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -75,6 +75,13 @@ struct DevCtl {
   unsigned long long bc_gate_hits;
   unsigned int bc_zero_streak;         // gates in a row with lookups and no hit
   unsigned int bc_off;                 // gates the cache still sits out (0 = on)
+  unsigned long long ndefer;           // work items of the running gate the streaming kernel left to the general one
+  unsigned int fast_all;               // 1: the streaming kernel left every item of the running gate
+  unsigned int fast_pad;
+  unsigned long long fast_items;       // work items the streaming kernel committed (cumulative)
+  unsigned long long fast_deferred;    // work items it left to the general kernel (cumulative)
+  unsigned int timeout_site;           // where a bounded wait gave up (E_TIMEOUT): 1 item start, 2 pass, 3 item end
+  unsigned int timeout_pad;
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -1431,6 +1438,27 @@ __device__ __forceinline__ void apply_pair(const GateCoef& g, double2& a, double
   a.y = row_eval(g, 1, x);
   b.x = row_eval(g, 2, x);
   b.y = row_eval(g, 3, x);
+}
+
+// The first row pair (a'r, a'i) or the second (b'r, b'i) of apply_pair alone, with the
+// same sums in the same order (for a thread that owns only one amplitude of the pair).
+__device__ __forceinline__ double2 apply_rows01(const GateCoef& g, const double2 a, const double2 b) {
+  if (g.dense) {
+    const double* c = g.c;
+    return make_double2(__fma_rn(c[3], b.y, __fma_rn(c[2], b.x, __fma_rn(c[1], a.y, __dmul_rn(c[0], a.x)))),
+                        __fma_rn(c[7], b.x, __fma_rn(c[6], b.y, __fma_rn(c[5], a.x, __dmul_rn(c[4], a.y)))));
+  }
+  const double x[4] = {a.x, a.y, b.x, b.y};
+  return make_double2(row_eval(g, 0, x), row_eval(g, 1, x));
+}
+__device__ __forceinline__ double2 apply_rows23(const GateCoef& g, const double2 a, const double2 b) {
+  if (g.dense) {
+    const double* c = g.c;
+    return make_double2(__fma_rn(c[11], b.y, __fma_rn(c[10], b.x, __fma_rn(c[9], a.y, __dmul_rn(c[8], a.x)))),
+                        __fma_rn(c[15], b.x, __fma_rn(c[14], b.y, __fma_rn(c[13], a.x, __dmul_rn(c[12], a.y)))));
+  }
+  const double x[4] = {a.x, a.y, b.x, b.y};
+  return make_double2(row_eval(g, 2, x), row_eval(g, 3, x));
 }
 
 // Image of a chunk whose amplitudes all equal (v0, v1): what encode_block writes

@@ -10,6 +10,7 @@
 //          change to E, and records the controller's level and fidelity bounds.
 // others   initialisation, codec entry points, readout and the uncompressed path.
 #include "launch.h"
+#include "gate_common.cuh"
 
 // Resident CTAs per SM that the fused kernel's register budget is sized for (the grid
 // follows the occupancy the build achieves).
@@ -69,13 +70,6 @@ struct GateCta {
   unsigned long long next_item;   // item whose entries were prefetched into set cur ^ 1
 };
 
-// Asynchronous 16-byte global -> shared copies (the next item's directory entries).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 // Bulk asynchronous shared -> global copy (one page of a new image); the issuing thread
 // later waits until the source has been read before the buffer is reused.
 __device__ __forceinline__ void bulk_store(void* gmem, const void* smem, uint32_t bytes) {
@@ -201,28 +195,14 @@ __device__ __forceinline__ void cta_end(const GateLaunch& L, GateCta& st, const 
   if (st.acc->wr) atomicAdd(&ctl->bytes_out, st.acc->wr);
 }
 
-// Section 3.7: the bound of the running gate, from E after the previous gate.  Every
-// CTA evaluates the same rule on the same values (only the post kernel writes them).
-__device__ __forceinline__ uint32_t gate_bits(const GateLaunch& L) {
-  return (uint32_t)level_bits(L.ctl, next_level(L.ctl, L.P.ctl->E, L.P.ctl->level));
-}
-
-// The chunk index of the k-th active chunk (or pair): the bits of k deposited into the
-// free chunk-index bits, run by run.
-__device__ __forceinline__ unsigned long long item_chunk(const GateLaunch& L, unsigned long long k) {
-  if (L.nruns < 0) return deposit_bits(k, L.free_mask);
-  unsigned long long out = 0;
-  for (int i = 0; i < L.nruns; ++i) out |= (k << L.run_shift[i]) & L.run_mask[i];
-  return out;
-}
-
 // One work item (two chunks) of a gate: stage, decode, apply, encode, commit.
 // Returns false if the simulator's error word is set (nothing more to do for it).
-// PREF: the CTA's next item is item + gridDim.x of the same gate; its directory
+// PREF: nx is the CTA's next item of the same gate (~0 if none); its directory
 // entries are fetched asynchronously during this item and its pages pulled into L2.
 template <int VPT, bool PREF>
-__device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long long item, uint32_t S,
-                                          unsigned long long serial, bool bc_on, const GateSmem& m, GateCta& st) {
+__device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long long item, unsigned long long nx,
+                                          uint32_t S, unsigned long long serial, bool bc_on, const GateSmem& m,
+                                          GateCta& st) {
   const int kc = L.P.kc;
   const uint32_t A = 1u << kc;
   const uint32_t cap = imgcap(kc);
@@ -274,8 +254,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   // them, and this item touches only its own chunks
   unsigned long long nc0 = 0, nc1 = 0;
   bool nhas1 = false;
-  if (PREF && item + gridDim.x < L.items) {
-    const unsigned long long nx = item + gridDim.x;
+  if (PREF && nx != ~0ull) {
     if (L.pair) {
       nc0 = item_chunk(L, nx) | L.hi_vals;
       nc1 = nc0 | L.pair_bit;
@@ -584,8 +563,15 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_
   const uint32_t S = gate_bits(L);
   const unsigned long long serial = L.P.ctl->gates + 1ull;
   const bool bc_on = L.bc != nullptr && L.P.ctl->bc_off == 0u;
-  for (unsigned long long item = blockIdx.x; item < L.items; item += gridDim.x)
-    if (!gate_item<VPT, true>(L, item, S, serial, bc_on, m, st)) break;
+  // all items of the gate, or (list) those the streaming kernel left to this one
+  const bool listed = L.list && !L.P.ctl->fast_all;
+  const unsigned long long count = listed ? L.P.ctl->ndefer : L.items;
+  for (unsigned long long k = blockIdx.x; k < count; k += gridDim.x) {
+    const unsigned long long nk = k + gridDim.x;
+    const unsigned long long item = listed ? (unsigned long long)L.defer[k] : k;
+    const unsigned long long nx = nk < count ? (listed ? (unsigned long long)L.defer[nk] : nk) : ~0ull;
+    if (!gate_item<VPT, true>(L, item, nx, S, serial, bc_on, m, st)) break;
+  }
   cp_async_wait_all();  // no copy may still target shared memory at exit
   bulk_wait_all();      // nor read from it
   cta_end(L, st, s_ph);
@@ -629,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
       serial = jobs[cur].L.P.ctl->gates + 1ull;
       bc_on = jobs[cur].L.bc != nullptr && jobs[cur].L.P.ctl->bc_off == 0u;
     }
-    gate_item<VPT, false>(jobs[cur].L, g - jobs[cur].begin, S, serial, bc_on, m, st);
+    gate_item<VPT, false>(jobs[cur].L, g - jobs[cur].begin, ~0ull, S, serial, bc_on, m, st);
   }
   bulk_wait_all();  // no bulk page store may still read shared memory at exit
   if (cur >= 0) cta_end(jobs[cur].L, st, s_ph);
@@ -642,24 +628,34 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
   __shared__ unsigned long long s_top;
   if (threadIdx.x == 0) s_top = (unsigned long long)ctl->top;
   __syncthreads();
+  // every warp takes its slots of the stack with one atomic (loop bounds rounded to whole
+  // warps, so all lanes vote)
+  const uint32_t lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
   const unsigned long long slots = (unsigned long long)grid_ctas * kCacheCap;
-  for (unsigned long long q = threadIdx.x; q < slots; q += blockDim.x) {
-    const unsigned long long b = q / kCacheCap, i = q % kCacheCap;
-    if (i < P.cache_n[b]) {
-      const unsigned long long pos = atomicAdd(&s_top, 1ull);
-      P.stack[pos] = P.cache[q];
-    }
+  for (unsigned long long q = threadIdx.x; q < ((slots + 31ull) & ~31ull); q += blockDim.x) {
+    const bool has = q < slots && (q % kCacheCap) < P.cache_n[q / kCacheCap];
+    const uint32_t m = __ballot_sync(0xffffffffu, has);
+    unsigned long long base = 0;
+    if (lane == 0 && m) base = atomicAdd(&s_top, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (has) P.stack[base + __popc(m & below)] = P.cache[q];
   }
   const unsigned long long nf = ctl->nfreed;
-  for (unsigned long long i = threadIdx.x; i < nf; i += blockDim.x) {
-    const unsigned long long pos = atomicAdd(&s_top, 1ull);
-    P.stack[pos] = P.freed[i];
+  for (unsigned long long i = threadIdx.x; i < ((nf + 31ull) & ~31ull); i += blockDim.x) {
+    const bool has = i < nf;
+    const uint32_t m = __ballot_sync(0xffffffffu, has);
+    unsigned long long base = 0;
+    if (lane == 0 && m) base = atomicAdd(&s_top, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (has) P.stack[base + __popc(m & below)] = P.freed[i];
   }
   __syncthreads();
   for (unsigned long long b = threadIdx.x; b < (unsigned long long)grid_ctas; b += blockDim.x) P.cache_n[b] = 0;
   if (threadIdx.x == 0) {
     ctl->top = (long long)s_top;
     ctl->nfreed = 0;
+    ctl->ndefer = 0;
+    ctl->fast_all = 0u;
     const int lvl = next_level(cp, ctl->E, ctl->level);
     const int S = level_bits(cp, lvl);
     if (lvl > 0 && ctl->switch_gate < 0) ctl->switch_gate = (long long)ctl->gates;

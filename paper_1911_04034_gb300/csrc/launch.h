@@ -34,6 +34,17 @@ struct GateLaunch {
   unsigned long long* trace_n;
   unsigned long long trace_cap;
   uint8_t* bc;                   // block cache lines (kBcLines of bc_line_bytes) or nullptr
+  uint32_t* defer;               // streaming kernel: items left to the general kernel (device list)
+  int fast_kind;                 // streaming kernel: 0 cross-chunk pairs, 1 in-chunk target < 2, 2 in-chunk
+                                 // target 2..6 (partner in another lane), 3 in-chunk diagonal gate
+  int list;                      // general kernel: 1 = run the items the streaming kernel left
+  // streaming kernel arithmetic (the same values as the kept-term sums of GateCoef):
+  int arith;                     // 0 dense: the four sums with every coefficient, zeros included;
+                                 // 1 diagonal (u01 = u10 = 0); 2 anti-diagonal (u00 = u11 = 0)
+  int rop[2];                    // diagonal / anti-diagonal, per output row: 0 complex product, 1 copy
+                                 // (the entry is exactly 1), 2 negation (exactly -1)
+  double cf[16];                 // dense: row r's coefficients of (ar, ai, br, bi) / (ai, ar, bi, br) at 4r
+  double du[4];                  // diagonal: u00, u11; anti-diagonal: u01, u10 (re, im)
 };
 
 // One gate of one simulator inside a batched launch; its work items are the global
@@ -46,12 +57,25 @@ struct BatchJob {
 // Records the message sim_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 
+// Eq. sigbits: significant bits S = 12 - EXP(eps) kept of a binary64 value under the
+// pointwise relative bound eps (EXP = the IEEE exponent of eps); 64 for eps = 0 (the
+// lossless stage); -1 for a bound outside {0} U [2^-52, 1).
+int sig_bits_of(double eps);
+
 int vpt_for(int kc);
 size_t gate_smem_bytes(int kc);
 size_t codec_smem_bytes(int kc);
 int gate_ctas_per_sm(int kc);
 
 cudaError_t launch_gate(const GateLaunch& L, int grid, cudaStream_t st);
+// The streaming kernel (chunk_log2 in [7, 11]): the work items it can take whole, the
+// rest appended to L.defer for launch_gate with L.list = 1 right after it.
+constexpr int kFastMinKC = 7;
+int fast_ctas_per_sm(int kc);
+int fast_warps();        // warps per CTA of the streaming kernel (a pair of warps per work item)
+int fast_pairs();        // work items a CTA of the streaming kernel runs at once
+int fast_warp_cache();   // page ids each of its warps may hold
+cudaError_t launch_gate_fast(const GateLaunch& L, int grid, cudaStream_t st);
 cudaError_t launch_post(const Pool& P, const CtlParams& cp, int grid_ctas, cudaStream_t st);
 cudaError_t launch_gate_batch(const BatchJob* jobs, int njobs, unsigned long long total, int kc, int grid,
                               cudaStream_t st);

@@ -14,8 +14,12 @@
 // process exits.  All calls on a device share it, so two calls whose work overlaps
 // on that device (different host threads or streams) race on it: callers must
 // serialise them.  Each call rewrites the parts it uses (inputs, images, lengths,
-// error word), so nothing from an earlier call leaks into its result.
-#include <cstring>
+// error word), so nothing from an earlier call leaks into its result.  The first
+// call on a device looks up the array's device address (under a lock, so concurrent
+// first calls from several host threads are safe) and keeps it; a cudaDeviceReset
+// unloads the module and invalidates that address, so this entry point must not be
+// used on a device after it was reset.
+#include <mutex>
 
 #include "../../include/qcsim.h"
 #include "launch.h"
@@ -31,6 +35,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 // device current (host code cannot use the symbol itself as a device pointer).
 constexpr int kMaxDevices = 64;
 static void* g_scratch_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_scratch_lock;
 
 sim_status noalloc_fail(sim_status s, const char* msg) {
   qc::set_last_error(msg);
@@ -44,19 +49,16 @@ extern "C" sim_status sim_codec_encode_noalloc(const double* in, uint64_t n_chun
   if (!in || !out || !out_len) return noalloc_fail(SIM_ERR_INVALID, "NULL argument");
   if (chunk_log2 < 0 || chunk_log2 > qc::kMaxKC) return noalloc_fail(SIM_ERR_INVALID, "chunk_log2 outside [0, 11]");
   if (force_mode >= (int)qc::M_NMODES) return noalloc_fail(SIM_ERR_INVALID, "unknown mode");
-  // Eq. sigbits: S = 12 - EXP(eps) for binary64; eps = 0 keeps all 64 bits
-  int S = 64;
-  if (eps != 0.0) {
-    if (!(eps > 0.0) || !(eps < 1.0)) return noalloc_fail(SIM_ERR_INVALID, "eps outside {0} U [2^-52, 1)");
-    uint64_t b;
-    std::memcpy(&b, &eps, 8);
-    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
-    if (ex < -52) return noalloc_fail(SIM_ERR_INVALID, "eps outside {0} U [2^-52, 1)");
-    S = 12 - ex > 64 ? 64 : 12 - ex;
-  }
+  const int S = qc::sig_bits_of(eps);  // Eq. sigbits, as every other entry point maps eps
+  if (S < 0) return noalloc_fail(SIM_ERR_INVALID, "eps outside {0} U [2^-52, 1)");
   const uint64_t need = 16 + (16ull << chunk_log2) + (1ull << chunk_log2) / 2 + 32;
   if (out_stride < need || (out_stride & 15)) return noalloc_fail(SIM_ERR_INVALID, "out_stride too small or not 16-aligned");
   if (n_chunks == 0) return SIM_OK;
+  // Bound the request before forming any product with n_chunks, so that none can wrap:
+  // each chunk needs its input, its image slot and its length in the array.
+  if (out_stride > kNoAllocScratchBytes ||
+      n_chunks > kNoAllocScratchBytes / ((16ull << chunk_log2) + out_stride + 4))
+    return noalloc_fail(SIM_ERR_INVALID, "request larger than the 8 MiB scratch");
   // layout inside the static array: [error word | pad to 256][inputs][images][lengths]
   const uint64_t in_bytes = n_chunks * (16ull << chunk_log2);
   const uint64_t img_bytes = n_chunks * out_stride;
@@ -70,13 +72,18 @@ extern "C" sim_status sim_codec_encode_noalloc(const double* in, uint64_t n_chun
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return noalloc_fail(SIM_ERR_CUDA, "cudaGetDevice failed or device index too large");
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
-      return noalloc_fail(SIM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-    g_scratch_ptr[dev] = p;
+  void* ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> guard(g_scratch_lock);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+        return noalloc_fail(SIM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+      g_scratch_ptr[dev] = p;
+    }
+    ptr = g_scratch_ptr[dev];
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(ptr);
   unsigned int* derr = reinterpret_cast<unsigned int*>(base);
   double* din = reinterpret_cast<double*>(base + off_in);
   uint8_t* dimg = base + off_img;

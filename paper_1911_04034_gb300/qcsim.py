@@ -42,6 +42,7 @@ class Stats(C.Structure):
         ("phase_cycles", C.c_uint64 * 6),
         ("split_trials", C.c_uint64),
         ("cache_lookups", C.c_uint64), ("cache_hits", C.c_uint64),
+        ("fast_items", C.c_uint64), ("fast_deferred", C.c_uint64), ("kernel_launches", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -100,6 +101,7 @@ def lib():
             "sim_mlp_grad": [vp, vp, vp, vp, u64, vp, C.POINTER(C.c_float)],
             "sim_timing": [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                            C.POINTER(C.c_uint64)],
+            "sim_timing_launches": [vp, u64, vp, vp, vp, C.POINTER(C.c_uint64)],
             "sim_sv_create": [i32, pp],
             "sim_sv_destroy": [vp],
             "sim_sv_set_stream": [vp, vp],
@@ -299,6 +301,20 @@ class Sim:
         _check(lib().sim_timing(self._h, C.byref(ms), C.byref(n), C.byref(rd), C.byref(wr)), "sim_timing")
         return {"gate_kernel_ms": float(ms.value), "launches": int(n.value), "bytes_read": int(rd.value),
                 "bytes_written": int(wr.value)}
+
+    def timing_launches(self) -> dict:
+        """Per gate-kernel launch since timing was switched on or last read by timing():
+        CUDA-event ms and image bytes read / written (call before timing())."""
+        n = C.c_uint64()
+        _check(lib().sim_timing_launches(self._h, 0, None, None, None, C.byref(n)), "sim_timing_launches")
+        k = int(n.value)
+        ms = np.zeros(k, dtype=np.float32)
+        rd = np.zeros(k, dtype=np.uint64)
+        wr = np.zeros(k, dtype=np.uint64)
+        if k:
+            _check(lib().sim_timing_launches(self._h, k, C.c_void_p(_ptr(ms)), C.c_void_p(_ptr(rd)),
+                                             C.c_void_p(_ptr(wr)), C.byref(n)), "sim_timing_launches")
+        return {"ms": ms, "bytes_read": rd, "bytes_written": wr}
 
     def chunk_image(self, c: int) -> bytes:
         cap = 16 + (16 << self.chunk_log2) + 64
