@@ -177,6 +177,8 @@ struct sim {
     cudaFree(P.freed);
     cudaFree(P.cache);
     cudaFree(P.cache_n);
+    cudaFree(P.wcache);
+    cudaFree(P.wcache_n);
     cudaFree(d_ctl);
     cudaFree(d_counts);
     cudaFree(d_scratch);
@@ -310,6 +312,10 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
       {(void**)&P.freed, (size_t)s->npages * 4, "freed list"},
       {(void**)&P.cache, (size_t)s->grid * qc::kCacheCap * 4, "page caches"},
       {(void**)&P.cache_n, (size_t)s->grid * 4, "page cache counts"},
+      {(void**)&P.wcache, (size_t)(s->fast_grid ? s->fast_grid : 1) * qc::fast_warps() * qc::fast_warp_cache() * 4,
+       "streaming-kernel page caches"},
+      {(void**)&P.wcache_n, (size_t)(s->fast_grid ? s->fast_grid : 1) * qc::fast_warps() * 4,
+       "streaming-kernel page cache counts"},
       {(void**)&s->d_ctl, sizeof(DevCtl), "counters"},
       {(void**)&s->d_counts, 8 * sizeof(unsigned long long), "mode counts"},
       {(void**)&s->d_defer, (size_t)(s->nchunks / 2 + 1) * sizeof(uint32_t), "deferred-item list"},
@@ -330,6 +336,7 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
   h.S_last = 64;
   cudaError_t e = cudaMemcpy(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(P.cache_n, 0, (size_t)s->grid * 4);
+  if (e == cudaSuccess) e = cudaMemset(P.wcache_n, 0, (size_t)(s->fast_grid ? s->fast_grid : 1) * qc::fast_warps() * 4);
   if (e == cudaSuccess) e = qc::launch_pool_init(P, s->nchunks, 0);
   if (e == cudaSuccess) e = qc::launch_init_chunk0(P, s->nchunks, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -877,7 +884,7 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->inflight_bytes = s->cp.inflight;
   for (int k = 0; k < 8; ++k) o->chunks_by_mode[k] = counts[k];
   o->pool_bytes = s->npages * qc::kPage;
-  o->pages_in_use_bytes = (s->npages - (uint64_t)h.top) * qc::kPage;
+  o->pages_in_use_bytes = (s->npages - (uint64_t)h.top - h.wc_pages) * qc::kPage;  // pages holding images
   o->peak_pages_bytes = h.peak_pages * qc::kPage;
   o->device_bytes = s->device_bytes + s->scratch_bytes;
   o->amp_updates = s->amp_updates;
@@ -1255,6 +1262,8 @@ sim_status sim_checkpoint_load(sim_t* s, const void* in, uint64_t in_len, int in
     e = cudaMemcpyAsync(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(s->P.cache_n, 0, (size_t)s->grid * sizeof(uint32_t), s->st);
+  if (e == cudaSuccess)  // the streaming kernel's warp caches held pages of the replaced arena
+    e = cudaMemsetAsync(s->P.wcache_n, 0, (size_t)(s->fast_grid ? s->fast_grid : 1) * qc::fast_warps() * 4, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   cudaFree(d_off);
   cudaFree(d_pb);

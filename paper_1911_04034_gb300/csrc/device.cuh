@@ -82,6 +82,7 @@ struct DevCtl {
   unsigned long long fast_deferred;    // work items it left to the general kernel (cumulative)
   unsigned int timeout_site;           // where a bounded wait gave up (E_TIMEOUT): 1 item start, 2 pass, 3 item end
   unsigned int timeout_pad;
+  unsigned long long wc_pages;         // free pages the streaming kernel's warps keep in their caches
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -133,6 +134,8 @@ struct Pool {
   uint32_t* freed;         // overflow list, [0, nfreed)
   uint32_t* cache;         // grid * kCacheCap page ids
   uint32_t* cache_n;       // grid counts
+  uint32_t* wcache;        // streaming kernel: page ids each of its warps keeps across launches
+  uint32_t* wcache_n;      // ... and their counts (one per warp of its grid)
   DevCtl* ctl;
   unsigned long long npages;
   uint32_t dir_words;      // dir_stride / 4

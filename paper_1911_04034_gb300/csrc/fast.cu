@@ -44,12 +44,11 @@ constexpr uint32_t kWinBlocks = kFastWin / 16;
 constexpr uint32_t kWarpCache = 64;   // page ids a warp keeps between its items
 
 __host__ __device__ __forceinline__ uint32_t fast_pg_words(int kc) { return (max_pages(kc) + 3u) & ~3u; }
-// Per warp (one chunk): input codes, output codes (2^(kc+1) / 4 bytes each), two input
-// windows, one output window, the input and the output page ids, the values it shows
-// its partner warp (two passes), its page cache, the first half's sampled values.
+// Per warp (one chunk): two input windows, one output window, the input and the output
+// page ids, the values it shows its partner warp (two passes), its page cache, one
+// sample per lane of each pass of the chunk's first half.
 __host__ __device__ __forceinline__ uint32_t fast_warp_bytes(int kc) {
-  return 2u * (1u << (kc - 1)) + 3u * kFastWin + 8u * fast_pg_words(kc) + 2u * 1024u + 4u * kWarpCache + 16u +
-         (1u << kc);
+  return 3u * kFastWin + 8u * fast_pg_words(kc) + 2u * 1024u + 4u * kWarpCache + 16u + (1u << (kc - 1));
 }
 // Largest STREAM image of a chunk at S <= 32 bits.
 __host__ __device__ __forceinline__ uint32_t fast_max_image(int kc) {
@@ -177,6 +176,14 @@ __device__ __forceinline__ uint32_t lead_compose(uint32_t A, uint32_t B) {
 // all lanes) the top bytes of the warp's last value.
 __device__ __forceinline__ uint32_t lead_scan_warp(uint32_t W, uint32_t carry, uint32_t& after) {
   const uint32_t lane = threadIdx.x & 31u;
+  if (__all_sync(0xffffffffu, (W & 3u) == 0u)) {
+    // every lane has a value with code 0 (all three leading bytes explicit): a lane's
+    // predecessor's leading bytes are the previous lane's run alone
+    uint32_t exc = __shfl_up_sync(0xffffffffu, W, 1);
+    if (lane == 0) exc = carry;
+    after = __shfl_sync(0xffffffffu, W, 31) & 0xFFFFFF00u;
+    return exc & 0xFFFFFF00u;
+  }
   uint32_t inc = W;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -390,40 +397,51 @@ __device__ __forceinline__ void fast_pair_in_lane(const GateLaunch& L, uint32_t 
 
 // Shared-memory buffers of one warp (its chunk of the pair's item).
 struct FastWarp {
-  uint32_t* icode;
-  uint32_t* ocode;
   uint32_t* iwin0;
   uint32_t* iwin1;
   uint32_t* owin;
   uint32_t* ipg;
   uint32_t* opg;
   uint32_t* xch;  // [2][256]: the pass's decoded high words, for the partner warp
-  uint2* half;    // [passes / 2][32]: two sampled values per lane of each first-half pass
+  uint32_t* half;  // [passes / 2][32]: one sample per lane of each first-half pass
 };
 
 __device__ __forceinline__ FastWarp fast_warp(uint8_t* base, int kc) {
-  const uint32_t cb = 1u << (kc - 1);
   FastWarp f;
-  f.icode = reinterpret_cast<uint32_t*>(base);
-  f.ocode = reinterpret_cast<uint32_t*>(base + cb);
-  f.iwin0 = reinterpret_cast<uint32_t*>(base + 2u * cb);
+  f.iwin0 = reinterpret_cast<uint32_t*>(base);
   f.iwin1 = f.iwin0 + kFastWin / 4u;
   f.owin = f.iwin1 + kFastWin / 4u;
   f.ipg = f.owin + kFastWin / 4u;
   f.opg = f.ipg + fast_pg_words(kc);
   f.xch = f.opg + fast_pg_words(kc);
-  f.half = reinterpret_cast<uint2*>(f.xch + 512u + kWarpCache + 4u);
+  f.half = f.xch + 512u + kWarpCache + 4u;
   return f;
 }
 
 // One work item: this warp's chunk (side 0 or 1 of the pair).  Returns 0 when both
 // chunks were committed, 1 when the pair left the item to the general kernel (nothing
 // of the state changed), 2 when the pair stops (a device error is set).
+// Per-phase SM cycles of a warp when profiling (lane 0 counts): 0 staging (directory
+// entries, headers, the partners' agreement, waits for input windows), 1 decoding, 2 the
+// gate (with the exchange between the partners), 3 encoding, 4 committing (finished
+// blocks, header, codes, directory entry, pages).
+struct FastPhases {
+  long long* t;  // shared memory: the five sums, then the last clock
+  bool on;
+  __device__ __forceinline__ void mark(int k) {
+    if (on) {
+      const long long now = clock64();
+      t[k] += now - t[5];
+      t[5] = now;
+    }
+  }
+};
+
 template <int KIND, int ARITH>
 __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long item, uint32_t S, const FastWarp& fw,
                                          const uint32_t* xpeer, const WarpPages& wp, uint32_t side,
                                          volatile uint32_t* seq, uint32_t* slots, uint32_t& phase, long long& dE,
-                                         unsigned long long& rd, unsigned long long& wr) {
+                                         unsigned long long& rd, unsigned long long& wr, FastPhases& ph) {
   const Pool& P = L.P;
   const int kc = P.kc;
   const uint32_t lane = threadIdx.x & 31u;
@@ -471,25 +489,29 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
     if (!((mine & other) & 1u)) return 1;
   }
   const uint32_t nbs = (ib - 16u - cb) >> 4;
-  // input codes (one group), the first pass's window (a second group); output window cleared
-  for (uint32_t u = lane; u < cb / 16u; u += 32u) {
-    const uint32_t b = 16u + 16u * u;
-    cp_async16(fw.icode + 4u * u, P.pages + (unsigned long long)fw.ipg[b >> 9] * kPage + (b & (kPage - 1u)));
-  }
-  cp_async_commit();
+  // the code word of this lane's values in pass p (image byte 16 + 64 p + 4 (lane / 2))
+  auto code_word_at = [&](uint32_t p) -> uint32_t {
+    const uint32_t b = 16u + 64u * p + 4u * (lane >> 1);
+    return *reinterpret_cast<const uint32_t*>(P.pages + (unsigned long long)fw.ipg[b >> 9] * kPage + (b & (kPage - 1u)));
+  };
+  uint32_t cw_next = code_word_at(0u);
+  // the first pass's window; output window cleared; the output pages of header and codes
   fast_issue_window(P, fw.ipg, fw.iwin0, cb, 0u, nbs);
   cp_async_commit();
   for (uint32_t k = lane; k < kWinBlocks; k += 32u) reinterpret_cast<uint4*>(fw.owin)[k] = make_uint4(0u, 0u, 0u, 0u);
-  cp_async_wait_group<1>();  // the codes
+  uint32_t onp = 0u;
+  bool oom = !wp_grow(P, wp, fw.opg, onp, (16u + cb + kPage - 1u) / kPage);
   __syncwarp();
+  ph.mark(0);
   const uint32_t mh = (uint32_t)(trunc_mask(S) >> 32), mhin = (uint32_t)(trunc_mask(Sin) >> 32);
-  uint32_t ioff = 0u, ooff = 0u, lead = 0u, prv = 0u, refr = 0u, refi = 0u, nzor = 0u, onp = 0u;
-  bool spec = false, cst = true, oom = false, halves = true, lost = false;
+  uint32_t ioff = 0u, ooff = 0u, lead = 0u, prv = 0u, refr = 0u, refi = 0u, nzor = 0u;
+  bool spec = false, cst = true, halves = true, lost = false;
   for (uint32_t p = 0; p < NP; ++p) {
     uint32_t* const win = (p & 1u) ? fw.iwin1 : fw.iwin0;
     uint32_t* const wnext = (p & 1u) ? fw.iwin0 : fw.iwin1;
     // residual lengths of this lane's 8 values, their offsets in the pass
-    const uint32_t cw = (fw.icode[16u * p + (lane >> 1)] >> (16u * (lane & 1u))) & 0xffffu;
+    const uint32_t cw = (cw_next >> (16u * (lane & 1u))) & 0xffffu;
+    if (p + 1u < NP) cw_next = code_word_at(p + 1u);  // in flight while this pass runs
     uint32_t tot;
     const uint32_t ps = ioff;
     const uint32_t o = ps + warp_excl(rsum8(cw, Sin), tot);
@@ -497,8 +519,10 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
     // the next pass's window is in flight while this pass runs
     if (p + 1u < NP) fast_issue_window(P, fw.ipg, wnext, cb, ioff >> 7, nbs);
     cp_async_commit();
+    ph.mark(1);
     cp_async_wait_group<1>();
     __syncwarp();
+    ph.mark(0);
     // explicit parts, leading bytes from the predecessors
     uint32_t v[8];
     {
@@ -508,12 +532,14 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
       lead = after;
       fast_rebuild(v, cw, Pl);
     }
+    ph.mark(1);
     // the gate on every amplitude pair whose in-chunk control bits match; results
     // truncated to S bits in place
     const uint32_t ibase = 128u * p + 4u * lane;  // the lane's first amplitude in the chunk
     uint32_t w[8];                                // the partner amplitudes' high words (kinds 0 and 2)
-    if constexpr (KIND == 0) {
+    if constexpr (KIND == 0 && ARITH != 1) {
       // the partner warp holds the other amplitude of every pair, at the same position
+      // (a diagonal gate needs only the amplitude itself)
       uint32_t* xs = fw.xch + 256u * (p & 1u);
       reinterpret_cast<uint4*>(xs)[2u * lane] = make_uint4(v[0], v[1], v[2], v[3]);
       reinterpret_cast<uint4*>(xs)[2u * lane + 1u] = make_uint4(v[4], v[5], v[6], v[7]);
@@ -566,6 +592,7 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
         v[2 * k + 1] = outi;
       }
     }
+    ph.mark(2);
     // encoder: constant-chunk and period filters, codes, output offsets
     if (p == 0u) {
       refr = __shfl_sync(0xffffffffu, v[0], 0);
@@ -587,10 +614,9 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
         const uint32_t b = __shfl_xor_sync(0xffffffffu, v[5], 16);
         halves &= (a == v[0]) & (b == v[5]);
       } else if (p < NP / 2u) {
-        fw.half[32u * p + lane] = make_uint2(v[0], v[5]);
+        fw.half[32u * p + lane] = v[0] ^ __funnelshift_l(v[5], v[5], 13);
       } else {
-        const uint2 h = fw.half[32u * (p - NP / 2u) + lane];
-        halves &= h.x == v[0] && h.y == v[5];
+        halves &= fw.half[32u * (p - NP / 2u) + lane] == (v[0] ^ __funnelshift_l(v[5], v[5], 13));
       }
     }
     uint32_t osum, otot;
@@ -599,9 +625,13 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
     fast_pack(fw.owin, 4u * ob, ooff + warp_excl(osum, otot), v, ocw, S);
     // codes: two lanes fill one 32-bit word
     const uint32_t pairw = ocw | (__shfl_down_sync(0xffffffffu, ocw, 1) << 16);
-    if ((lane & 1u) == 0u) fw.ocode[16u * p + (lane >> 1)] = pairw;
+    if ((lane & 1u) == 0u && !oom) {  // image byte 16 + 64 p + 2 lane
+      const uint32_t b = 16u + 64u * p + 2u * lane;
+      *reinterpret_cast<uint32_t*>(P.pages + (unsigned long long)fw.opg[b >> 9] * kPage + (b & (kPage - 1u))) = pairw;
+    }
     ooff += otot;
     __syncwarp();
+    ph.mark(3);
     // finished blocks to the pages (the last pass also its unfinished one, zero-padded)
     const bool last = p + 1u == NP;
     const uint32_t endb = last ? (ooff + 127u) >> 7 : ooff >> 7;
@@ -622,6 +652,7 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
       for (uint32_t k = lane; k <= nb; k += 32u) z[k] = k == 0u ? carry : make_uint4(0u, 0u, 0u, 0u);
       __syncwarp();
     }
+    ph.mark(4);
   }
   // every input bit consumed exactly (else the image is corrupt); this chunk a STREAM
   // image unless it is constant or possibly periodic, or holds special values
@@ -639,13 +670,8 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
     __syncwarp();
     return ((mine | other) & 2u) ? 2 : 1;
   }
-  // header and codes, then the directory entry; the old pages freed
+  // the header, then the directory entry; the old pages freed
   const uint32_t plen = cb + resid_bytes(ooff), bytes = 16u + plen;
-  for (uint32_t u = lane; u < cb / 16u; u += 32u) {
-    const uint32_t b = 16u + 16u * u;
-    reinterpret_cast<uint4*>(P.pages + (unsigned long long)fw.opg[b >> 9] * kPage + (b & (kPage - 1u)))[0] =
-        reinterpret_cast<const uint4*>(fw.ocode)[u];
-  }
   if (lane == 0)
     reinterpret_cast<uint4*>(P.pages + (unsigned long long)fw.opg[0] * kPage)[0] = make_uint4(M_STREAM | (S << 8), plen, N, ooff);
   uint32_t* e = dir_entry(P, ch);
@@ -658,6 +684,7 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
     wr += bytes;
   }
   wp_free(P, wp, fw.ipg, inp);
+  ph.mark(4);
   return 0;
 }
 
@@ -680,17 +707,32 @@ __global__ void __launch_bounds__(kFastThreads, QC_FAST_MIN_CTAS) k_gate_fast(co
   uint8_t* wb = smem + (size_t)wid * fast_warp_bytes(kc);
   const FastWarp fw = fast_warp(wb, kc);
   const uint32_t* xpeer = fast_warp(smem + (size_t)(wid ^ 1u) * fast_warp_bytes(kc), kc).xch;
+  // the warp's page cache, kept in global memory between launches
   WarpPages wp;
   wp.ids = fw.xch + 512u;
   wp.n = wp.ids + kWarpCache;
-  if (lane == 0) *wp.n = 0u;
-  __syncwarp();
+  const size_t gw = (size_t)blockIdx.x * kFastWarps + wid;
+  const uint32_t n_start = L.P.wcache_n[gw];
+  {
+    const uint32_t n = n_start;
+    for (uint32_t q = lane; q < n; q += 32u) wp.ids[q] = L.P.wcache[gw * kWarpCache + q];
+    if (lane == 0) *wp.n = n;
+    __syncwarp();
+  }
   uint32_t phase = 0;
+  __shared__ long long s_ph[kFastWarps][6];
+  FastPhases ph;
+  ph.t = s_ph[wid];
+  ph.on = L.prof && lane == 0;
+  if (ph.on) {
+    for (int k = 0; k < 5; ++k) ph.t[k] = 0;
+    ph.t[5] = clock64();
+  }
   long long dE = 0;
   unsigned long long rd = 0, wr = 0, done = 0, deferred = 0;
   const unsigned long long pairs = (unsigned long long)gridDim.x * kFastPairs;
   for (unsigned long long item = (unsigned long long)blockIdx.x * kFastPairs + pr; item < L.items; item += pairs) {
-    const int r = fast_item<KIND, ARITH>(L, item, S, fw, xpeer, wp, side, s_seq[pr], s_slots[pr], phase, dE, rd, wr);
+    const int r = fast_item<KIND, ARITH>(L, item, S, fw, xpeer, wp, side, s_seq[pr], s_slots[pr], phase, dE, rd, wr, ph);
     if (r == 2) break;
     if (r == 1) {
       if (side == 0 && lane == 0) {
@@ -704,14 +746,13 @@ __global__ void __launch_bounds__(kFastThreads, QC_FAST_MIN_CTAS) k_gate_fast(co
   }
   cp_async_wait_all();
   __syncwarp();
-  // the warp's cached pages back to the freed list (the post kernel returns them)
+  // the warp's cached pages stay with it for the next launch
   {
     const uint32_t n = *wp.n;
-    unsigned long long base = 0;
-    if (n) {
-      if (lane == 0) base = atomicAdd(&ctl->nfreed, (unsigned long long)n);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      for (uint32_t q = lane; q < n; q += 32u) L.P.freed[base + q] = wp.ids[q];
+    for (uint32_t q = lane; q < n; q += 32u) L.P.wcache[gw * kWarpCache + q] = wp.ids[q];
+    if (lane == 0) {
+      L.P.wcache_n[gw] = n;
+      if (n != n_start) atomicAdd(&ctl->wc_pages, (unsigned long long)((long long)n - (long long)n_start));
     }
   }
   if (lane == 0) {
@@ -720,6 +761,9 @@ __global__ void __launch_bounds__(kFastThreads, QC_FAST_MIN_CTAS) k_gate_fast(co
     if (wr) atomicAdd(&ctl->bytes_out, wr);
     if (done) atomicAdd(&ctl->fast_items, done);
     if (deferred) atomicAdd(&ctl->fast_deferred, deferred);
+    if (ph.on)
+      for (int k = 0; k < 5; ++k)
+        if (ph.t[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)ph.t[k]);
   }
 }
 

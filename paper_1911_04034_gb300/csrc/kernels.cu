@@ -684,7 +684,7 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
         ctl->bc_zero_streak = 0u;
       }
     }
-    const unsigned long long in_use = P.npages - s_top;
+    const unsigned long long in_use = P.npages - s_top - ctl->wc_pages;  // pages holding images
     if (in_use > ctl->peak_pages) ctl->peak_pages = in_use;
   }
 }
