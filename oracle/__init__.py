@@ -31,7 +31,8 @@ _lib = None
 OK, ERR_INVALID, ERR_OOM, ERR_CORRUPT, ERR_STATE = 0, -1, -2, -4, -6
 MODE_ZERO, MODE_CONST, MODE_PERIOD, MODE_STREAM, MODE_RAW, MODE_SPLIT = 0, 1, 2, 3, 4, 5
 MODE_NAMES = ("ZERO", "CONST", "PERIOD", "STREAM", "RAW", "SPLIT")
-DEFAULT_MODES = 0x1F  # Solution C; SPLIT (Solution D) only when asked for
+DEFAULT_MODES = 0x1F  # Solution C; SPLIT (Solution D) and PALETTE only when asked for
+ALL_MODES = 0x7F      # ZERO, CONST, PERIOD, STREAM, RAW, SPLIT, PALETTE
 
 
 class OracleError(RuntimeError):
@@ -187,7 +188,7 @@ def encode_chunk(values, kc: int, S: int, force_mode: int = -1, modes: int = DEF
     """values: 2^kc complex128 amplitudes (or 2^(kc+1) float64 / uint64 patterns)."""
     x = _as_bits(values)
     assert x.size == 2 << kc, (x.size, kc)
-    cap = 16 + 8 * x.size + x.size // 4 + 64  # forced STREAM can exceed RAW
+    cap = 16 + 9 * x.size + x.size // 4 + 2048 + 64  # forced STREAM or PALETTE can exceed RAW
     out = np.zeros(cap, dtype=np.uint8)
     L = lib().orc_encode_chunk_mask(_ptr(x, C.c_uint64), kc, S, force_mode, modes, _ptr(out, C.c_uint8), cap)
     if L < 0:
@@ -211,7 +212,7 @@ def mode_sizes(values, kc: int, S: int) -> list[int]:
     rc = lib().orc_mode_sizes(_ptr(x, C.c_uint64), kc, S, _ptr(sizes, C.c_uint64))
     if rc:
         raise OracleError(rc, "mode_sizes")
-    return [int(s) for s in sizes[:6]]
+    return [int(s) for s in sizes[:7]]
 
 
 # ---------------------------------------------------------- state vector --- #

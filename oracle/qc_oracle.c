@@ -41,8 +41,10 @@
 #define ORC_MODE_STREAM 3
 #define ORC_MODE_RAW 4
 #define ORC_MODE_SPLIT 5
-#define ORC_NMODES 6
-#define ORC_DEFAULT_MODES 0x1F /* Solution C: ZERO..RAW; SPLIT (Solution D) on request */
+#define ORC_MODE_PALETTE 6
+#define ORC_NMODES 7
+#define ORC_DEFAULT_MODES 0x1F /* Solution C: ZERO..RAW; SPLIT (Solution D) and PALETTE on request */
+#define ORC_PALETTE_MAX 256    /* most distinct values a PALETTE image lists */
 
 /* Planted-mistake switch used only by the mutation tests: each nonzero value
  * introduces one plausible bug so the tests can show that some pin catches it. */
@@ -161,6 +163,12 @@ static uint64_t bw_get(const uint64_t* w, uint64_t pos, int r) {
  *   RAW    : the N truncated values verbatim.
  *   SPLIT  : Solution D (Section 4.2): the real parts of all amplitudes, then the
  *            imaginary parts, XOR-coded like STREAM (enabled by a mode mask).
+ *   PALETTE: the lossless stage's dictionary part (the role Section 3.7 gives Zstd on
+ *            few-valued states): the P <= 256 distinct truncated values, ascending as
+ *            unsigned 64-bit integers, 8 bytes each, padded to 16 bytes; then every value's
+ *            index in that list in k = max(1, ceil(log2 P)) bits, MSB first in 64-bit
+ *            little-endian words like the residual stream, padded to 16 bytes.  Header
+ *            byte 2 = k, coded values = N, bytes 12..15 = P (enabled by a mode mask).
  * XOR coding layout: the 2-bit codes, four per byte with the first code in the top
  * two bits, padded to 16 bytes; then the residual bit stream in 64-bit
  * little-endian words, first bit = bit 63 of word 0, padded to 16 bytes.
@@ -275,6 +283,45 @@ static void split_order(const uint64_t* t, int kc, uint64_t* u) {
   }
 }
 
+static int cmp_u64(const void* a, const void* b) {
+  const uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* The distinct values of t[0..N), ascending, into pal (room for ORC_PALETTE_MAX);
+ * returns how many there are, or ORC_PALETTE_MAX + 1 if there are more. */
+static int palette_of(const uint64_t* t, size_t N, uint64_t* pal) {
+  uint64_t* s = (uint64_t*)malloc(N * 8);
+  memcpy(s, t, N * 8);
+  qsort(s, N, 8, cmp_u64);
+  int P = 0;
+  for (size_t j = 0; j < N; ++j) {
+    if (j > 0 && s[j] == s[j - 1]) continue;
+    if (P == ORC_PALETTE_MAX) { free(s); return ORC_PALETTE_MAX + 1; }
+    pal[P++] = s[j];
+  }
+  free(s);
+  return P;
+}
+
+/* Index width of a palette of P entries: the smallest k >= 1 with 2^k >= P. */
+static int palette_bits(int P) {
+  int k = 1;
+  while ((1 << k) < P) ++k;
+  return k;
+}
+
+/* Position of v in pal[0..P) (v is in it). */
+static int palette_index(const uint64_t* pal, int P, uint64_t v) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) / 2;
+    if (pal[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 /* Size in bytes of the image in mode m, or 0 if m does not apply. */
 static size_t mode_size(int m, const uint64_t* t, int kc, int S, int period) {
   size_t N = (size_t)2 << kc;
@@ -301,6 +348,12 @@ static size_t mode_size(int m, const uint64_t* t, int kc, int S, int period) {
       free(u);
       return sz;
     }
+    case ORC_MODE_PALETTE: {
+      uint64_t pal[ORC_PALETTE_MAX];
+      int P = palette_of(t, N, pal);
+      if (P > ORC_PALETTE_MAX) return 0;
+      return 16 + pad16(8 * (size_t)P) + resid_area((uint64_t)N * (uint64_t)palette_bits(P));
+    }
   }
   return 0;
 }
@@ -314,7 +367,7 @@ int orc_mode_sizes(const uint64_t* x, int kc, int S_req, uint64_t* sizes_out) {
   uint64_t* t = (uint64_t*)malloc(N * 8);
   for (size_t j = 0; j < N; ++j) t[j] = orc_truncate(x[j], S);
   int period = find_period(t, kc);
-  for (int m = 0; m < ORC_NMODES; ++m) sizes_out[m] = mode_size(m, t, kc, S, period);  /* 6 entries */
+  for (int m = 0; m < ORC_NMODES; ++m) sizes_out[m] = mode_size(m, t, kc, S, period);  /* 7 entries */
   free(t);
   return ORC_OK;
 }
@@ -383,6 +436,21 @@ long orc_encode_chunk_mask(const uint64_t* x, int kc, int S_req, int force_mode,
       free(u);
       break;
     }
+    case ORC_MODE_PALETTE: {
+      uint64_t pal[ORC_PALETTE_MAX];
+      const int P = palette_of(t, N, pal), k = palette_bits(P);
+      const size_t pa = pad16(8 * (size_t)P), nwords = resid_area((uint64_t)N * (uint64_t)k) / 8;
+      for (int i = 0; i < P; ++i) put_u64(p + 8 * i, pal[i]);
+      uint64_t* w = (uint64_t*)calloc(nwords + 1, 8);
+      bitw b = {w, nwords, 0};
+      for (size_t j = 0; j < N; ++j) bw_put(&b, (uint64_t)palette_index(pal, P, t[j]), k);
+      for (size_t q = 0; q < nwords; ++q) put_u64(p + pa + 8 * q, w[q]);
+      free(w);
+      out[2] = (uint8_t)k;
+      nv = (uint32_t)N;
+      bits = (uint64_t)P;  /* bytes 12..15 hold the palette size */
+      break;
+    }
   }
   put_u32(out + 4, (uint32_t)(best - 16));
   put_u32(out + 8, nv);
@@ -427,6 +495,28 @@ int orc_decode_chunk(const uint8_t* img, size_t len, int kc, uint64_t* out) {
       if (lp != 0 || nv != N || bits != 0 || plen != 8 * N) return ORC_ERR_CORRUPT;
       for (size_t j = 0; j < N; ++j) out[j] = get_u64(p + 8 * j);
       return ORC_OK;
+    case ORC_MODE_PALETTE: {
+      /* lp = k, bits = P; the list strictly ascending, every index inside it */
+      const uint32_t P = bits;
+      if (nv != N || P < 1 || P > ORC_PALETTE_MAX || lp != palette_bits((int)P)) return ORC_ERR_CORRUPT;
+      const size_t pa = pad16(8 * (size_t)P), ia = resid_area((uint64_t)N * (uint64_t)lp);
+      if (pa + ia != plen) return ORC_ERR_CORRUPT;
+      uint64_t pal[ORC_PALETTE_MAX];
+      for (uint32_t i = 0; i < P; ++i) {
+        pal[i] = get_u64(p + 8 * i);
+        if (i > 0 && pal[i] <= pal[i - 1]) return ORC_ERR_CORRUPT;
+      }
+      uint64_t* w = (uint64_t*)calloc(ia / 8 + 1, 8);
+      for (size_t q = 0; q < ia / 8; ++q) w[q] = get_u64(p + pa + 8 * q);
+      int rc = ORC_OK;
+      for (size_t j = 0; j < N; ++j) {
+        const uint64_t ix = bw_get(w, (uint64_t)j * (uint64_t)lp, lp);
+        if (ix >= P) { rc = ORC_ERR_CORRUPT; break; }
+        out[j] = pal[ix];
+      }
+      free(w);
+      return rc;
+    }
     case ORC_MODE_SPLIT: {
       if (lp != 0 || nv != N) return ORC_ERR_CORRUPT;
       uint64_t* u = (uint64_t*)malloc(N * 8);

@@ -201,6 +201,9 @@ def _chunks(rng, kc):
     neg = rng.standard_normal(A) + 0j
     neg[::3] = -0.0
     yield "negzero", neg
+    # a few-valued state (the Grover diffusion's +-c pattern): PALETTE territory
+    lv = np.array([0.125, -0.125, 0.5, -0.0625])
+    yield "few", lv[rng.integers(0, 4, A)] + 1j * lv[rng.integers(0, 4, A)] * (rng.random(A) < 0.5)
 
 
 @pytest.mark.parametrize("kc", [0, 1, 2, 3, 5, 8, 10])
@@ -210,8 +213,11 @@ def test_roundtrip(kc):
         bits = np.ascontiguousarray(a, dtype=np.complex128).view(np.uint64)
         has_sub = np.any(((bits >> np.uint64(52)) & np.uint64(0x7FF) == 0) & (bits & np.uint64((1 << 52) - 1) != 0))
         for S in (64, 29, 26, 22, 19, 16):
-          for force in (-1, 5):
-            img = O.encode_chunk(a, kc, S, force_mode=force)
+          for force in (-1, 5, 6):
+            t = np_truncate(bits, 64 if has_sub else S)
+            if force == 6 and np.unique(t).size > 256:
+                continue
+            img = O.encode_chunk(a, kc, S, force_mode=force, modes=O.ALL_MODES)
             assert len(img) % 16 == 0
             eff = 64 if has_sub else S
             if img[0] != 0:
@@ -229,8 +235,19 @@ def _smallest_period(t: np.ndarray, kc: int):
     return None
 
 
-@pytest.mark.parametrize("kc", [1, 2, 4, 6])
-@pytest.mark.parametrize("modes", [O.DEFAULT_MODES, 0x3F])
+def _palette_size(t: np.ndarray):
+    """PALETTE image size from the format rule: header, the distinct values (8 bytes
+    each, padded to 16), then N indices of k = max(1, ceil(log2 P)) bits padded to 16
+    bytes; None above 256 distinct values."""
+    P = np.unique(t).size
+    if P > 256:
+        return None
+    k = max(1, (P - 1).bit_length())
+    return 16 + (8 * P + 15) // 16 * 16 + (t.size * k + 127) // 128 * 16
+
+
+@pytest.mark.parametrize("kc", [1, 2, 4, 6, 9])
+@pytest.mark.parametrize("modes", [O.DEFAULT_MODES, 0x3F, 0x7F])
 def test_selector_is_minimal_and_modes_apply(kc, modes):
     rng = np.random.default_rng(kc)
     for name, a in _chunks(rng, kc):
@@ -244,9 +261,10 @@ def test_selector_is_minimal_and_modes_apply(kc, modes):
                 3: True,
                 4: True,
                 5: True,
+                6: _palette_size(t) is not None,
             }
             sizes = {}
-            for m in range(6):
+            for m in range(7):
                 if not (modes >> m) & 1:
                     continue
                 if applicable[m]:
@@ -261,6 +279,8 @@ def test_selector_is_minimal_and_modes_apply(kc, modes):
             if applicable[2]:
                 assert O.encode_chunk(a, kc, S, force_mode=2)[2] == _smallest_period(t, kc)
             assert sizes[4] == 16 + 16 * (1 << kc)
+            if 6 in sizes:
+                assert sizes[6] == _palette_size(t)
 
 
 def test_subnormal_forces_full_width():
@@ -290,3 +310,38 @@ def test_corrupt_images_rejected():
             O.decode_chunk(bytes(bad), 6)
     with pytest.raises(O.OracleError):
         O.decode_chunk(bytes(img[:-16]), 6)
+
+
+def test_palette_index_width_and_limit():
+    """k = max(1, ceil(log2 P)) for P distinct values; above 256 the mode does not apply."""
+    for P, k in ((1, 1), (2, 1), (3, 2), (4, 2), (5, 3), (17, 5), (128, 7), (129, 8), (256, 8)):
+        vals = np.arange(1, P + 1, dtype=np.float64)
+        a = np.resize(vals, 512)  # 256 amplitudes, kc = 8: P distinct values
+        img = O.encode_chunk(a, 8, 64, force_mode=6, modes=O.ALL_MODES)
+        assert img[0] == 6 and img[2] == k and int.from_bytes(img[12:16], "little") == P
+        assert np.array_equal(O.decode_chunk(img, 8).view(np.float64), a)
+    with pytest.raises(O.OracleError):
+        O.encode_chunk(np.arange(1, 258, dtype=np.float64).tolist() + [0.0] * 255, 8, 64, force_mode=6)
+
+
+def test_palette_corrupt_images_rejected():
+    lv = np.array([0.5, -0.25, 0.125, 2.0, 3.0])
+    rng = np.random.default_rng(3)
+    a = lv[rng.integers(0, 5, 256)]
+    img = bytearray(O.encode_chunk(a, 7, 26, force_mode=6, modes=O.ALL_MODES))
+    assert img[0] == 6 and img[2] == 3
+    P = int.from_bytes(img[12:16], "little")
+    assert P == 5
+    bad = bytearray(img)
+    bad[16:24], bad[24:32] = img[24:32], img[16:24]  # palette no longer ascending
+    with pytest.raises(O.OracleError):
+        O.decode_chunk(bytes(bad), 7)
+    bad = bytearray(img)
+    bad[2] = 4  # wrong index width
+    with pytest.raises(O.OracleError):
+        O.decode_chunk(bytes(bad), 7)
+    bad = bytearray(img)
+    pa = (8 * P + 15) // 16 * 16
+    bad[16 + pa + 7] = 0xFF  # first index 0b111 = 7 >= P
+    with pytest.raises(O.OracleError):
+        O.decode_chunk(bytes(bad), 7)
