@@ -197,9 +197,12 @@ sim_status sim_set_option(sim_t* sim, const char* key, int64_t value);
 sim_status sim_set_block_cache(sim_t* sim, int on);
 
 /* Chunk modes the encoder chooses from for later gates (bit m = mode m).  The default
- * 0x1F is Solution C (Section 4.2) with its Zstd stand-in modes ZERO..RAW; 0x3F adds
- * SPLIT, Solution D (the real parts, then the imaginary parts, XOR-coded).  The set
- * must contain 0x1F. */
+ * 0x1F is Solution C (Section 4.2) with its Zstd stand-in modes ZERO..RAW; bit 5 adds
+ * SPLIT, Solution D (the real parts, then the imaginary parts, XOR-coded); bit 6 adds
+ * PALETTE (the lossless stage's dictionary part, Section 3.7: a chunk's at most 256
+ * distinct truncated values ascending, then one k-bit index per value,
+ * k = max(1, ceil(log2 P))).  The set must contain 0x1F.  With any extra mode every work
+ * item runs in the general gate kernel. */
 sim_status sim_set_modes(sim_t* sim, uint32_t modes);
 
 /* Learned selector (not from the paper).  selector 0: Solution C modes only (the
@@ -313,7 +316,10 @@ const char* sim_last_error(void);
  * 16-byte header [mode, S, log2 P, 0, payload bytes u32, coded values u32,
  * residual bits u32] then the payload (a multiple of 16 bytes); modes 0 ZERO,
  * 1 CONST, 2 PERIOD, 3 STREAM, 4 RAW (Section 4.2 Solution C for the coded streams;
- * the modes stand in for its Zstd stage), 5 SPLIT (Solution D).  The encoder truncates with
+ * the modes stand in for its Zstd stage), 5 SPLIT (Solution D), 6 PALETTE (header byte 2
+ * = index bits k, bytes 12..15 = palette size P; payload: the P values ascending as
+ * unsigned 64-bit integers, padded to 16 bytes, then the k-bit indices like a residual
+ * stream, padded to 16 bytes).  The encoder truncates with
  * S = 12 - EXP(eps) bits (eps = 0: 64 bits), forced to 64 for a chunk holding a
  * nonzero subnormal, and keeps the smallest image (ties: lower mode); force_mode
  * >= 0 selects a mode instead (SIM_ERR_INVALID if it does not apply).

@@ -23,9 +23,19 @@ constexpr int kPage = 512;
 constexpr int kCacheCap = 128;
 constexpr int kMaxKC = 11;
 
-enum : uint32_t { M_ZERO = 0, M_CONST = 1, M_PERIOD = 2, M_STREAM = 3, M_RAW = 4, M_SPLIT = 5, M_NMODES = 6 };
-// Solution C's modes; SPLIT (Solution D, re parts then im parts) only on request
+enum : uint32_t {
+  M_ZERO = 0, M_CONST = 1, M_PERIOD = 2, M_STREAM = 3, M_RAW = 4, M_SPLIT = 5, M_PALETTE = 6, M_NMODES = 7
+};
+// Solution C's modes; SPLIT (Solution D, re parts then im parts) and PALETTE (distinct
+// values plus k-bit indices) only on request
 constexpr uint32_t kDefaultModes = 0x1Fu;
+constexpr uint32_t kPaletteMax = 256;  // most distinct values a PALETTE image lists
+// Index width of a palette of P entries: the smallest k >= 1 with 2^k >= P.
+__host__ __device__ __forceinline__ uint32_t palette_bits(uint32_t P) {
+  uint32_t k = 1;
+  while ((1u << k) < P) ++k;
+  return k;
+}
 
 enum : uint32_t { E_OK = 0, E_OOM = 1, E_CORRUPT = 2, E_NONFINITE = 4, E_MODE = 8, E_TIMEOUT = 16 };
 
@@ -547,8 +557,27 @@ __device__ bool decode_block(const uint8_t* img, uint32_t img_bytes, int kc, uin
       case M_STREAM: ok = lp == 0 && nv == N; break;
       case M_RAW: ok = lp == 0 && nv == N && bits == 0 && plen == 8u * N; break;
       case M_SPLIT: ok = lp == 0 && nv == N; break;
+      case M_PALETTE:  // lp = k, bits = P
+        ok = nv == N && bits >= 1u && bits <= kPaletteMax && lp == palette_bits(bits) &&
+             plen == round16(8u * bits) + resid_bytes(N * lp);
+        break;
       default: ok = false;
     }
+  }
+  if (ok && mode == M_PALETTE) {
+    // the list strictly ascending, every index inside it
+    const uint32_t P = bits, k = lp;
+    const uint64_t* pal = reinterpret_cast<const uint64_t*>(payload);
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(payload + round16(8u * P));
+    bool good = true;
+    for (uint32_t i = threadIdx.x + 1u; i < P; i += kThreads) good &= pal[i] > pal[i - 1];
+    for (uint32_t j = threadIdx.x; j < N; j += kThreads) {
+      const uint32_t ix = (uint32_t)get_bits(w, j * k, k);
+      good &= ix < P;
+      tile[tile_val(j)] = ix < P ? pal[ix] : 0ull;
+    }
+    if (__syncthreads_and(good)) return true;
+    ok = false;
   }
   if (ok && mode == M_SPLIT) {
     if (S <= 32u ? decode_xor_block<VPT, true, true, true>(payload, plen, nv, S, bits, tile, s, pp)
@@ -901,6 +930,91 @@ __device__ __forceinline__ void pack_xor32(uint8_t* img, uint32_t nv, uint32_t j
   if (fill > 0u && cur) atomicOr(&m32[q ^ 1u], cur);
 }
 
+// PALETTE trial over a tile of N values (already truncated), using the payload area
+// `area` (at least 8 N bytes, nothing in it live) as scratch: the values are copied
+// there and sorted ascending (bitonic network), the distinct ones compacted to the
+// front.  Returns their number P if P <= kPaletteMax (the list stays at area[0, 8P)),
+// else 0.  All threads; barriers.
+template <int VPT>
+__device__ __forceinline__ uint32_t palette_block(const uint64_t* tile, uint32_t N, uint8_t* area, ScanSmem& s,
+                                                  int& pp) {
+  uint64_t* a = reinterpret_cast<uint64_t*>(area);
+  for (uint32_t j = threadIdx.x; j < N; j += kThreads) a[j] = tile[tile_val(j)];
+  __syncthreads();
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < N; i += kThreads) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const uint64_t x = a[i], y = a[l];
+          if ((x > y) == ((i & k) == 0u)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // distinct values: first of each run of equal ones; rank by a block scan
+  // thread t holds values [t VPT, t VPT + VPT) of the sorted list (VPT = N / kThreads,
+  // or 1 with fewer values than threads)
+  uint64_t v[VPT];
+  uint32_t first = 0u, cnt = 0u;
+  const uint32_t j0 = threadIdx.x * VPT;
+#pragma unroll
+  for (uint32_t q = 0; q < VPT; ++q) {
+    v[q] = 0ull;
+    if (j0 + q < N) {
+      v[q] = a[j0 + q];
+      if (j0 + q == 0u || v[q] != a[j0 + q - 1u]) {
+        first |= 1u << q;
+        ++cnt;
+      }
+    }
+  }
+  uint32_t total, fo, fa;
+  uint32_t r = block_scan(cnt, 0u, 0u, s, pp, &total, &fo, &fa);
+  if (total > kPaletteMax) {
+    __syncthreads();
+    return 0u;
+  }
+#pragma unroll
+  for (uint32_t q = 0; q < VPT; ++q)
+    if ((first >> q) & 1u) a[r++] = v[q];
+  __syncthreads();
+  return total;
+}
+
+// Writes the k-bit indices of a tile's N values into a PALETTE payload whose list of P
+// values is at pay[0, 8P) (the index stream follows at round16(8 P), MSB first in 64-bit
+// little-endian words, cleared here first).  All threads; one barrier.
+template <int VPT>
+__device__ __forceinline__ void palette_pack(const uint64_t* tile, uint32_t N, uint8_t* pay, uint32_t P) {
+  const uint64_t* pal = reinterpret_cast<const uint64_t*>(pay);
+  const uint32_t k = palette_bits(P);
+  uint32_t* m32 = reinterpret_cast<uint32_t*>(pay + round16(8u * P));
+  const uint32_t words = resid_bytes(N * k) / 4u;
+  for (uint32_t u = threadIdx.x; u < words; u += kThreads) m32[u] = 0u;
+  if (threadIdx.x == 0 && (P & 1u)) reinterpret_cast<uint64_t*>(pay)[P] = 0ull;  // the list's padding
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < N; j += kThreads) {
+    const uint64_t x = tile[tile_val(j)];
+    uint32_t lo = 0, hi = P - 1u;  // the value is in the list
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (pal[mid] < x) lo = mid + 1u;
+      else hi = mid;
+    }
+    // k bits at stream position j k: one or two 32-bit units (unit q is word q ^ 1)
+    const uint32_t pos = j * k, q = pos >> 5, off = pos & 31u;
+    const uint32_t f = lo << (32u - k);  // the index in the top k bits
+    atomicOr(&m32[q ^ 1u], f >> off);
+    if (off + k > 32u) atomicOr(&m32[(q + 1u) ^ 1u], f << (32u - off));
+  }
+  __syncthreads();
+}
+
 // Leading identical bytes of two high words (values whose low words are zero), capped at 3.
 __device__ __forceinline__ uint32_t xor_code32(uint32_t v, uint32_t prev) {
   return min((uint32_t)__clz((int)(v ^ prev)) >> 3, 3u);
@@ -1001,6 +1115,11 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
     o0 = block_scan(sum, nz ? 1u : 0u, (cst ? 1u : 0u) | (gtop ? 2u : 0u), s, pp, &total, &f_or, &f_and);
   const bool allzero = (f_or & 1u) == 0u;
   const bool allconst = (f_and & 1u) != 0u;
+  // PALETTE trial: the chunk's values sorted in the (still unused) payload area, the
+  // distinct ones kept in place ascending; the area is cleared again for the packers
+  uint32_t npal = 0;
+  const bool want_pal = force_mode == (int)M_PALETTE || (force_mode < 0 && ((modes >> M_PALETTE) & 1u));
+  if (want_pal) npal = palette_block<VPT>(tile, N, img + 16, s, pp);
   // 4. smallest power-of-two period P (amplitudes), 2 <= P < 2^kc: the chunk is
   //    P-periodic iff flipping any amplitude-index bit >= log2 P leaves it unchanged.
   //    The scan's flag compared one value per thread with its partner half a chunk
@@ -1045,6 +1164,7 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
   size[M_STREAM] = 16u + code_bytes(N) + resid_bytes(total);
   size[M_RAW] = 16u + 8u * N;
   size[M_SPLIT] = want_split ? 16u + code_bytes(N) + resid_bytes(total2) : 0u;
+  size[M_PALETTE] = npal ? 16u + round16(8u * npal) + resid_bytes(N * palette_bits(npal)) : 0u;
   uint32_t mode = 0, best = 0;
   if (force_mode >= 0) {
     if (force_mode >= (int)M_NMODES || size[force_mode] == 0 || size[force_mode] > img_cap) {
@@ -1070,6 +1190,7 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
   if (mode == M_STREAM) { nv = N; rbits = total; }
   if (mode == M_RAW) nv = N;
   if (mode == M_SPLIT) { nv = N; rbits = total2; }
+  if (mode == M_PALETTE) { nv = N; rbits = npal; }
   if (sel && sel->split_trials && threadIdx.x == 0 && want_split && force_mode < 0) atomicAdd(sel->split_trials, 1ull);
   // training record: the chunk's inputs, the exhaustive choice and both trial sizes
   if (sel && sel->trace && threadIdx.x == 0 && want_split) {
@@ -1086,13 +1207,26 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
   }
   if (threadIdx.x == 0) {
     uint32_t* h = reinterpret_cast<uint32_t*>(img);
-    h[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | ((mode == M_PERIOD ? (uint32_t)period : 0u) << 16);
+    const uint32_t b2 = mode == M_PERIOD ? (uint32_t)period : (mode == M_PALETTE ? palette_bits(npal) : 0u);
+    h[0] = mode | ((mode == M_ZERO ? 0u : S) << 8) | (b2 << 16);
     h[1] = best - 16u;
     h[2] = nv;
     h[3] = rbits;
   }
   uint64_t* pay64 = reinterpret_cast<uint64_t*>(img + 16);
-  if (mode == M_CONST) {
+  if (mode == M_PALETTE) {
+    // the list is in place; each value's index by binary search, packed k bits each
+    palette_pack<VPT>(tile, N, img + 16, npal);
+  } else if (want_pal) {
+    // another mode won: the sort scratch goes, the packers need a cleared payload
+    const uint32_t span = min(img_cap, max_coded_bytes(kc)) - 16u;
+    uint4* z = reinterpret_cast<uint4*>(img + 16);
+    for (uint32_t u = threadIdx.x; u < span / 16u; u += kThreads) z[u] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+  }
+  if (mode == M_PALETTE) {
+    // written above
+  } else if (mode == M_CONST) {
     if (threadIdx.x == 0) {
       pay64[0] = a0x;
       pay64[1] = a0y;

@@ -475,7 +475,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   // both chunks in one pass when neither needs the Solution D trial, the network or
   // 64-bit widths; otherwise (or if a chunk holds a subnormal) chunk by chunk
-  const bool enc_paired = paired && S <= 32u && L.selector != 2 && !L.trace && !((L.modes >> M_SPLIT) & 1u) &&
+  const bool enc_paired = paired && S <= 32u && L.selector != 2 && !L.trace && (L.modes >> M_SPLIT) == 0u &&
                           encode_pair32<VPT>(m.tile0, m.tile1, kc, S, L.modes, m.img0, m.img1, cap, *m.s, st.pp,
                                              &ctl->err, n0, n1);
   if (!enc_paired) {

@@ -199,7 +199,7 @@ class Sim:
         _check(lib().sim_apply_circuit(self._h, C.c_void_p(_ptr(g)), g.shape[0]), "sim_apply_circuit")
 
     def set_modes(self, modes: int) -> None:
-        """0x1F: Solution C modes (default); 0x3F adds SPLIT (Solution D)."""
+        """0x1F: Solution C modes (default); bit 5 adds SPLIT (Solution D), bit 6 PALETTE."""
         _check(lib().sim_set_modes(self._h, int(modes)), "sim_set_modes")
 
     def set_selector(self, selector: int, bf16_params=None) -> None:

@@ -52,7 +52,7 @@ def chunk_families(rng, kc, count):
     return out
 
 
-@pytest.mark.parametrize("modes", [0x1F, 0x3F])
+@pytest.mark.parametrize("modes", [0x1F, 0x3F, 0x5F, 0x7F])
 @pytest.mark.parametrize("kc", [0, 1, 2, 3, 5, 7, 8, 9, 10, 11])
 def test_encode_bytes_match_oracle(kc, modes):
     rng = np.random.default_rng(1000 + kc)
@@ -150,3 +150,32 @@ def test_nonfinite_input_rejected():
     with pytest.raises(qc().SimError) as ei:
         qc().codec_encode(a, 4, 1e-4)
     assert ei.value.code == qc().ERR_INVALID
+
+
+@pytest.mark.parametrize("kc", [0, 2, 6, 8, 10, 11])
+def test_palette_mode_forced_and_decoded_like_the_oracle(kc):
+    """PALETTE forced on few-valued chunks (the distinct-value count from 1 to 256, and
+    257, where it does not apply): the device's images are the oracle's byte for byte
+    and decode to the oracle's values."""
+    rng = np.random.default_rng(77 + kc)
+    A = 1 << kc
+    q = qc()
+    for P in (1, 2, 3, 5, 16, 100, 256, 257):
+        if P > 2 * A:
+            continue
+        lv = rng.standard_normal(P)
+        vals = np.resize(rng.permutation(lv), 2 * A)  # every one of the P values occurs
+        rng.shuffle(vals)
+        a = vals.view(np.complex128)
+        for eps in (0.0, 1e-4):
+            S = O.sig_bits(eps)
+            t = np.unique(vals.view(np.uint64) & np.uint64(~((1 << (64 - S)) - 1) & (2**64 - 1)))
+            if t.size > 256:
+                with pytest.raises(q.SimError):
+                    q.codec_encode(a, kc, eps, force_mode=6, modes=0x7F)
+                continue
+            imgs, _ = q.codec_encode(a, kc, eps, force_mode=6, modes=0x7F)
+            ref = O.encode_chunk(a, kc, S, force_mode=6, modes=0x7F)
+            assert imgs[0] == ref, (P, eps)
+            dec = q.codec_decode([ref], kc)
+            assert np.array_equal(dec.view(np.uint64), O.decode_chunk(ref, kc).view(np.uint64))

@@ -39,7 +39,7 @@ def stats_match(gs, os_):
     assert gs["level"] == os_["level"]
     assert gs["fidelity_lb_sum"] == pytest.approx(os_["fid_lb_sum"], abs=1e-12)
     assert gs["fidelity_lb_prod"] == pytest.approx(os_["fid_lb_prod"], rel=1e-12)
-    assert gs["chunks_by_mode"][:6] == os_["chunks_by_mode"][:6]
+    assert gs["chunks_by_mode"][:7] == os_["chunks_by_mode"][:7]
 
 
 @pytest.mark.parametrize("kc", [0, 1, 4, 7, 8, 9, 10, 11])
@@ -378,6 +378,30 @@ def _oracle_pair_check(gpu, gate, before_imgs, chunks, eps, kc):
         pass
     orc.apply(g2)
     return [orc.image(k) for k in range(len(chunks))]
+
+
+@pytest.mark.parametrize("modes", [0x5F, 0x7F])
+def test_palette_mode_bit_exact(modes):
+    """PALETTE (and with 0x7F also SPLIT) enabled on both sides: Grover's few-valued
+    states take PALETTE images in the lossless and the lossy stage; random-circuit and
+    QAOA states mostly do not.  Every image equals the oracle's."""
+    n = 12
+    grover, _ = Cc.grover(n, 4, seed=8)
+    rc = Cc.rcs(3, 4, 4, seed=9)
+    qa, _ = Cc.qaoa_maxcut(n, 1, 3, seed=10)
+    seen = set()
+    for circ, eps, kc in ((grover, 1e-4, 8), (grover, 0.0, 10), (rc, 1e-3, 7), (qa, 1e-4, 9)):
+        budget = (16 << n) // 5
+        orc = O.CSim(n, 10, kc, eps, budget, modes=modes)
+        gpu = qc().Sim(n, 10, eps, chunk_log2=kc, budget=budget, pool_bytes=64 << 20)
+        gpu.set_modes(modes)
+        for k in range(0, len(circ), 9):
+            gpu.apply_circuit(circ[k:k + 9])
+            orc.apply(circ[k:k + 9])
+            assert images_equal(gpu, orc) == [], k
+            seen |= {gpu.chunk_image(c)[0] for c in range(gpu.n_chunks)}
+        stats_match(gpu.stats(), orc.stats())
+    assert 6 in seen
 
 
 def test_full_size_30q_sampled_chunks():
