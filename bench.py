@@ -140,8 +140,11 @@ def per_class(gates: np.ndarray, tl: dict, n: int, kc: int, hbm: float | None) -
     return out
 
 
-# GB300 FP64 (vector pipe): 1.25 TFLOP/s nominal; a DFMA loop measured 1.2 TFLOP/s here.
+# GB300 FP64 (vector pipe): the nominal rate of the part; a DFMA-throughput loop on this
+# pool's GB300 (eight independent chains per thread, 1216 CTAs of 256 threads) measured
+# 6.27e11 fused multiply-adds per second = 1.255 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_SOURCE = "nominal GB300 FP64 (vector) rate; a DFMA-throughput loop measured 1.255 TFLOP/s"
 
 
 def peaks() -> dict:
@@ -214,6 +217,40 @@ def replica_seed(rank: int) -> int:
     return SEED + rank
 
 
+CFG2_DEPTH = 20  # the random-circuit configuration's depth: fidelity and the bound sweep are taken there
+
+
+def depth20_run(qcsim, torch, gates_d20: np.ndarray, n: int, eps: float, kc_req: int, sv_data_ptr: int | None,
+                no_fast: bool) -> dict:
+    """The depth-20 random circuit alone at bound eps (device-timed from |0...0>, the
+    lossless start included): rate, compression and fidelity against the uncompressed
+    state vector's device buffer."""
+    raw = 16 << n
+    stream = torch.cuda.Stream()
+    sim = qcsim.Sim(n, BLOCK_LOG2, eps, chunk_log2=kc_req, budget=raw // 4, pool_bytes=raw + raw // 8 + (64 << 20),
+                    stream=stream)
+    if no_fast:
+        sim.set_option("fast_path", 0)
+    kc = sim.chunk_log2
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.apply_circuit(gates_d20)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = sim.stats()
+    out = {"amp_updates_per_s": amp_updates(gates_d20, n, kc) / (ms * 1e-3), "seconds": ms * 1e-3,
+           "compression_ratio": st["ratio"], "min_compression_ratio": st["min_ratio"],
+           "fidelity_lb_sum": st["fidelity_lb_sum"], "eps_switch_gate": st["eps_switch_gate"]}
+    if sv_data_ptr is not None:
+        F = qcsim.C.c_double()
+        qcsim._check(qcsim.lib().sim_fidelity(sim._h, qcsim.C.c_void_p(sv_data_ptr), 1, qcsim.C.byref(F), None, None),
+                     "sim_fidelity")
+        out["fidelity"] = float(F.value)
+    sim.close()
+    return out
+
+
 def run_gpu(args) -> dict | None:
     import torch
 
@@ -229,9 +266,11 @@ def run_gpu(args) -> dict | None:
 
         dist.init_process_group("nccl")
     n = ROWS * COLS
-    depth = max(20, 1 + args.warmup + 2 * args.steps)
+    # the depth-20 circuit, then further layers of the same family for the timed steps
+    depth = CFG2_DEPTH + args.warmup + 2 * args.steps
     gates = Cc.rcs(ROWS, COLS, depth, seed=replica_seed(rank))
     layers = layers_of(gates, n, depth)
+    d20 = np.concatenate(layers[: 1 + CFG2_DEPTH])
     raw = 16 << n
     stream = torch.cuda.Stream()
     pool = raw + raw // 8 + (64 << 20)  # page rounding + per-CTA page caches
@@ -246,13 +285,31 @@ def run_gpu(args) -> dict | None:
         if dist is not None:
             dist.barrier()
 
-    # warm-up: the Hadamard layer and W circuit layers
-    sim.apply_circuit(layers[0])
-    for L in layers[1:1 + args.warmup]:
+    # the depth-20 circuit (untimed here) and its fidelity against the uncompressed
+    # complex128 state vector on the same GPU (same gates)
+    sim.apply_circuit(d20)
+    fid = sv_rate = None
+    sweep = {}
+    sv = None
+    if not args.no_sv:
+        sv = qcsim.StateVector(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sv.apply_circuit(d20)
+        torch.cuda.synchronize()
+        sv_rate = len(d20) * float(1 << n) / (time.perf_counter() - t0)
+        F = qcsim.C.c_double()
+        qcsim._check(qcsim.lib().sim_fidelity(sim._h, qcsim.C.c_void_p(sv.data_ptr()), 1, qcsim.C.byref(F), None, None),
+                     "sim_fidelity")
+        fid = float(F.value)
+    st_d20 = sim.stats()
+    # warm-up: W further layers
+    for L in layers[1 + CFG2_DEPTH: 1 + CFG2_DEPTH + args.warmup]:
         sim.apply_circuit(L)
     st0 = sim.stats()
     # timed region (device time, CUDA events on the simulator's stream)
-    timed = layers[1 + args.warmup: 1 + args.warmup + args.steps]
+    t_first = 1 + CFG2_DEPTH + args.warmup
+    timed = layers[t_first: t_first + args.steps]
     clocks = Clocks(local)
     sim.set_timing(2 if args.phases else 1)
     barrier()
@@ -273,7 +330,7 @@ def run_gpu(args) -> dict | None:
     updates = st1["amp_updates"] - st0["amp_updates"]
     assert updates == amp_updates(np.concatenate(timed), n, kc)
     # end to end through the public API: host gate records in, statistics read back
-    e2e_layers = layers[1 + args.warmup + args.steps: 1 + args.warmup + 2 * args.steps]
+    e2e_layers = layers[t_first + args.steps: t_first + 2 * args.steps]
     barrier()
     t0 = time.perf_counter()
     h2d = d2h = 0
@@ -286,22 +343,14 @@ def run_gpu(args) -> dict | None:
     e2e_s = time.perf_counter() - t0
     e2e_updates = amp_updates(np.concatenate(e2e_layers), n, kc)
     st2 = sim.stats()
-    # fidelity against the uncompressed complex128 state vector on the same GPU
-    applied = np.concatenate(layers[: 1 + args.warmup + 2 * args.steps])
-    fid = None
-    sv_rate = None
-    if not args.no_sv:
-        sv = qcsim.StateVector(n)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sv.apply_circuit(applied)
-        sv_s = time.perf_counter() - t0
-        sv_rate = len(applied) * float(1 << n) / sv_s
-        # the state vector's own device buffer is the reference of sim_fidelity
-        F = qcsim.C.c_double()
-        qcsim._check(qcsim.lib().sim_fidelity(sim._h, qcsim.C.c_void_p(sv.data_ptr()), 1, qcsim.C.byref(F), None, None),
-                     "sim_fidelity")
-        fid = float(F.value)
+    sim.close()
+    # the bound sweep of the configuration: the depth-20 circuit at 1e-5 and 1e-3 (and
+    # 1e-4 above), each from |0...0> with its fidelity against the same state vector
+    if not args.no_sweep:
+        for e in (1e-5, 1e-3):
+            sweep[f"{e:g}"] = depth20_run(qcsim, torch, d20, n, e, args.kc, sv.data_ptr() if sv is not None else None,
+                                          args.no_fast)
+    if sv is not None:
         sv.close()
     ms_max, upd_total = ms, updates
     if dist is not None:
@@ -309,6 +358,9 @@ def run_gpu(args) -> dict | None:
         dist.destroy_process_group()
     if rank != 0:
         return None
+    sweep["0.0001"] = {"fidelity": fid, "compression_ratio": st_d20["ratio"], "min_compression_ratio": st_d20["min_ratio"],
+                       "fidelity_lb_sum": st_d20["fidelity_lb_sum"], "eps_switch_gate": st_d20["eps_switch_gate"],
+                       "note": "the timed simulator itself at depth 20"}
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     kernel_ms_avg = tm["gate_kernel_ms"] / max(1, tm["launches"])
@@ -316,6 +368,7 @@ def run_gpu(args) -> dict | None:
     achieved = bytes_per_launch / (kernel_ms_avg * 1e-3) / 1e9 if kernel_ms_avg > 0 else 0.0
     traffic = (NCU_TRAFFIC["ratio_to_image_bytes"] * bytes_per_launch
                if NCU_TRAFFIC["source_sha"] == kernel_sha() else None)
+    flops = fp64_flops(np.concatenate(timed), n, kc)
     out = {
         "metric": METRIC,
         "value": upd_total / (ms_max * 1e-3),
@@ -330,8 +383,9 @@ def run_gpu(args) -> dict | None:
         "dtype": "f64",
         "data": "synthetic",
         "config": {
-            "workload": f"random circuit {ROWS}x{COLS} grid, {n} qubits, layers {1 + args.warmup}-{args.warmup + args.steps} "
-                        f"timed; eps {args.eps}; blocks 2^{BLOCK_LOG2}, chunks 2^{kc}",
+            "workload": f"random circuit {ROWS}x{COLS} grid, {n} qubits: the depth-{CFG2_DEPTH} circuit, then "
+                        f"{args.warmup} warm-up layers and layers {t_first}-{t_first + args.steps - 1} timed; "
+                        f"eps {args.eps}; blocks 2^{BLOCK_LOG2}, chunks 2^{kc}",
             "n_qubits": n, "block_log2": BLOCK_LOG2, "chunk_log2": kc, "eps": args.eps,
             "budget_bytes": raw // 4, "pool_bytes": pool, "gates_timed": int(sum(len(x) for x in timed)),
             "l2": "no flush: compressed state larger than L2",
@@ -340,10 +394,14 @@ def run_gpu(args) -> dict | None:
         "compression_ratio": st1["ratio"],
         "min_compression_ratio": st2["min_ratio"],
         "fidelity": fid,
-        "fidelity_lb_sum": st2["fidelity_lb_sum"],
-        "eps_switch_gate": st2["eps_switch_gate"],
+        "fidelity_depth": CFG2_DEPTH,
+        "fidelity_lb_sum": st_d20["fidelity_lb_sum"],
+        "eps_switch_gate": st_d20["eps_switch_gate"],
+        "eps_sweep_depth20": sweep,
         "encoded_gb": st1["encoded_bytes"] / 1e9,
-        "chunks_by_mode": st1["chunks_by_mode"][:5],
+        "chunks_by_mode": st1["chunks_by_mode"][:7],
+        "fast_items_timed": st1["fast_items"] - st0["fast_items"],
+        "fast_deferred_timed": st1["fast_deferred"] - st0["fast_deferred"],
         "uncompressed_value": sv_rate,
         "roofline": {
             "bound": "hbm",
@@ -352,23 +410,23 @@ def run_gpu(args) -> dict | None:
             "unit": "GB/s",
             "frac": (achieved / hbm) if hbm else None,
             "traffic": traffic,
-            "kernel": "k_gate",
+            "kernel": "k_gate_fast + k_gate (one gate's launches)",
             "kernel_ms_avg": kernel_ms_avg,
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else None,
         },
         "roofline_fp64": {
             "bound": "alu",
-            "achieved": fp64_flops(np.concatenate(timed), n, kc) / (tm["gate_kernel_ms"] * 1e-3) / 1e12,
+            "achieved": flops / (tm["gate_kernel_ms"] * 1e-3) / 1e12,
             "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
-            "frac": fp64_flops(np.concatenate(timed), n, kc) / (tm["gate_kernel_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-            "kernel": "k_gate",
-            "peak_source": "nominal GB300 FP64 (vector) rate; a DFMA loop measured 1.2 TFLOP/s",
-            "note": "the fused kernel's arithmetic ceiling: dense gates cost 28 flops per amplitude pair",
+            "frac": flops / (tm["gate_kernel_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "kernel": "k_gate_fast + k_gate",
+            "peak_source": FP64_PEAK_SOURCE,
+            "note": "the fused kernels' arithmetic ceiling: dense gates cost 28 flops per amplitude pair",
         },
         "roofline_by_class": per_class(np.concatenate(timed), tl, n, kc, hbm),
-        "gpu_launches": 2 * tm["launches"],
+        "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
         "phase_share": ({k: round(v / max(1, sum(st1["phase_cycles"])), 4) for k, v in
                          zip(("stage", "decode", "apply", "encode", "commit", "const"), st1["phase_cycles"])}
                         if args.phases else None),
@@ -445,10 +503,16 @@ def run_qaoa34(args) -> dict:
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     n, kc = 34, args.kc
-    pool = 180 * 10**9
+    # every byte the handle holds within 180 GB: the directory (one entry per chunk), the
+    # free-page stack and freed list (4 bytes per page each) and small bookkeeping come
+    # out of the 180 GB first, the page arena gets the rest
+    limit = 180 * 10**9
+    dir_bytes = (1 << (n - kc)) * (((16 + 4 * ((16 + (16 << kc) + 511) // 512)) + 15) // 16 * 16)
+    pool = int((limit - dir_bytes - (256 << 20)) / (1 + 8 / 512)) // 512 * 512
     gates, edges = Cc.qaoa_maxcut(n, 2, 3, seed=SEED)
     stream = torch.cuda.Stream()
     sim = qcsim.Sim(n, 20, args.eps, chunk_log2=kc, budget=pool, ladder=2, pool_bytes=pool, stream=stream)
+    assert sim.stats()["device_bytes"] <= limit, sim.stats()["device_bytes"]
     w = n + args.warmup
     sim.apply_circuit(gates[:w])
     st0 = sim.stats()
@@ -483,7 +547,8 @@ def run_qaoa34(args) -> dict:
             "warmup": args.warmup, "ms_per_step": ms / len(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"QAOA p=2 MaxCut, random 3-regular graph ({len(edges)} edges), {n} qubits, "
-                                   f"eps {args.eps} via the guarded ladder, page pool 180 GB; gates {w}-{len(gates) - 1} timed",
+                                   f"eps {args.eps} via the guarded ladder, all device memory of the simulator within "
+                                   f"180 GB (page arena {pool / 1e9:.1f} GB); gates {w}-{len(gates) - 1} timed",
                        "n_qubits": n, "chunk_log2": kc, "block_log2": 20, "gates": len(gates), "pool_bytes": pool,
                        "raw_bytes": 16 << n},
             "max_encoded_gb": st["max_encoded_bytes"] / 1e9, "peak_pages_gb": st["peak_pages_bytes"] / 1e9,
@@ -620,23 +685,52 @@ def _oracle_sample(job: tuple) -> tuple[int, float, int]:
     return upd, time.perf_counter() - t0, k
 
 
+def _oracle_cfg2_gate(job: tuple) -> tuple[int, float]:
+    """The oracle on the random-circuit configuration's own 30-qubit circuit: its first
+    gate on |0...0>, a whole-state pass like every later gate.  Returns (amplitude
+    updates, seconds)."""
+    eps, seed, rows, cols = job
+    import oracle as O
+
+    n = rows * cols
+    gates = Cc.rcs(rows, cols, 1, seed=seed)
+    cs = O.CSim(n, BLOCK_LOG2, CHUNK_LOG2, eps, (16 << n) // 4)
+    t0 = time.perf_counter()
+    cs.apply(gates[:1])
+    dt = time.perf_counter() - t0
+    upd = amp_updates(gates[:1], n, CHUNK_LOG2)
+    cs.close()
+    return upd, dt
+
+
 def cpu_sample(eps: float, warm_layers: int = 3, timed_layers: int = 2, budget_s: float = 20.0) -> dict:
-    """The oracle on the host cores: one single-threaded run, then one run per core at
-    once (processes started with spawn, each on its own seeded circuit of the same
-    family); value = all runs' updates / the slowest run's time."""
+    """The oracle on the host cores.  The baseline proper is the configuration's own
+    circuit: one process per core at once (started with spawn), each applying the first
+    gate of the 30-qubit circuit (a whole-state pass, about 45 s of one core); value =
+    all processes' updates / the slowest one's time.  The first 50 gates of that circuit
+    would take about 50 times one gate's time on each core.  Beside it, the 20-qubit
+    sample of the same family (whole layers after a warm-up, one circuit seed per core)."""
     import multiprocessing as mp
 
-    u1, s1, k1 = _oracle_sample((eps, SEED, warm_layers, timed_layers, budget_s))
     cores = host_cores()
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_sample, [(eps, SEED + c, warm_layers, timed_layers, budget_s) for c in range(cores)])
+        res = pool.map(_oracle_cfg2_gate, [(eps, SEED, ROWS, COLS)] * cores)
     upd = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
+    u1, s1, _ = _oracle_sample((eps, SEED, warm_layers, timed_layers, budget_s))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res20 = pool.map(_oracle_sample, [(eps, SEED + c, warm_layers, timed_layers, budget_s) for c in range(cores)])
+    n = ROWS * COLS
     return {"value": upd / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"CPU oracle, random circuit 4x5 grid (20 qubits), eps {eps}, budget raw/4, "
-                      f"{timed_layers} layers after the Hadamard layer + {warm_layers} warm-up layers, "
-                      f"{cores} single-threaded processes at once (one circuit seed each)",
-            "single_core_value": u1 / s1, "seconds": wall}
+            "sample": f"CPU oracle on the {ROWS}x{COLS} random circuit ({n} qubits), eps {eps}: its first gate (a "
+                      f"whole-state pass of 2^{n} amplitudes) applied by {cores} single-threaded processes at once; "
+                      f"the first 50 gates extrapolate to 50 x {wall:.1f} s per core",
+            "seconds": wall, "single_core_value": res[0][0] / min(r[1] for r in res),
+            "stand_in_20q": {"value": sum(r[0] for r in res20) / max(r[1] for r in res20), "cores": cores,
+                             "single_core_value": u1 / s1,
+                             "sample": f"CPU oracle, random circuit 4x5 grid (20 qubits), eps {eps}, budget raw/4, "
+                                       f"{timed_layers} layers after the Hadamard layer + {warm_layers} warm-up layers, "
+                                       f"one circuit seed per process"}}
 
 
 def host_cores() -> int:
@@ -701,6 +795,7 @@ def main():
     ap.add_argument("--cols", type=int, default=6)
     ap.add_argument("--kc", type=int, default=CHUNK_LOG2, help="chunk_log2 (amplitudes per coded chunk = 2^kc)")
     ap.add_argument("--no-fast", action="store_true", help="every work item through the general gate kernel")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the depth-20 runs at 1e-5 and 1e-3")
     args = ap.parse_args()
     global ROWS, COLS, BLOCK_LOG2
     ROWS, COLS = args.rows, args.cols
