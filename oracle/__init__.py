@@ -101,9 +101,8 @@ def lib():
             "orc_csim_set_modes": (C.c_int, [C.c_void_p, C.c_uint]),
             "orc_csim_set_mlp": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float)]),
             "orc_mlp_forward": (None, [C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
-            "orc_mlp_wants_split": (C.c_int, [C.POINTER(C.c_float), C.POINTER(C.c_float)]),
-            "orc_mlp_features": (None, [u8p, C.c_size_t, C.c_int, C.POINTER(_Gate), C.c_int, C.POINTER(C.c_uint64),
-                                     C.POINTER(C.c_float)]),
+            "orc_mlp_trials": (C.c_int, [C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+            "orc_mlp_features": (None, [u8p, C.c_size_t, C.c_int, C.POINTER(_Gate), C.c_int, C.POINTER(C.c_float)]),
             "orc_decode_chunk": (C.c_int, [u8p, C.c_size_t, C.c_int, u64p]),
             "orc_gate_check": (C.c_int, [C.POINTER(_Gate), C.c_int]),
             "orc_sv_init": (None, [dp, C.c_int]),
@@ -262,22 +261,20 @@ def mlp_forward_c(params_flat, x) -> np.ndarray:
     return out
 
 
-def mlp_wants_split_c(params_flat, x) -> bool:
-    """The C oracle's selector decision on one feature row."""
+def mlp_trials_c(params_flat, x) -> int:
+    """The C oracle's selector decision on one feature row: bit 0 the SPLIT trial,
+    bit 1 the PALETTE trial."""
     v = np.ascontiguousarray(params_flat, dtype=np.float32)
     xx = np.ascontiguousarray(x, dtype=np.float32)
-    return bool(lib().orc_mlp_wants_split(_ptr(v, C.c_float), _ptr(xx, C.c_float)))
+    return int(lib().orc_mlp_trials(_ptr(v, C.c_float), _ptr(xx, C.c_float)))
 
 
-def mlp_features_c(img: bytes, kc: int, gate_rec, S_gate: int, values) -> np.ndarray:
-    """The C oracle's selector inputs for a chunk with image img whose values after
-    the gate are `values` (2^kc complex128)."""
+def mlp_features_c(img: bytes, kc: int, gate_rec, S_gate: int) -> np.ndarray:
+    """The C oracle's selector inputs for a chunk whose current image is img, about to
+    be rewritten by the gate (no decoded value is needed)."""
     buf = np.frombuffer(bytes(img), dtype=np.uint8).copy()
-    x = _as_bits(values)
-    assert x.size == 2 << kc
     out = np.zeros(16, dtype=np.float32)
-    lib().orc_mlp_features(_ptr(buf, C.c_uint8), buf.size, kc, _gates(gate_rec), S_gate, _ptr(x, C.c_uint64),
-                           _ptr(out, C.c_float))
+    lib().orc_mlp_features(_ptr(buf, C.c_uint8), buf.size, kc, _gates(gate_rec), S_gate, _ptr(out, C.c_float))
     return out
 
 

@@ -1,15 +1,16 @@
 """Oracle of the learned chunk-mode selector -- TEST INFRASTRUCTURE ONLY.
 
-The network is not from the paper: it predicts, for each chunk a gate re-encodes,
-whether the Solution D order (SPLIT, Section 4.2) is worth a trial encode, so the
-exhaustive trial of Solution C and D can be replaced by one trial most of the time.
-The codec itself enforces the error bound; the network only picks among lossless
-re-orderings of the same truncated values.
+The network is not from the paper: for each chunk a gate is about to rewrite it
+predicts the best chunk mode and a bit budget (the best image's size as a fraction of
+the RAW size), from the chunk's current image header and the gate alone, so that the
+trial encodes of SPLIT (Solution D, Section 4.2) and PALETTE run only where they may
+pay.  The exhaustive trial of every mode stays the fallback and the judge of the
+network's choices; the codec itself enforces the error bound, the network only picks
+among lossless codings of the same truncated values.
 
-Architecture: 16 inputs -> 32 (ReLU) -> 32 (ReLU) -> 8 outputs.  Outputs 0..5 are
-logits over the chunk modes ZERO, CONST, PERIOD, STREAM, RAW, SPLIT; outputs 6 and 7
-predict the STREAM and SPLIT image sizes as fractions of the RAW size.  Weights are
-bfloat16 values.
+Architecture: 16 inputs -> 32 (ReLU) -> 32 (ReLU) -> 8 outputs.  Outputs 0..6 are
+logits over the chunk modes ZERO, CONST, PERIOD, STREAM, RAW, SPLIT, PALETTE; output 7
+is the bit budget.  Weights are bfloat16 values.
 
 Inference (what the simulator's decision depends on) is defined in float32 with a
 fixed order: every unit sums its products over the inputs in index order, each
@@ -20,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_H, N_OUT, N_MODES = 16, 32, 8, 6
+N_IN, N_H, N_OUT, N_MODES = 16, 32, 8, 7
 SHAPES = {"W1": (N_H, N_IN), "b1": (N_H,), "W2": (N_H, N_H), "b2": (N_H,), "W3": (N_OUT, N_H), "b3": (N_OUT,)}
 ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
 
@@ -82,23 +83,30 @@ def forward32(p: dict, x) -> np.ndarray:
     return _layer32(p["W3"], p["b3"], h2)
 
 
-SPLIT_MARGIN = np.float32(2.0)
+TRIAL_MARGIN = np.float32(2.0)
 
 
-def wants_split(p: dict, x) -> np.ndarray:
-    """The selector's decision: run the Solution D trial iff the SPLIT logit plus a
-    margin of 2 reaches the largest mode logit (float32 sum and comparison).  The
-    margin leans towards a trial: a missed SPLIT costs memory, a needless trial only
-    time."""
+def trials(p: dict, x) -> np.ndarray:
+    """The selector's decision per row: bit 0 runs the SPLIT trial, bit 1 the PALETTE
+    trial; each iff that mode's logit plus a margin of 2 reaches the largest of the
+    seven logits and the bit budget (output 7) is below the chunk's current size
+    fraction (input 7) -- float32 sums and comparisons.  The margin leans towards a
+    trial (a missed one costs memory, a needless one only time); the budget drops
+    trials where no smaller image is expected."""
+    x = np.asarray(x, dtype=np.float32)
     out = forward32(p, x)
-    lifted = (out[:, 5] + SPLIT_MARGIN).astype(np.float32)
-    return lifted >= out[:, :N_MODES].max(axis=1)
+    mx = out[:, :N_MODES].max(axis=1)
+    smaller = out[:, 7] < x[:, 7]
+    split = ((out[:, 5] + TRIAL_MARGIN).astype(np.float32) >= mx) & smaller
+    pal = ((out[:, 6] + TRIAL_MARGIN).astype(np.float32) >= mx) & smaller
+    return split.astype(np.int64) | (pal.astype(np.int64) << 1)
 
 
 def loss_and_grads(p: dict, x, mode, sizes, w_size: float = 1.0):
-    """Mean over the rows of: softmax cross-entropy of the mode logits against the best
-    mode, plus w_size * squared error of outputs 6, 7 against the two size fractions.
-    float64 throughout; returns (loss, grads dict)."""
+    """Mean over the rows of: softmax cross-entropy of the seven mode logits against
+    the best mode, plus w_size * squared error of the bit budget (output 7) against the
+    best image's size fraction (`sizes`, one per row).  float64 throughout; returns
+    (loss, grads dict)."""
     x = np.asarray(x, dtype=np.float64)
     B = x.shape[0]
     W1, b1 = p["W1"].astype(np.float64), p["b1"].astype(np.float64)
@@ -116,7 +124,7 @@ def loss_and_grads(p: dict, x, mode, sizes, w_size: float = 1.0):
     y = np.zeros_like(sm)
     y[np.arange(B), np.asarray(mode, dtype=np.int64)] = 1.0
     ce = -np.sum(y * np.log(sm + 1e-300)) / B
-    diff = o[:, N_MODES:] - np.asarray(sizes, dtype=np.float64)
+    diff = o[:, N_MODES:] - np.asarray(sizes, dtype=np.float64).reshape(B, N_OUT - N_MODES)
     mse = w_size * np.sum(diff * diff) / B
     do = np.zeros_like(o)
     do[:, :N_MODES] = (sm - y) / B
@@ -138,40 +146,26 @@ def loss_only(p: dict, x, mode, sizes, w_size: float = 1.0) -> float:
     return loss_and_grads(p, x, mode, sizes, w_size)[0]
 
 
-def zero_groups(values, kc: int) -> tuple[int, int, int]:
-    """Splits the chunk's 2^kc amplitudes into G = min(2^kc, 256) equal groups and
-    counts the groups whose real parts, and those whose imaginary parts, are all zero
-    (+0 or -0).  Returns (real-zero groups, imaginary-zero groups, G)."""
-    v = np.ascontiguousarray(values, dtype=np.complex128)
-    A = 1 << kc
-    G = min(A, 256)
-    re = v.real.reshape(G, A // G)
-    im = v.imag.reshape(G, A // G)
-    return int(np.sum(np.all(re == 0, axis=1))), int(np.sum(np.all(im == 0, axis=1))), G
-
-
-def features(prev_image: bytes, kc: int, u, target: int, S_gate: int, values) -> np.ndarray:
-    """The selector's 16 inputs for one chunk about to be re-encoded (float32):
-    one-hot of the previous image's mode (6), its size / RAW size, its S / 64, its
-    residual bits / (64 N), whether the gate matrix is real, diagonal, a permutation,
-    whether the target lies inside the chunk, the fraction of amplitude groups whose
-    real parts are all zero, the gate's S / 64, and the fraction of groups whose
-    imaginary parts are all zero.  `values` are the chunk's amplitudes after the gate."""
+def features(image: bytes, kc: int, u, target: int, S_gate: int) -> np.ndarray:
+    """The selector's 16 inputs (float32) for a chunk whose current image is `image`,
+    about to be rewritten by the gate (matrix u, target) at S_gate bits: one-hot of the
+    image mode (7), its size / RAW size, its S / 64, header word 3 / (64 N) (residual
+    bits; the palette size for PALETTE), header byte 2 / 16, whether the gate matrix is
+    real, diagonal, anti-diagonal, whether the target lies inside the chunk, S_gate / 64."""
     f32 = np.float32
-    mode, S = prev_image[0], prev_image[1]
-    bits = int.from_bytes(prev_image[12:16], "little")
-    zre, zim, G = zero_groups(values, kc)
+    mode, S, b2 = image[0], image[1], image[2]
+    w3 = int.from_bytes(image[12:16], "little")
     x = np.zeros(16, dtype=np.float32)
-    x[mode] = 1
-    x[6] = f32(len(prev_image)) / f32(16 + (16 << kc))
-    x[7] = f32(S) / f32(64)
-    x[8] = f32(bits) / f32(64 * (2 << kc))
+    if mode < 7:
+        x[mode] = 1
+    x[7] = f32(len(image)) / f32(16 + (16 << kc))
+    x[8] = f32(S) / f32(64)
+    x[9] = f32(w3) / f32(64 * (2 << kc))
+    x[10] = f32(b2) / f32(16)
     u = [float(v) for v in u]
-    x[9] = float(u[1] == 0 and u[3] == 0 and u[5] == 0 and u[7] == 0)
-    x[10] = float(u[2] == 0 and u[3] == 0 and u[4] == 0 and u[5] == 0)
-    x[11] = float(u[0] == 0 and u[1] == 0 and u[6] == 0 and u[7] == 0)
-    x[12] = float(target < kc)
-    x[13] = f32(zre) / f32(G)
-    x[14] = f32(S_gate) / f32(64)
-    x[15] = f32(zim) / f32(G)
+    x[11] = float(u[1] == 0 and u[3] == 0 and u[5] == 0 and u[7] == 0)
+    x[12] = float(u[2] == 0 and u[3] == 0 and u[4] == 0 and u[5] == 0)
+    x[13] = float(u[0] == 0 and u[1] == 0 and u[6] == 0 and u[7] == 0)
+    x[14] = float(target < kc)
+    x[15] = f32(S_gate) / f32(64)
     return x

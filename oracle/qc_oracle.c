@@ -681,7 +681,7 @@ int orc_sv_measure(const double* psi, int n, uint64_t seed, uint64_t* outcome, d
 }
 
 /* ------------------------------------------------------------------------- */
-/* 9. Learned selector (not from the paper): when to try Solution D          */
+/* 9. Learned selector (not from the paper): which trial encodes to run       */
 /* ------------------------------------------------------------------------- */
 /* 16 -> 32 (ReLU) -> 32 (ReLU) -> 8, parameters W1[32][16] b1[32] W2[32][32] b2[32]
  * W3[8][32] b3[8] (bfloat16 values held as float).  float32, every unit summing its
@@ -711,60 +711,57 @@ void orc_mlp_forward(const float* prm, const float* x, float* out) {
   for (int j = 0; j < 8; ++j) out[j] = mlp_unit(W3 + 32 * j, h2, 32, b3[j]);
 }
 
-/* Decision: try Solution D iff the SPLIT logit, plus a margin of 2, reaches the largest
- * of the six mode logits (float32 sum and comparison).  The margin makes the rule
- * lean towards a trial: a missed SPLIT costs memory, a needless trial only time. */
-int orc_mlp_wants_split(const float* prm, const float* x) {
+/* Outputs 0..6: logits of the chunk modes ZERO, CONST, PERIOD, STREAM, RAW, SPLIT,
+ * PALETTE; output 7: the bit budget, the predicted size of the chunk's best image as a
+ * fraction of the RAW size.  Decision: the SPLIT (bit 0) and PALETTE (bit 1) trials
+ * each run iff that mode's logit plus a margin of 2 reaches the largest of the seven
+ * logits and the budget is below the chunk's current image size (input 7); float32
+ * sums and comparisons.  The margin leans towards a trial (a missed trial costs memory,
+ * a needless one only time); the budget drops trials where no smaller image is
+ * expected.  The cheap modes are always computed; the codec keeps the bound. */
+int orc_mlp_trials(const float* prm, const float* x) {
   float out[8];
   orc_mlp_forward(prm, x, out);
   float mx = out[0];
-  for (int m = 1; m < 6; ++m)
+  for (int m = 1; m < 7; ++m)
     if (out[m] > mx) mx = out[m];
-  float lifted = out[5] + 2.0f;
-  return lifted >= mx;
+  const int smaller = out[7] < x[7];
+  int t = 0;
+  if (out[5] + 2.0f >= mx && smaller) t |= 1;
+  if (out[6] + 2.0f >= mx && smaller) t |= 2;
+  return t;
 }
 
-/* Counts, over the chunk's amplitudes split into G = min(2^kc, 256) equal groups, the
- * groups whose real parts (*zre) and whose imaginary parts (*zim) are all zero (+0 or
- * -0); vals = the chunk's 2^(kc+1) words as the gate left them. */
-static void zero_groups(const uint64_t* vals, int kc, uint32_t* zre, uint32_t* zim, uint32_t* G) {
-  const uint64_t A = (uint64_t)1 << kc;
-  const uint64_t ng = A < 256 ? A : 256, gs = A / ng;
-  uint32_t cr = 0, ci = 0;
-  for (uint64_t k = 0; k < ng; ++k) {
-    int re_nz = 0, im_nz = 0;
-    for (uint64_t a = k * gs; a < (k + 1) * gs; ++a) {
-      re_nz |= (vals[2 * a] << 1) != 0;
-      im_nz |= (vals[2 * a + 1] << 1) != 0;
-    }
-    cr += !re_nz;
-    ci += !im_nz;
-  }
-  *zre = cr;
-  *zim = ci;
-  *G = (uint32_t)ng;
-}
-
-/* The selector's inputs for a chunk whose current image is img (length len) and whose
- * values after the gate are vals. */
-void orc_mlp_features(const uint8_t* img, size_t len, int kc, const orc_gate* g, int S_gate, const uint64_t* vals,
-                      float* x) {
-  uint32_t bits = (uint32_t)img[12] | ((uint32_t)img[13] << 8) | ((uint32_t)img[14] << 16) | ((uint32_t)img[15] << 24);
+/* The selector's 16 inputs for a chunk about to be rewritten by gate g, from its current
+ * image (img, len bytes) and the gate alone (no decoded value), so that the decisions
+ * of a whole gate can be taken before it runs: one-hot of the image mode (7), its
+ * size / RAW size, its S / 64, header word 3 / (64 N) (residual bits; the palette size
+ * for PALETTE), header byte 2 / 16 (log2 period, palette index width), whether the gate
+ * matrix is real, diagonal, anti-diagonal, whether the target lies inside the chunk, and
+ * the gate's S / 64. */
+void orc_mlp_features(const uint8_t* img, size_t len, int kc, const orc_gate* g, int S_gate, float* x) {
+  uint32_t w3 = (uint32_t)img[12] | ((uint32_t)img[13] << 8) | ((uint32_t)img[14] << 16) | ((uint32_t)img[15] << 24);
   const double* u = g->u;
-  uint32_t zre, zim, G;
-  zero_groups(vals, kc, &zre, &zim, &G);
   for (int m = 0; m < 16; ++m) x[m] = 0.0f;
-  if (img[0] < 6) x[img[0]] = 1.0f;
-  x[6] = (float)len / (float)(16 + (16 << kc));
-  x[7] = (float)img[1] / 64.0f;
-  x[8] = (float)bits / (float)(64 * (2 << kc));
-  x[9] = (u[1] == 0 && u[3] == 0 && u[5] == 0 && u[7] == 0) ? 1.0f : 0.0f;
-  x[10] = (u[2] == 0 && u[3] == 0 && u[4] == 0 && u[5] == 0) ? 1.0f : 0.0f;
-  x[11] = (u[0] == 0 && u[1] == 0 && u[6] == 0 && u[7] == 0) ? 1.0f : 0.0f;
-  x[12] = g->target < kc ? 1.0f : 0.0f;
-  x[13] = (float)zre / (float)G;
-  x[14] = (float)S_gate / 64.0f;
-  x[15] = (float)zim / (float)G;
+  if (img[0] < 7) x[img[0]] = 1.0f;
+  x[7] = (float)len / (float)(16 + (16 << kc));
+  x[8] = (float)img[1] / 64.0f;
+  x[9] = (float)w3 / (float)(64 * (2 << kc));
+  x[10] = (float)img[2] / 16.0f;
+  x[11] = (u[1] == 0 && u[3] == 0 && u[5] == 0 && u[7] == 0) ? 1.0f : 0.0f;
+  x[12] = (u[2] == 0 && u[3] == 0 && u[4] == 0 && u[5] == 0) ? 1.0f : 0.0f;
+  x[13] = (u[0] == 0 && u[1] == 0 && u[6] == 0 && u[7] == 0) ? 1.0f : 0.0f;
+  x[14] = g->target < kc ? 1.0f : 0.0f;
+  x[15] = (float)S_gate / 64.0f;
+}
+
+/* The mode set a chunk is encoded with under the selector: Solution C's modes plus
+ * the trials it grants. */
+static unsigned mlp_mask(const float* prm, const uint8_t* img, size_t len, int kc, const orc_gate* g, int S_gate) {
+  float x[16];
+  orc_mlp_features(img, len, kc, g, S_gate, x);
+  const int t = orc_mlp_trials(prm, x);
+  return ORC_DEFAULT_MODES | ((t & 1) ? (1u << ORC_MODE_SPLIT) : 0u) | ((t & 2) ? (1u << ORC_MODE_PALETTE) : 0u);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -781,7 +778,7 @@ typedef struct {
 typedef struct {
   int n, b, kc, ladder, S_cur, level, nlevels;
   unsigned modes;
-  int use_mlp;                    /* 1: Solution D tried only where the selector says so */
+  int use_mlp;                    /* 1: SPLIT / PALETTE tried only where the selector says so */
   float mlp[ORC_MLP_NPARAMS];
   double levels[8];
   double eps_max, tau;
@@ -918,7 +915,6 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
   uint64_t* x0 = (uint64_t*)malloc(N * 8);
   uint64_t* x1 = (uint64_t*)malloc(N * 8);
   unsigned m0 = s->modes, m1 = s->modes;
-  float feat[16];
   for (uint64_t q = 0; q < s->nchunks && rc == ORC_OK; ++q) {
     if ((q & hi_mask) != hi_vals) continue;
     if (t < kc) {
@@ -930,10 +926,7 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
         if ((i & lo_mask) != lo_vals) continue;
         apply_pair(g->u, d + 2 * i, d + 2 * (i | ((size_t)1 << t)));
       }
-      if (s->use_mlp) {
-        orc_mlp_features(s->img[q], s->len[q], kc, g, s->S_cur, x0, feat);
-        m0 = orc_mlp_wants_split(s->mlp, feat) ? 0x3Fu : ORC_DEFAULT_MODES;
-      }
+      if (s->use_mlp) m0 = mlp_mask(s->mlp, s->img[q], s->len[q], kc, g, s->S_cur);
       rc = csim_store(s, q, x0, m0);
     } else {
       uint64_t qb = (uint64_t)1 << (t - kc);
@@ -948,10 +941,8 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
         apply_pair(g->u, d0 + 2 * i, d1 + 2 * i);
       }
       if (s->use_mlp) {
-        orc_mlp_features(s->img[q], s->len[q], kc, g, s->S_cur, x0, feat);
-        m0 = orc_mlp_wants_split(s->mlp, feat) ? 0x3Fu : ORC_DEFAULT_MODES;
-        orc_mlp_features(s->img[q1], s->len[q1], kc, g, s->S_cur, x1, feat);
-        m1 = orc_mlp_wants_split(s->mlp, feat) ? 0x3Fu : ORC_DEFAULT_MODES;
+        m0 = mlp_mask(s->mlp, s->img[q], s->len[q], kc, g, s->S_cur);
+        m1 = mlp_mask(s->mlp, s->img[q1], s->len[q1], kc, g, s->S_cur);
       }
       rc = csim_store(s, q, x0, m0);
       if (!rc) rc = csim_store(s, q1, x1, m1);

@@ -50,7 +50,7 @@ def test_backward_matches_finite_differences():
         p[k] = rng.standard_normal(M.SHAPES[k]) * 0.1
     x = rng.standard_normal((32, M.N_IN))
     mode = rng.integers(0, M.N_MODES, size=32)
-    sizes = rng.random((32, 2))
+    sizes = rng.random((32, 1))
     _, g = M.loss_and_grads(p, x, mode, sizes)
     h = 1e-6
     for k in M.ORDER:
@@ -70,8 +70,8 @@ def test_plain_gradient_descent_reduces_the_loss():
     rng = np.random.default_rng(6)
     p = {k: v.astype(np.float64) for k, v in M.init_params(7).items()}
     x = rng.standard_normal((256, M.N_IN))
-    mode = np.where(x[:, 0] > 0, 5, 3)  # a separable rule
-    sizes = np.stack([0.4 + 0.1 * np.tanh(x[:, 1]), 0.3 + 0.1 * np.tanh(x[:, 2])], axis=1)
+    mode = np.where(x[:, 0] > 0, 6, 3)  # a separable rule
+    sizes = (0.4 + 0.1 * np.tanh(x[:, 1]))[:, None]
     l0, _ = M.loss_and_grads(p, x, mode, sizes)
     for _ in range(300):
         _, g = M.loss_and_grads(p, x, mode, sizes)
@@ -96,38 +96,30 @@ def test_c_inference_equals_numpy_definition_bit_for_bit():
         assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
-def test_decision_rule_margin_edges():
-    """Output layer weights zero: the logits are the biases b3, so the rule can be
-    checked at its edges (SPLIT logit exactly 2 below the top one is a trial, and so is
-    one whose float32 sum with 2 rounds up to the top; one float32 step of the sum
-    below is not); C and numpy agree."""
+def test_decision_rule_margin_and_budget_edges():
+    """Output layer weights zero: the logits and the budget are the biases b3, so the
+    rule can be checked at its edges.  A trial mode's logit exactly 2 below the top one
+    is a trial, and so is one whose float32 sum with 2 rounds up to the top; one float32
+    step of the sum below is not.  The budget must be below the current size fraction
+    (input 7): equal is not below.  C and numpy agree."""
     import oracle as O
 
-    x = np.zeros((1, M.N_IN), dtype=np.float32)
     below1 = np.nextafter(np.float32(1), np.float32(0))  # 1 - 2^-24: + 2 rounds back to 3 in float32
-    cases = [([0, 0, 0, 3.0, 0, 1.0], True), ([0, 0, 0, 3.0, 0, below1], True),
-             ([0, 0, 0, 3.0, 0, np.float32(1 - 2.0 ** -22)], False),
-             ([5.0, 0, 0, 0, 0, 3.0], True), ([0, 0, 0, 0, 0, -1.0], True), ([0, 0, 8.0, 0, 0, 5.0], False),
-             ([1.0, 1.0, 1.0, 1.0, 1.0, 1.0], True)]
-    for b, want in cases:
+    cases = [  # logits ZERO..PALETTE, budget, input 7, expected bits (1 SPLIT, 2 PALETTE)
+        ([0, 0, 0, 3.0, 0, 1.0, 0], 0.1, 0.5, 1), ([0, 0, 0, 3.0, 0, below1, 0], 0.1, 0.5, 1),
+        ([0, 0, 0, 3.0, 0, np.float32(1 - 2.0 ** -22), 0], 0.1, 0.5, 0),
+        ([0, 0, 0, 3.0, 0, 0, 1.0], 0.1, 0.5, 2), ([0, 0, 0, 0, 0, 3.0, 3.0], 0.1, 0.5, 3),
+        ([5.0, 0, 0, 0, 0, 3.0, 2.0], 0.1, 0.5, 1), ([0, 0, 8.0, 0, 0, 5.0, 5.0], 0.1, 0.5, 0),
+        ([1.0] * 7, 0.1, 0.5, 3), ([1.0] * 7, 0.5, 0.5, 0), ([1.0] * 7, np.nextafter(np.float32(0.5), 0), 0.5, 3),
+    ]
+    for b, budget, x7, want in cases:
         p = M.init_params(0)
         p["W3"] = np.zeros_like(p["W3"])
-        p["b3"] = np.array(list(b) + [0, 0], dtype=np.float32)
-        assert M.wants_split(p, x)[0] == want, b
-        assert O.mlp_wants_split_c(M.flatten(p), x[0]) == want, b
-
-
-def test_zero_group_counts_hand_cases():
-    # kc = 10: 256 groups of 4 amplitudes; kc = 3: 8 groups of one amplitude
-    v = np.zeros(1 << 10, dtype=np.complex128)
-    assert M.zero_groups(v, 10) == (256, 256, 256)
-    v[5] = 1.0          # group 1 gets a real part
-    v[6] = 1j           # group 1 an imaginary part
-    v[1023] = -0.0 - 0.0j   # -0 counts as zero
-    v[12] = 3e-320      # a subnormal is not zero: group 3
-    assert M.zero_groups(v, 10) == (254, 255, 256)
-    w = np.array([1, 1j, 0, 1 + 1j, -0.0, 2, 3j, 0], dtype=np.complex128)
-    assert M.zero_groups(w, 3) == (5, 5, 8)  # zero real parts at 1, 2, 4, 6, 7; imaginary at 0, 2, 4, 5, 7
+        p["b3"] = np.array(list(b) + [budget], dtype=np.float32)
+        x = np.zeros((1, M.N_IN), dtype=np.float32)
+        x[0, 7] = x7
+        assert M.trials(p, x)[0] == want, (b, budget)
+        assert O.mlp_trials_c(M.flatten(p), x[0]) == want, (b, budget)
 
 
 def test_features_c_equal_python_definition():
@@ -138,15 +130,19 @@ def test_features_c_equal_python_definition():
     for kc in (3, 6, 10):
         A = 1 << kc
         a = rng.standard_normal(A) + 1j * rng.standard_normal(A)
-        real = rng.standard_normal(A) + 0j
-        sparse = np.where(rng.random(A) < 0.3, a, 0)
-        for img in (O.encode_chunk(a, kc, 26), O.encode_chunk(np.zeros(A, complex), kc, 64),
-                    O.encode_chunk(a, kc, 26, force_mode=5)):
-            for vals in (a, real, sparse, 1j * real):
-                for g in (Cc.gate(2, Cc.H), Cc.gate(9, Cc.T, {1: 1}), Cc.gate(2, Cc.X), Cc.gate(7, Cc.SX)):
-                    for S in (64, 26):
-                        want = M.features(img, kc, g["u"], int(g["target"]), S, vals)
-                        got = O.mlp_features_c(img, kc, g, S, vals)
-                        assert np.array_equal(got, want)
-    x = M.features(O.encode_chunk(real, 10, 26), 10, Cc.H.ravel().view(np.float64), 3, 26, real)
-    assert x[13] == 0.0 and x[15] == 1.0 and x[9] == 1.0 and x[12] == 1.0
+        few = np.resize(np.array([0.5, -0.5, 0.25]), A) + 0j
+        imgs = [O.encode_chunk(a, kc, 26), O.encode_chunk(np.zeros(A, complex), kc, 64),
+                O.encode_chunk(a, kc, 26, force_mode=5), O.encode_chunk(few, kc, 26, force_mode=6, modes=O.ALL_MODES)]
+        if kc >= 2:
+            imgs.append(O.encode_chunk(np.tile(a[:2], A // 2), kc, 26, force_mode=2))
+        for img in imgs:
+            for g in (Cc.gate(2, Cc.H), Cc.gate(9, Cc.T, {1: 1}), Cc.gate(2, Cc.X), Cc.gate(7, Cc.SX)):
+                for S in (64, 26):
+                    want = M.features(img, kc, g["u"], int(g["target"]), S)
+                    got = O.mlp_features_c(img, kc, g, S)
+                    assert np.array_equal(got, want)
+    img = O.encode_chunk(few, 10, 26, force_mode=6, modes=O.ALL_MODES)
+    x = M.features(img, 10, Cc.X.ravel().view(np.float64), 3, 26)
+    # PALETTE one-hot, k = 2 -> 2 / 16, palette size 4 (0.5, -0.5, 0.25 and the zero imaginary parts)
+    assert x[6] == 1.0 and x[10] == np.float32(2 / 16) and x[9] == np.float32(4 / (64 * 2048))
+    assert x[11] == 1.0 and x[12] == 0.0 and x[13] == 1.0 and x[14] == 1.0 and x[15] == np.float32(26 / 64)
