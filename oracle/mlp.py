@@ -89,16 +89,16 @@ TRIAL_MARGIN = np.float32(2.0)
 def trials(p: dict, x) -> np.ndarray:
     """The selector's decision per row: bit 0 runs the SPLIT trial, bit 1 the PALETTE
     trial; each iff that mode's logit plus a margin of 2 reaches the largest of the
-    seven logits and the bit budget (output 7) is below the chunk's current size
-    fraction (input 7) -- float32 sums and comparisons.  The margin leans towards a
-    trial (a missed one costs memory, a needless one only time); the budget drops
-    trials where no smaller image is expected."""
+    seven logits, and both when the bit budget (output 7) is below half the chunk's
+    current size fraction (input 7) -- float32 sums and comparisons.  Both rules lean
+    towards a trial (a missed one costs memory, a needless one only time); the budget
+    rule catches a predicted collapse of the image that the mode logits may miss."""
     x = np.asarray(x, dtype=np.float32)
     out = forward32(p, x)
     mx = out[:, :N_MODES].max(axis=1)
-    smaller = out[:, 7] < x[:, 7]
-    split = ((out[:, 5] + TRIAL_MARGIN).astype(np.float32) >= mx) & smaller
-    pal = ((out[:, 6] + TRIAL_MARGIN).astype(np.float32) >= mx) & smaller
+    shrink = out[:, 7] < (x[:, 7] * np.float32(0.5)).astype(np.float32)
+    split = ((out[:, 5] + TRIAL_MARGIN).astype(np.float32) >= mx) | shrink
+    pal = ((out[:, 6] + TRIAL_MARGIN).astype(np.float32) >= mx) | shrink
     return split.astype(np.int64) | (pal.astype(np.int64) << 1)
 
 

@@ -715,20 +715,21 @@ void orc_mlp_forward(const float* prm, const float* x, float* out) {
  * PALETTE; output 7: the bit budget, the predicted size of the chunk's best image as a
  * fraction of the RAW size.  Decision: the SPLIT (bit 0) and PALETTE (bit 1) trials
  * each run iff that mode's logit plus a margin of 2 reaches the largest of the seven
- * logits and the budget is below the chunk's current image size (input 7); float32
- * sums and comparisons.  The margin leans towards a trial (a missed trial costs memory,
- * a needless one only time); the budget drops trials where no smaller image is
- * expected.  The cheap modes are always computed; the codec keeps the bound. */
+ * logits, and both run when the budget is below half the chunk's current size fraction
+ * (input 7) -- a predicted collapse of the image the mode logits may miss; float32
+ * sums and comparisons.  Every rule leans towards a trial: a missed trial costs memory,
+ * a needless one only time.  The cheap modes are always computed; the codec keeps the
+ * bound. */
 int orc_mlp_trials(const float* prm, const float* x) {
   float out[8];
   orc_mlp_forward(prm, x, out);
   float mx = out[0];
   for (int m = 1; m < 7; ++m)
     if (out[m] > mx) mx = out[m];
-  const int smaller = out[7] < x[7];
+  const int shrink = out[7] < x[7] * 0.5f;
   int t = 0;
-  if (out[5] + 2.0f >= mx && smaller) t |= 1;
-  if (out[6] + 2.0f >= mx && smaller) t |= 2;
+  if (out[5] + 2.0f >= mx || shrink) t |= 1;
+  if (out[6] + 2.0f >= mx || shrink) t |= 2;
   return t;
 }
 

@@ -100,17 +100,21 @@ def test_decision_rule_margin_and_budget_edges():
     """Output layer weights zero: the logits and the budget are the biases b3, so the
     rule can be checked at its edges.  A trial mode's logit exactly 2 below the top one
     is a trial, and so is one whose float32 sum with 2 rounds up to the top; one float32
-    step of the sum below is not.  The budget must be below the current size fraction
-    (input 7): equal is not below.  C and numpy agree."""
+    step of the sum below is not.  A budget below half the current size fraction (input
+    7) runs both trials whatever the logits say: equal to the half is not below.  C and
+    numpy agree."""
     import oracle as O
 
     below1 = np.nextafter(np.float32(1), np.float32(0))  # 1 - 2^-24: + 2 rounds back to 3 in float32
     cases = [  # logits ZERO..PALETTE, budget, input 7, expected bits (1 SPLIT, 2 PALETTE)
-        ([0, 0, 0, 3.0, 0, 1.0, 0], 0.1, 0.5, 1), ([0, 0, 0, 3.0, 0, below1, 0], 0.1, 0.5, 1),
-        ([0, 0, 0, 3.0, 0, np.float32(1 - 2.0 ** -22), 0], 0.1, 0.5, 0),
-        ([0, 0, 0, 3.0, 0, 0, 1.0], 0.1, 0.5, 2), ([0, 0, 0, 0, 0, 3.0, 3.0], 0.1, 0.5, 3),
-        ([5.0, 0, 0, 0, 0, 3.0, 2.0], 0.1, 0.5, 1), ([0, 0, 8.0, 0, 0, 5.0, 5.0], 0.1, 0.5, 0),
-        ([1.0] * 7, 0.1, 0.5, 3), ([1.0] * 7, 0.5, 0.5, 0), ([1.0] * 7, np.nextafter(np.float32(0.5), 0), 0.5, 3),
+        ([0, 0, 0, 3.0, 0, 1.0, 0], 0.3, 0.5, 1), ([0, 0, 0, 3.0, 0, below1, 0], 0.3, 0.5, 1),
+        ([0, 0, 0, 3.0, 0, np.float32(1 - 2.0 ** -22), 0], 0.3, 0.5, 0),
+        ([0, 0, 0, 3.0, 0, 0, 1.0], 0.3, 0.5, 2), ([0, 0, 0, 0, 0, 3.0, 3.0], 0.3, 0.5, 3),
+        ([5.0, 0, 0, 0, 0, 3.0, 2.0], 0.3, 0.5, 1), ([0, 0, 8.0, 0, 0, 5.0, 5.0], 0.3, 0.5, 0),
+        ([0, 0, 8.0, 0, 0, 5.0, 5.0], 0.25, 0.5, 0),
+        ([0, 0, 8.0, 0, 0, 5.0, 5.0], np.nextafter(np.float32(0.25), np.float32(0)), 0.5, 3),
+        ([0, 0, 8.0, 0, 0, 5.0, 5.0], 0.1, 0.5, 3), ([0, 0, 8.0, 0, 0, 5.0, 5.0], 0.1, 0.2, 0),
+        ([1.0] * 7, 0.9, 0.5, 3),
     ]
     for b, budget, x7, want in cases:
         p = M.init_params(0)
