@@ -96,7 +96,8 @@ typedef struct sim_stats_t {
   uint64_t cache_hits;        /* ... that took a cached result */
   uint64_t fast_items;        /* work items the streaming gate kernel wrote (cumulative) */
   uint64_t fast_deferred;     /* work items it left to the general gate kernel (cumulative) */
-  uint64_t kernel_launches;   /* kernels the gates enqueued (streaming, general and post kernels) */
+  uint64_t kernel_launches;   /* kernels the gates enqueued (selector, streaming, general and post kernels) */
+  uint64_t palette_trials;    /* chunk encodes that ran the PALETTE trial */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
@@ -205,24 +206,34 @@ sim_status sim_set_block_cache(sim_t* sim, int on);
  * item runs in the general gate kernel. */
 sim_status sim_set_modes(sim_t* sim, uint32_t modes);
 
-/* Learned selector (not from the paper).  selector 0: Solution C modes only (the
- * default); 1: Solution C and D, every chunk trying both orders (exhaustive);
- * 2: Solution C and D, a chunk trying the Solution D order only where a
- * 16 -> 32 -> 32 -> 8 network with bfloat16 weights (1864 values, W1[32][16] b1 W2[32][32]
- * b2 W3[8][32] b3, host pointer) predicts that SPLIT wins.  The network reads the chunk's
- * previous image header and the gate (see the selector section of device.cuh); its
- * float32 inference has a fixed order, so its decisions are reproducible.  The bound
- * is enforced by the codec whatever the network says. */
+/* Learned selector (not from the paper).  selector 0: the mode set of sim_set_modes
+ * (default Solution C, 0x1F); 1: every mode (0x7F), each chunk running the SPLIT
+ * (Solution D) and PALETTE trials (exhaustive); 2: Solution C's modes, plus the SPLIT /
+ * PALETTE trial for a chunk only where a 16 -> 32 -> 32 -> 8 network with bfloat16
+ * weights (1864 values, W1[32][16] b1 W2[32][32] b2 W3[8][32] b3, host pointer, copied)
+ * grants it.  The network predicts the best mode (outputs 0..6) and a bit budget (output
+ * 7: the best image's size over the RAW size) from the chunk's current image header and
+ * the gate alone, so one small kernel takes a whole gate's decisions before the gate
+ * runs; a trial runs iff its mode's logit + 2 reaches the largest mode logit, and both
+ * run when the budget is below half the chunk's current size fraction.  Items none of
+ * whose chunks got a trial stay on the streaming kernel.  float32 inference in a fixed
+ * order: decisions are reproducible.  The codec enforces the bound whatever the network
+ * says.  Selector 2 allocates one decision byte per chunk.  Counts in
+ * sim_stats_t.split_trials / palette_trials. */
 sim_status sim_set_selector(sim_t* sim, int selector, const uint16_t* bf16_params);
 
-/* Selector training records: with capacity > 0, every chunk encode that tries both
- * orders appends 20 floats (16 network inputs, the chosen mode, STREAM and SPLIT image
- * sizes as fractions of RAW, 0) until capacity records exist; 0 stops and frees. */
+/* Selector training records: with capacity > 0, every chunk a gate encodes appends 20
+ * floats (the network's 16 inputs from the chunk's pre-gate image and the gate, the mode
+ * the mode set chose, that image's size over the RAW size, 0, 0) until capacity records
+ * exist; with selector 1 the chosen mode is the best of all seven.  Gates run in the
+ * general kernel while records are written.  0 stops and frees. */
 sim_status sim_trace(sim_t* sim, uint64_t capacity);
 sim_status sim_trace_read(sim_t* sim, float* out, uint64_t cap_records, uint64_t* n_records);
 
 /* Selector training on the GPU with the library's own kernels: n samples of 16 inputs
- * (x), the exhaustive mode (0..5) and the two size fractions; float32 master weights
+ * (x), the exhaustive mode (0..6) and the best size fraction (sizes, one per sample);
+ * loss: softmax cross-entropy of outputs 0..6 plus the squared error of output 7;
+ * float32 master weights
  * (params, 1864 values, in: initial, out: trained) rounded to bfloat16 for every
  * forward and backward pass; Adam (beta 0.9, 0.999), minibatches from a seeded
  * shuffle.  bf16_out (may be NULL) receives the trained bfloat16 weights, last_loss

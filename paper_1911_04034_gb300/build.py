@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqcsim.so")
-SOURCES = ["kernels.cu", "fast.cu", "api.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["kernels.cu", "fast.cu", "api.cu", "noalloc.cu", "mlp.cu", "select.cu"]
 HEADERS = ["device.cuh", "launch.h", "gate_common.cuh"]
 
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -150,6 +150,7 @@ struct sim {
   uint32_t modes = qc::kDefaultModes;
   int selector = 0;                  // 0 mode set, 2 selector network
   unsigned short* d_mlp = nullptr;   // bfloat16 parameters of the selector network
+  uint8_t* d_dec = nullptr;          // its decisions for the running gate (one byte per chunk)
   float* d_trace = nullptr;          // selector training records
   uint8_t* d_bc = nullptr;           // block cache lines (Section 3.4) or nullptr
   uint32_t* d_defer = nullptr;       // items the streaming kernel leaves to the general one
@@ -169,6 +170,7 @@ struct sim {
     cudaFree(d_tlog);
     cudaFree(d_defer);
     cudaFree(d_mlp);
+    cudaFree(d_dec);
     cudaFree(d_trace);
     cudaFree(d_bc);
     cudaFree(P.pages);
@@ -400,8 +402,7 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
   L.target = t;
   L.prof = s->phases ? 1 : 0;
   L.modes = s->modes;
-  L.selector = s->selector;
-  L.mlp = s->d_mlp;
+  L.sel_dec = s->selector == 2 ? s->d_dec : nullptr;
   {
     const double* u = g->u;
     const bool real = u[1] == 0 && u[3] == 0 && u[5] == 0 && u[7] == 0;
@@ -451,10 +452,12 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
 }
 
 // True if the streaming kernel can take the gate's items (see kernels.cu): chunk sizes
-// 2^7..2^11, the plain mode set and selector, no block cache or training records, and a
-// partner amplitude within a warp's pass unless the gate is diagonal.  Sets L.fast_kind.
+// 2^7..2^11, Solution C's mode set (under the selector network: the items none of
+// whose chunks was granted a trial), no block cache or training records, and a partner
+// amplitude within a warp's pass unless the gate is diagonal.  Sets L.fast_kind.
 static bool fast_applies(const sim* s, const sim_gate* g, GateLaunch& L) {
-  if (!s->fast || s->fast_grid == 0 || L.bc || L.trace || L.selector != 0 || L.modes != qc::kDefaultModes) return false;
+  if (!s->fast || s->fast_grid == 0 || L.bc || L.trace) return false;
+  if (!L.sel_dec && L.modes != qc::kDefaultModes) return false;
   const double* u = g->u;
   const bool diag = u[2] == 0.0 && u[3] == 0.0 && u[4] == 0.0 && u[5] == 0.0;
   const bool anti = u[0] == 0.0 && u[1] == 0.0 && u[6] == 0.0 && u[7] == 0.0;
@@ -497,6 +500,14 @@ static sim_status enqueue_gate(sim* s, const sim_gate* g) {
     e0 = s->ev_pool[s->ev_next++];
     e1 = s->ev_pool[s->ev_next++];
     CK(cudaEventRecord(e0, s->st), "event record");
+  }
+  if (L.sel_dec) {
+    // the selector's decisions for every chunk the gate rewrites, before either gate kernel
+    const unsigned long long n = L.pair ? 2ull * L.items : L.nact;
+    const unsigned long long want = (n + 255ull) / 256ull;
+    const int sg = (unsigned long long)s->grid < want ? s->grid : (int)want;
+    CK(qc::launch_select(L, s->d_mlp, s->d_dec, sg, s->st), "selector kernel launch");
+    s->kernel_launches += 1;
   }
   if (fast) {
     // the streaming kernel first; the general kernel then runs the items it left
@@ -724,9 +735,10 @@ sim_status sim_set_selector(sim_t* s, int selector, const uint16_t* bf16_params)
   if (selector == 2) {
     if (!bf16_params) return fail(SIM_ERR_INVALID, "the selector network needs its parameters");
     if (!s->d_mlp) CK(cudaMalloc(&s->d_mlp, qc::kMlpParams * 2), "selector parameters");
+    if (!s->d_dec) CK(cudaMalloc(&s->d_dec, s->nchunks + 16), "selector decisions");
     CK(cudaMemcpy(s->d_mlp, bf16_params, qc::kMlpParams * 2, cudaMemcpyHostToDevice), "selector parameters");
   }
-  s->modes = selector == 1 ? (qc::kDefaultModes | (1u << qc::M_SPLIT)) : qc::kDefaultModes;
+  s->modes = selector == 1 ? qc::kAllModes : qc::kDefaultModes;
   s->selector = selector == 2 ? 2 : 0;
   return SIM_OK;
 }
@@ -905,6 +917,7 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->fast_items = h.fast_items;
   o->fast_deferred = h.fast_deferred;
   o->kernel_launches = s->kernel_launches;
+  o->palette_trials = h.palette_trials;
   if (h.err) return s->check_device();
   return SIM_OK;
 }
@@ -949,6 +962,7 @@ sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const*
   // step t holds gate t of every circuit that has one; its jobs' items are numbered
   // consecutively
   std::vector<qc::BatchJob> jobs;
+  std::vector<sim*> job_sim;  // the handle of each job
   std::vector<size_t> off(steps + 1, 0);
   std::vector<unsigned long long> total(steps, 0);
   int grid = sims[0]->grid;
@@ -963,6 +977,7 @@ sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const*
       j.begin = begin;
       begin += j.L.items;
       jobs.push_back(j);
+      job_sim.push_back(sims[k]);
     }
     total[t] = begin;
   }
@@ -987,7 +1002,15 @@ sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const*
   for (size_t t = 0; t < steps && e == cudaSuccess; ++t) {
     const int n = (int)(off[t + 1] - off[t]);
     const int g = (unsigned long long)grid < total[t] ? grid : (int)total[t];
-    e = qc::launch_gate_batch(d_jobs + off[t], n, total[t], kc, g, cs);
+    // the selector's decisions of every handle that runs the network, before the step
+    for (size_t j = off[t]; j < off[t + 1] && e == cudaSuccess; ++j) {
+      const GateLaunch& L = jobs[j].L;
+      if (!L.sel_dec) continue;
+      const unsigned long long na = L.pair ? 2ull * L.items : L.nact;
+      const int sg = (unsigned long long)grid < (na + 255ull) / 256ull ? grid : (int)((na + 255ull) / 256ull);
+      e = qc::launch_select(L, job_sim[j]->d_mlp, const_cast<uint8_t*>(L.sel_dec), sg, cs);
+    }
+    if (e == cudaSuccess) e = qc::launch_gate_batch(d_jobs + off[t], n, total[t], kc, g, cs);
     if (e == cudaSuccess) e = qc::launch_post_batch(d_jobs + off[t], n, grid, cs);
   }
   if (use_graph && cs != st) {

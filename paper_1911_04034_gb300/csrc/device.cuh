@@ -29,6 +29,7 @@ enum : uint32_t {
 // Solution C's modes; SPLIT (Solution D, re parts then im parts) and PALETTE (distinct
 // values plus k-bit indices) only on request
 constexpr uint32_t kDefaultModes = 0x1Fu;
+constexpr uint32_t kAllModes = 0x7Fu;  // every mode, SPLIT and PALETTE trials included
 constexpr uint32_t kPaletteMax = 256;  // most distinct values a PALETTE image lists
 // Index width of a palette of P entries: the smallest k >= 1 with 2^k >= P.
 __host__ __device__ __forceinline__ uint32_t palette_bits(uint32_t P) {
@@ -93,6 +94,7 @@ struct DevCtl {
   unsigned int timeout_site;           // where a bounded wait gave up (E_TIMEOUT): 1 item start, 2 pass, 3 item end
   unsigned int timeout_pad;
   unsigned long long wc_pages;         // free pages the streaming kernel's warps keep in their caches
+  unsigned long long palette_trials;   // chunk encodes that ran the PALETTE trial
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -202,11 +204,8 @@ struct ScanSmem {
   uint32_t wlm2[2][kWarps];  // the second chunk's lead-byte scan (decode_stream32_pair)
   uint32_t wlv2[2][kWarps];
   uint32_t bits_period;
-  int split_pick;  // the selector network's decision for the chunk being encoded
-  uint32_t zcnt[2];  // selector inputs: amplitude groups with all-zero real / imaginary parts
   unsigned long long bc_part[kWarps];  // block cache: per-warp partial hashes
   int bc_flag;                         // block cache: 0 miss, 1 candidate line, 2 line claimed
-  __align__(16) float sel_x[32];       // selector: the current layer's inputs (warp 0)
 };
 
 // Exclusive prefix sum over the CTA with one barrier; also ORs `fo` and ANDs `fa`
@@ -699,124 +698,96 @@ __device__ bool decode_stream32_pair(const uint8_t* img0, const uint8_t* img1, u
 }
 
 // ------------------------------------------------------- learned selector -- //
-// Not from the paper.  A 16 -> 32 -> 32 -> 8 network with bfloat16 weights predicts
-// whether the Solution D trial (SPLIT) can win for a chunk, so that trial runs only
-// where it may pay.  Inference is float32 with a fixed order: each unit sums its
-// products over its inputs in index order, one rounding per product and per sum
-// (no fused multiply-add), then adds its bias; ReLU maps non-positive sums to +0.
-// The trial runs iff the SPLIT logit plus 2 reaches the largest mode logit: a missed
-// SPLIT costs memory, a needless trial only time.
+// Not from the paper.  For every chunk a gate is about to rewrite, a 16 -> 32 -> 32 -> 8
+// network with bfloat16 weights predicts the best chunk mode (outputs 0..6: logits of
+// ZERO, CONST, PERIOD, STREAM, RAW, SPLIT, PALETTE) and a bit budget (output 7: the best
+// image's size over the RAW size) from the chunk's current image header and the gate
+// alone.  Needing no decoded value, the decisions of a whole gate come from one small
+// kernel that runs before the gate.  The SPLIT (Solution D) and PALETTE trials run
+// only for chunks whose decision grants them; the cheap modes are always computed, and
+// the codec keeps the error bound whatever the network says.
+//
+// Inference is float32 with a fixed order: each unit sums its products over its
+// inputs in index order, one rounding per product and per sum (no fused
+// multiply-add), then adds its bias; ReLU maps non-positive sums to +0.  A trial runs
+// iff its mode's logit plus 2 reaches the largest of the seven logits; both run when
+// the budget is below half the chunk's current size fraction (input 7), a predicted
+// collapse of the image that the logits may miss.  Both rules lean towards a trial: a
+// missed one costs memory, a needless one only time.
 constexpr int kMlpParams = 1864;  // W1[32][16] b1[32] W2[32][32] b2[32] W3[8][32] b3[8]
-constexpr int kTraceFloats = 20;  // features[16], best mode, STREAM and SPLIT size / RAW, 0
+constexpr int kTraceFloats = 20;  // features[16], best mode, best size / RAW size, 0, 0
+constexpr uint32_t kSelSplit = 1u, kSelPalette = 2u;  // decision bits
 
+// Gate features of the selector (bits): 0 the matrix is real, 1 diagonal, 2
+// anti-diagonal, 3 the target lies inside the chunk.
 struct SelCtx {
-  int selector;                    // 0: the mode set decides; 2: the network decides SPLIT trials
-  const unsigned short* mlp;       // bfloat16 parameters (16-byte aligned; a shared-memory copy in k_gate), selector 2
-  uint32_t gfeat;                  // gate features: bit0 real, 1 diagonal, 2 permutation, 3 target in chunk
+  uint32_t gfeat;
   uint32_t S_gate;                 // significant bits the controller chose for this gate
-  uint32_t prev_hdr[4];            // header of the chunk's previous image
+  uint32_t prev_hdr[4];            // header of the chunk's current (pre-gate) image
   uint32_t prev_len;               // and its length
-  float* trace;                    // trace records (device) or nullptr
+  float* trace;                    // training records (device) or nullptr
   unsigned long long* trace_n;
   unsigned long long trace_cap;
-  unsigned long long* split_trials;  // counts chunks that ran the Solution D trial
+  unsigned long long* split_trials;    // counts chunk encodes that ran the SPLIT trial
+  unsigned long long* palette_trials;  // ... and the PALETTE trial
 };
 
-__device__ __forceinline__ float bf16_at(const unsigned short* w, int i) { return __uint_as_float((uint32_t)w[i] << 16); }
-
-// Input i of the network for the chunk described by sel (kc = chunk_log2); zre / zim
-// count the chunk's G = min(2^kc, 256) groups of consecutive amplitudes whose real /
-// imaginary parts are all zero after the gate.
-__device__ __forceinline__ float sel_feature(const SelCtx& sel, int kc, int i, uint32_t zre, uint32_t zim) {
-  const uint32_t pmode = sel.prev_hdr[0] & 0xffu, pS = (sel.prev_hdr[0] >> 8) & 0xffu, pbits = sel.prev_hdr[3];
-  const float G = __uint2float_rn(min(1u << kc, 256u));
-  if (i < 6) return pmode == (uint32_t)i ? 1.0f : 0.0f;
-  if (i == 6) return __fdiv_rn(__uint2float_rn(sel.prev_len), __uint2float_rn(16u + (16u << kc)));
-  if (i == 7) return __fdiv_rn(__uint2float_rn(pS), 64.0f);
-  if (i == 8) return __fdiv_rn(__uint2float_rn(pbits), __uint2float_rn(64u * (2u << kc)));
-  if (i < 13) return ((sel.gfeat >> (i - 9)) & 1u) ? 1.0f : 0.0f;
-  if (i == 13) return __fdiv_rn(__uint2float_rn(zre), G);
-  if (i == 14) return __fdiv_rn(__uint2float_rn(sel.S_gate), 64.0f);
-  return __fdiv_rn(__uint2float_rn(zim), G);
+// The chunk modes a decision grants: Solution C's set plus the trials.
+__host__ __device__ __forceinline__ uint32_t sel_modes(uint32_t dec) {
+  return kDefaultModes | ((dec & kSelSplit) ? (1u << M_SPLIT) : 0u) | ((dec & kSelPalette) ? (1u << M_PALETTE) : 0u);
 }
 
-// Counts the groups of sel_feature (every thread of the block calls it; each thread's
-// VPT values form one group, or, at VPT = 1, one half of an amplitude).
-template <int VPT>
-__device__ __forceinline__ void zero_group_counts(const uint64_t* tile, uint32_t N, uint32_t& zre, uint32_t& zim) {
-  const uint32_t j0 = threadIdx.x * VPT;
-  uint64_t v[VPT];
-  load_vals<VPT>(tile, j0, N, v);
-  bool re_nz = false, im_nz = false;
-#pragma unroll
-  for (int k = 0; k < VPT; ++k) {
-    if (j0 + k < N) {
-      const bool nz = (v[k] << 1) != 0ull;
-      if ((j0 + k) & 1u) im_nz |= nz;
-      else re_nz |= nz;
-    }
-  }
-  const uint32_t G = min(N >> 1, 256u);
-  zre = G - (uint32_t)__syncthreads_count(re_nz);
-  zim = G - (uint32_t)__syncthreads_count(im_nz);
+// Input i of the network for a chunk whose current image has header hdr and length
+// len (kc = chunk_log2): one-hot of the image mode (0..6), its size over the RAW size
+// (7), its S / 64 (8), header word 3 / (64 N) (9: residual bits, or the palette size),
+// header byte 2 / 16 (10: log2 period, or the palette index width), the gate features
+// (11..14), the gate's S / 64 (15).
+__device__ __forceinline__ float sel_feature(const uint32_t hdr[4], uint32_t len, int kc, uint32_t gfeat,
+                                             uint32_t S_gate, int i) {
+  const uint32_t mode = hdr[0] & 0xffu, S = (hdr[0] >> 8) & 0xffu, b2 = (hdr[0] >> 16) & 0xffu;
+  if (i < 7) return mode == (uint32_t)i ? 1.0f : 0.0f;
+  if (i == 7) return __fdiv_rn(__uint2float_rn(len), __uint2float_rn(16u + (16u << kc)));
+  if (i == 8) return __fdiv_rn(__uint2float_rn(S), 64.0f);
+  if (i == 9) return __fdiv_rn(__uint2float_rn(hdr[3]), __uint2float_rn(64u * (2u << kc)));
+  if (i == 10) return __fdiv_rn(__uint2float_rn(b2), 16.0f);
+  if (i < 15) return ((gfeat >> (i - 11)) & 1u) ? 1.0f : 0.0f;
+  return __fdiv_rn(__uint2float_rn(S_gate), 64.0f);
 }
 
-// Warp-level inference; every lane of the warp must call it.  Returns (to all lanes)
-// whether SPLIT has the largest of the six mode logits (first maximum wins).
-// bfloat16 pair (one 32-bit word: element 2i in the low half) to two floats.
-__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
-
-// One unit's float32 sum over NIN inputs (a multiple of 8) in input order: weights read
-// as 16-byte vectors from w (16-byte aligned), inputs as 16-byte vectors from xs (the
-// layer's inputs in shared memory), so the chain of sums waits on no shuffle.
+// One unit: the float32 sum over NIN inputs in input order, then the bias.
 template <int NIN>
-__device__ __forceinline__ float sel_unit(const unsigned short* w, const float* xs) {
-  const uint4* wv = reinterpret_cast<const uint4*>(w);
-  const float4* xv = reinterpret_cast<const float4*>(xs);
+__device__ __forceinline__ float sel_unit(const float* w, const float* in, float bias) {
   float acc = 0.0f;
 #pragma unroll
-  for (int q = 0; q < NIN / 8; ++q) {
-    const uint4 p = wv[q];
-    const float4 a = xv[2 * q], b = xv[2 * q + 1];
-    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.x), a.x));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.x), a.y));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.y), a.z));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.y), a.w));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.z), b.x));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.z), b.y));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_lo(p.w), b.z));
-    acc = __fadd_rn(acc, __fmul_rn(bf16_hi(p.w), b.w));
-  }
-  return acc;
+  for (int i = 0; i < NIN; ++i) acc = __fadd_rn(acc, __fmul_rn(w[i], in[i]));
+  return __fadd_rn(acc, bias);
 }
 
-// Warp-level inference (every lane of the warp calls it; xs: 32 floats of shared
-// memory, 16-byte aligned, private to the warp).  Returns to all lanes whether the
-// Solution D trial runs (SPLIT logit + 2 >= the largest mode logit).
-__device__ __forceinline__ bool sel_wants_split(const SelCtx& sel, int kc, uint32_t zre, uint32_t zim, float* xs) {
-  const int lane = threadIdx.x & 31;
-  const unsigned short* w = sel.mlp;  // W1 (512) b1 (32) W2 (1024) b2 (32) W3 (256) b3 (8)
-  xs[lane] = lane < 16 ? sel_feature(sel, kc, lane, zre, zim) : 0.0f;
-  __syncwarp();
-  float acc = __fadd_rn(sel_unit<16>(w + 16 * lane, xs), bf16_at(w, 512 + lane));
-  const float h1 = acc > 0.0f ? acc : 0.0f;
-  __syncwarp();
-  xs[lane] = h1;
-  __syncwarp();
-  acc = __fadd_rn(sel_unit<32>(w + 544 + 32 * lane, xs), bf16_at(w, 1568 + lane));
-  const float h2 = acc > 0.0f ? acc : 0.0f;
-  __syncwarp();
-  xs[lane] = h2;
-  __syncwarp();
-  const int o = lane & 7;
-  acc = __fadd_rn(sel_unit<32>(w + 1600 + 32 * o, xs), bf16_at(w, 1856 + o));
-  float mx = __shfl_sync(0xffffffffu, acc, 0);
-  for (int m = 1; m < 6; ++m) {
-    const float v = __shfl_sync(0xffffffffu, acc, m);
-    if (v > mx) mx = v;
+// The decision bits for one chunk (one thread; w: the parameters as float32, in
+// shared memory; x: the 16 inputs).
+__device__ __forceinline__ uint32_t sel_decide(const float* w, const float x[16]) {
+  float h1[32], h2[32], o[8];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float z = sel_unit<16>(w + 16 * j, x, w[512 + j]);
+    h1[j] = z > 0.0f ? z : 0.0f;
   }
-  return __fadd_rn(__shfl_sync(0xffffffffu, acc, 5), 2.0f) >= mx;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float z = sel_unit<32>(w + 544 + 32 * j, h1, w[1568 + j]);
+    h2[j] = z > 0.0f ? z : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) o[j] = sel_unit<32>(w + 1600 + 32 * j, h2, w[1856 + j]);
+  float mx = o[0];
+#pragma unroll
+  for (int m = 1; m < 7; ++m)
+    if (o[m] > mx) mx = o[m];
+  const bool shrink = o[7] < __fmul_rn(x[7], 0.5f);
+  uint32_t d = 0;
+  if (__fadd_rn(o[5], 2.0f) >= mx || shrink) d |= kSelSplit;
+  if (__fadd_rn(o[6], 2.0f) >= mx || shrink) d |= kSelPalette;
+  return d;
 }
 
 // ----------------------------------------------------------- encoder ----- //
@@ -1092,7 +1063,6 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
     if (act && ((j0 >> 1) & Ptop)) gtop = t[0] == tile[tile_val(j0 ^ (2u * Ptop))];
   }
   // Solution D order (SPLIT): only its residual length is needed unless it wins
-  if (sel && sel->selector == 2) modes = s.split_pick ? (modes | (1u << M_SPLIT)) : (modes & ~(1u << M_SPLIT));
   const bool want_split = force_mode == (int)M_SPLIT || (force_mode < 0 && ((modes >> M_SPLIT) & 1u));
   uint32_t sum2 = 0;
   if (want_split) {
@@ -1191,17 +1161,20 @@ __device__ __forceinline__ uint32_t encode_core(uint64_t* tile, int kc, uint32_t
   if (mode == M_RAW) nv = N;
   if (mode == M_SPLIT) { nv = N; rbits = total2; }
   if (mode == M_PALETTE) { nv = N; rbits = npal; }
-  if (sel && sel->split_trials && threadIdx.x == 0 && want_split && force_mode < 0) atomicAdd(sel->split_trials, 1ull);
-  // training record: the chunk's inputs, the exhaustive choice and both trial sizes
-  if (sel && sel->trace && threadIdx.x == 0 && want_split) {
+  if (sel && threadIdx.x == 0 && force_mode < 0) {
+    if (want_split && sel->split_trials) atomicAdd(sel->split_trials, 1ull);
+    if (want_pal && sel->palette_trials) atomicAdd(sel->palette_trials, 1ull);
+  }
+  // training record: the chunk's pre-gate inputs, the mode the mode set chose and its
+  // size over the RAW size
+  if (sel && sel->trace && threadIdx.x == 0 && force_mode < 0) {
     const unsigned long long k = atomicAdd(sel->trace_n, 1ull);
     if (k < sel->trace_cap) {
       float* rec = sel->trace + k * kTraceFloats;
-      for (int i = 0; i < 16; ++i) rec[i] = sel_feature(*sel, kc, i, s.zcnt[0], s.zcnt[1]);
-      const float rawf = __uint2float_rn(16u + 8u * N);
+      for (int i = 0; i < 16; ++i) rec[i] = sel_feature(sel->prev_hdr, sel->prev_len, kc, sel->gfeat, sel->S_gate, i);
       rec[16] = (float)mode;
-      rec[17] = __fdiv_rn(__uint2float_rn(size[M_STREAM]), rawf);
-      rec[18] = __fdiv_rn(__uint2float_rn(size[M_SPLIT]), rawf);
+      rec[17] = __fdiv_rn(__uint2float_rn(best), __uint2float_rn(16u + 8u * N));
+      rec[18] = 0.0f;
       rec[19] = 0.0f;
     }
   }
@@ -1276,19 +1249,6 @@ __device__ uint32_t encode_block(uint64_t* tile, int kc, uint32_t S_req, int for
                                  uint32_t img_cap, ScanSmem& s, int& pp, unsigned int* err,
                                  const SelCtx* sel = nullptr) {
   const uint32_t N = 2u << kc;
-  // the selector network decides whether this chunk gets the Solution D trial
-  if (sel && (sel->selector == 2 || sel->trace)) {
-    uint32_t zre, zim;
-    zero_group_counts<VPT>(tile, N, zre, zim);
-    if (threadIdx.x == 0) {
-      s.zcnt[0] = zre;
-      s.zcnt[1] = zim;
-    }
-    if (sel->selector == 2 && threadIdx.x < 32u) {
-      const bool pick = sel_wants_split(*sel, kc, zre, zim, s.sel_x);
-      if (threadIdx.x == 0) s.split_pick = pick ? 1 : 0;
-    }
-  }
   const uint32_t j0 = threadIdx.x * VPT;
   // 0. clear the payload area the packers OR into (the buffer is free here)
   {

@@ -451,9 +451,9 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
   unsigned long long ch = 0;
   if (whole) ch = L.pair ? ((item_chunk(L, item) | L.hi_vals) | (side ? L.pair_bit : 0ull))
                          : (item_chunk(L, 2ull * item + side) | L.hi_vals);
-  // directory entry and header: a STREAM image at S <= 32
+  // directory entry and header: a STREAM image at S <= 32, granted no selector trial
   uint32_t ib = 0, inp = 0, Sin = 0, bits_in = 0;
-  bool ok = whole;
+  bool ok = whole && (!L.sel_dec || L.sel_dec[2ull * item + side] == 0u);
   if (ok) {
     const uint32_t* e = dir_entry(P, ch);
     const uint2 h = *reinterpret_cast<const uint2*>(e);

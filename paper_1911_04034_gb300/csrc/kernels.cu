@@ -34,7 +34,7 @@ __host__ __device__ __forceinline__ uint32_t pagelist_words(int kc) { return (ma
 __host__ __device__ __forceinline__ uint32_t imgbuf(int kc) { return imgcap(kc) + 16u; }
 size_t gate_smem_bytes(int kc) {
   return 2 * size_t(tile_words(kc)) * 8 + 2 * size_t(imgbuf(kc)) + 4 * size_t(dir_stride(kc)) +
-         round16(sizeof(ScanSmem)) + round16(2 * kMlpParams);
+         round16(sizeof(ScanSmem));
 }
 size_t codec_smem_bytes(int kc) {
   return size_t(tile_words(kc)) * 8 + size_t(codedcap(kc)) + 4 * size_t(pagelist_words(kc)) + round16(sizeof(ScanSmem));
@@ -49,7 +49,6 @@ struct GateSmem {
   uint32_t* ent[2][2];    // two sets of copies of the two directory entries (header, page
                           // ids or image): the current item's and the next item's
   ScanSmem* s;
-  unsigned short* mlp;    // the selector network's parameters, copied once per launch
   long long* ph;          // per-phase cycles, [6] = last clock (profiling)
   int* oom;
   uint32_t* np;
@@ -139,7 +138,6 @@ __device__ __forceinline__ GateSmem gate_smem(uint8_t* smem, int kc, uint32_t di
   m.ent[1][0] = m.ent[0][1] + dir_words;
   m.ent[1][1] = m.ent[1][0] + dir_words;
   m.s = reinterpret_cast<ScanSmem*>(m.ent[1][1] + dir_words);
-  m.mlp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint8_t*>(m.s) + round16(sizeof(ScanSmem)));
   m.ph = ph;
   m.oom = oom;
   m.np = np;
@@ -167,16 +165,6 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
     for (int k = 0; k < 6; ++k) ph[k] = 0;
     ph[6] = clock64();
   }
-}
-
-// The selector network's parameters into shared memory (all threads; the next barrier
-// publishes them).
-__device__ __forceinline__ void load_selector(const GateLaunch& L, const GateSmem& m) {
-  if (L.selector != 2 || !L.mlp) return;
-  static_assert((2 * kMlpParams) % 16 == 0, "the parameters copy as whole 16-byte units");
-  const uint4* src = reinterpret_cast<const uint4*>(L.mlp);
-  for (uint32_t u = threadIdx.x; u < (uint32_t)(2 * kMlpParams) / 16u; u += kThreads)
-    reinterpret_cast<uint4*>(m.mlp)[u] = src[u];
 }
 
 // Warp 0: hands the CTA's page cache and counters back to the simulator.
@@ -459,32 +447,37 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   }
   __syncthreads();
   QC_PHASE(2);
+  // chunk modes: the mode set, or Solution C's set plus the trials the selector granted
+  uint32_t md0 = L.modes, md1 = L.modes;
+  if (L.sel_dec) {
+    md0 = sel_modes(L.sel_dec[2ull * item]);
+    md1 = has1 ? sel_modes(L.sel_dec[2ull * item + 1ull]) : kDefaultModes;
+  }
   SelCtx sel;
-  sel.selector = L.selector;
-  sel.mlp = m.mlp;
   sel.gfeat = L.gfeat;
   sel.S_gate = S;
   sel.trace = L.trace;
   sel.trace_n = L.trace_n;
   sel.trace_cap = L.trace_cap;
   sel.split_trials = &ctl->split_trials;
+  sel.palette_trials = &ctl->palette_trials;
   {
-    const uint4 h = reinterpret_cast<const uint4*>(m.img0)[0];  // previous image header (still staged)
+    const uint4 h = reinterpret_cast<const uint4*>(m.img0)[0];  // the pre-gate image header (still staged)
     sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
     sel.prev_len = b0;
   }
-  // both chunks in one pass when neither needs the Solution D trial, the network or
-  // 64-bit widths; otherwise (or if a chunk holds a subnormal) chunk by chunk
-  const bool enc_paired = paired && S <= 32u && L.selector != 2 && !L.trace && (L.modes >> M_SPLIT) == 0u &&
-                          encode_pair32<VPT>(m.tile0, m.tile1, kc, S, L.modes, m.img0, m.img1, cap, *m.s, st.pp,
+  // both chunks in one pass when neither needs a SPLIT or PALETTE trial, a training
+  // record or 64-bit widths; otherwise (or if a chunk holds a subnormal) chunk by chunk
+  const bool enc_paired = paired && S <= 32u && !L.trace && ((md0 | md1) >> M_SPLIT) == 0u &&
+                          encode_pair32<VPT>(m.tile0, m.tile1, kc, S, md0, m.img0, m.img1, cap, *m.s, st.pp,
                                              &ctl->err, n0, n1);
   if (!enc_paired) {
-    n0 = encode_block<VPT>(m.tile0, kc, S, -1, L.modes, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
+    n0 = encode_block<VPT>(m.tile0, kc, S, -1, md0, m.img0, cap, *m.s, st.pp, &ctl->err, &sel);
     if (has1) {
       const uint4 h = reinterpret_cast<const uint4*>(m.img1)[0];
       sel.prev_hdr[0] = h.x; sel.prev_hdr[1] = h.y; sel.prev_hdr[2] = h.z; sel.prev_hdr[3] = h.w;
       sel.prev_len = b1;
-      n1 = encode_block<VPT>(m.tile1, kc, S, -1, L.modes, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
+      n1 = encode_block<VPT>(m.tile1, kc, S, -1, md1, m.img1, cap, *m.s, st.pp, &ctl->err, &sel);
     }
   }
   QC_PHASE(3);
@@ -559,7 +552,6 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS) k_
   st.cc.n = &s_cache_n;
   st.acc = &s_acc;
   cta_begin(L.P, st, L.prof, s_ph);
-  load_selector(L, m);
   const uint32_t S = gate_bits(L);
   const unsigned long long serial = L.P.ctl->gates + 1ull;
   const bool bc_on = L.bc != nullptr && L.P.ctl->bc_off == 0u;
@@ -610,7 +602,6 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
       cur = lo;
       __syncthreads();  // the previous job's items are done with the shared parameters
       cta_begin(jobs[cur].L.P, st, jobs[cur].L.prof, s_ph);
-      load_selector(jobs[cur].L, m);
       S = gate_bits(jobs[cur].L);
       serial = jobs[cur].L.P.ctl->gates + 1ull;
       bc_on = jobs[cur].L.bc != nullptr && jobs[cur].L.P.ctl->bc_off == 0u;

@@ -27,8 +27,8 @@ struct GateLaunch {
   int pair;                      // 1: target >= chunk_log2
   int prof;                      // 1: accumulate per-phase SM cycles
   uint32_t modes;                // chunk modes the encoder may choose (bit m = mode m)
-  int selector;                  // 0: the mode set decides; 2: the selector network decides SPLIT trials
-  const unsigned short* mlp;     // selector parameters (bfloat16, device)
+  const uint8_t* sel_dec;        // the selector's decisions, one byte per active chunk (index 2 item + side;
+                                 // bit 0 SPLIT trial, bit 1 PALETTE trial), or nullptr: the mode set decides
   uint32_t gfeat;                // gate features for the selector (see SelCtx)
   float* trace;                  // selector training records (device) or nullptr
   unsigned long long* trace_n;
@@ -77,6 +77,10 @@ int fast_pairs();        // work items a CTA of the streaming kernel runs at onc
 int fast_warp_cache();   // page ids each of its warps may hold
 cudaError_t launch_gate_fast(const GateLaunch& L, int grid, cudaStream_t st);
 cudaError_t launch_post(const Pool& P, const CtlParams& cp, int grid_ctas, cudaStream_t st);
+// The learned selector's decisions for every active chunk of the gate L describes,
+// written to dec (one byte per chunk, index 2 item + side) before the gate runs; mlp
+// holds the bfloat16 parameters (device, 16-byte aligned).
+cudaError_t launch_select(const GateLaunch& L, const unsigned short* mlp, uint8_t* dec, int grid, cudaStream_t st);
 cudaError_t launch_gate_batch(const BatchJob* jobs, int njobs, unsigned long long total, int kc, int grid,
                               cudaStream_t st);
 cudaError_t launch_post_batch(const BatchJob* jobs, int njobs, int grid_ctas, cudaStream_t st);

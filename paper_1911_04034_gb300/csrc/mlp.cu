@@ -4,9 +4,9 @@
 // bfloat16 weights.  Training keeps float32 master weights; every step rounds them
 // to bfloat16, runs the forward and backward passes over a minibatch with float32
 // arithmetic (one thread per sample, gradients summed in shared memory, then across
-// blocks), and applies an Adam update.  Loss: softmax cross-entropy of the six mode
-// logits against the mode the exhaustive trial chose, plus the squared error of
-// outputs 6 and 7 against the STREAM and SPLIT image sizes (fractions of RAW).
+// blocks), and applies an Adam update.  Loss: softmax cross-entropy of the seven mode
+// logits (outputs 0..6) against the mode the exhaustive trial chose, plus the squared
+// error of the bit budget (output 7) against the best image's size over the RAW size.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -16,7 +16,7 @@
 
 namespace {
 
-constexpr int NIN = 16, NH = 32, NOUT = 8, NMODES = 6;
+constexpr int NIN = 16, NH = 32, NOUT = 8, NMODES = 7, NSIZE = NOUT - NMODES;
 constexpr int OW1 = 0, OB1 = 512, OW2 = 544, OB2 = 1568, OW3 = 1600, OB3 = 1856, NP = 1864;
 static_assert(NP == qc::kMlpParams, "parameter layout");
 
@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ wq, 
     float dout[NOUT];
     float l = -(o[y] - mx - logf(se));
     for (int m = 0; m < NMODES; ++m) dout[m] = (expf(o[m] - mx) / se - (m == y ? 1.0f : 0.0f)) * inv_b;
-    for (int k = 0; k < 2; ++k) {
-      const float d = o[NMODES + k] - sizes[smp * 2 + k];
+    for (int k = 0; k < NSIZE; ++k) {
+      const float d = o[NMODES + k] - sizes[smp * NSIZE + k];
       l += d * d;
       dout[NMODES + k] = 2.0f * d * inv_b;
     }
@@ -155,7 +155,7 @@ sim_status mlp_fail(sim_status s, const char* msg) {
     if (e_ != cudaSuccess) return mlp_fail(SIM_ERR_CUDA, cudaGetErrorString(e_)); \
   } while (0)
 
-// Copies the training set to the device; layout: x (n*16 f32), sizes (n*2 f32),
+// Copies the training set to the device; layout: x (n*16 f32), sizes (n*NSIZE f32),
 // mode (n i32), idx (n i32), grad (NP), loss (1), wq (NP), w, m, v (NP each).
 struct TrainSet {
   DevBuf buf;
@@ -164,12 +164,12 @@ struct TrainSet {
 };
 
 sim_status upload(TrainSet& T, const float* x, const int32_t* mode, const float* sizes, uint64_t n) {
-  const size_t fl = (size_t)n * (NIN + 2) + 5 * NP + 1, in = (size_t)n * 2;
+  const size_t fl = (size_t)n * (NIN + NSIZE) + 5 * NP + 1, in = (size_t)n * 2;
   MCK(cudaMalloc(&T.buf.p, fl * 4 + in * 4 + 64));
   float* f = static_cast<float*>(T.buf.p);
   T.x = f;
   T.sizes = T.x + n * NIN;
-  T.grad = T.sizes + n * 2;
+  T.grad = T.sizes + n * NSIZE;
   T.loss = T.grad + NP;
   T.wq = T.loss + 1;
   T.w = T.wq + NP;
@@ -178,7 +178,7 @@ sim_status upload(TrainSet& T, const float* x, const int32_t* mode, const float*
   T.mode = reinterpret_cast<int*>(T.v + NP);
   T.idx = T.mode + n;
   MCK(cudaMemcpy(T.x, x, n * NIN * 4, cudaMemcpyHostToDevice));
-  MCK(cudaMemcpy(T.sizes, sizes, n * 2 * 4, cudaMemcpyHostToDevice));
+  MCK(cudaMemcpy(T.sizes, sizes, n * NSIZE * 4, cudaMemcpyHostToDevice));
   MCK(cudaMemcpy(T.mode, mode, n * 4, cudaMemcpyHostToDevice));
   return SIM_OK;
 }
@@ -192,7 +192,7 @@ sim_status sim_mlp_grad(const float* params, const float* x, const int32_t* mode
   if (!params || !x || !mode || !sizes || !grad_out || n == 0 || n > (1ull << 26))
     return mlp_fail(SIM_ERR_INVALID, "bad arguments");
   for (uint64_t i = 0; i < n; ++i)
-    if (mode[i] < 0 || mode[i] >= NMODES) return mlp_fail(SIM_ERR_INVALID, "mode label outside 0..5");
+    if (mode[i] < 0 || mode[i] >= NMODES) return mlp_fail(SIM_ERR_INVALID, "mode label outside 0..6");
   TrainSet T;
   if (sim_status r = upload(T, x, mode, sizes, n)) return r;
   std::vector<int> idx(n);
@@ -216,7 +216,7 @@ sim_status sim_mlp_train(const float* x, const int32_t* mode, const float* sizes
   if (!x || !mode || !sizes || !params || n == 0 || n > (1ull << 26) || epochs < 1 || batch < 1 || !(lr > 0.0f))
     return mlp_fail(SIM_ERR_INVALID, "bad arguments");
   for (uint64_t i = 0; i < n; ++i)
-    if (mode[i] < 0 || mode[i] >= NMODES) return mlp_fail(SIM_ERR_INVALID, "mode label outside 0..5");
+    if (mode[i] < 0 || mode[i] >= NMODES) return mlp_fail(SIM_ERR_INVALID, "mode label outside 0..6");
   TrainSet T;
   if (sim_status r = upload(T, x, mode, sizes, n)) return r;
   MCK(cudaMemcpy(T.w, params, NP * 4, cudaMemcpyHostToDevice));

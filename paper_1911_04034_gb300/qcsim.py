@@ -43,6 +43,7 @@ class Stats(C.Structure):
         ("split_trials", C.c_uint64),
         ("cache_lookups", C.c_uint64), ("cache_hits", C.c_uint64),
         ("fast_items", C.c_uint64), ("fast_deferred", C.c_uint64), ("kernel_launches", C.c_uint64),
+        ("palette_trials", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -203,8 +204,9 @@ class Sim:
         _check(lib().sim_set_modes(self._h, int(modes)), "sim_set_modes")
 
     def set_selector(self, selector: int, bf16_params=None) -> None:
-        """0 Solution C only, 1 Solution C and D exhaustively, 2 C and D with the
-        selector network deciding the D trials (bf16_params: 1864 uint16)."""
+        """0 the mode set (default Solution C), 1 every mode with the SPLIT and PALETTE
+        trials on every chunk (exhaustive), 2 Solution C plus the trials the selector
+        network grants each chunk before the gate (bf16_params: 1864 uint16)."""
         p = None
         if bf16_params is not None:
             p = np.ascontiguousarray(bf16_params, dtype=np.uint16)
