@@ -98,6 +98,9 @@ typedef struct sim_stats_t {
   uint64_t fast_deferred;     /* work items it left to the general gate kernel (cumulative) */
   uint64_t kernel_launches;   /* kernels the gates enqueued (selector, streaming, general and post kernels) */
   uint64_t palette_trials;    /* chunk encodes that ran the PALETTE trial */
+  uint64_t graph_replays;     /* sim_batch_apply calls led by this handle that replayed its kept graph */
+  int32_t ladder;             /* the controller's bound ladder (0 jump, 1 the paper's, 2 guarded) */
+  uint32_t modes;             /* the mode set of sim_set_modes / sim_set_selector */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2
@@ -128,6 +131,14 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
 /* Frees every device allocation of the handle (after synchronising its stream). */
 sim_status sim_destroy(sim_t* sim);
 
+/* Puts the handle back to the state sim_create_ex left it in: |0...0> (chunk 0 coded
+ * losslessly, every other chunk ZERO), the lossless stage, every statistic of the run
+ * and device counter zero (graph_replays counts on), the block-cache lines empty.  Keeps the allocations and the settings
+ * (modes, selector, block cache, fast path, stream, budget).  Synchronises the handle's
+ * stream.  Lets a serving loop run circuit after circuit on the same handles, and the
+ * batched path replay its cached graph. */
+sim_status sim_reset(sim_t* sim);
+
 /* Uses `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
  * for all later work of this handle.  The caller keeps the stream alive. */
 sim_status sim_set_stream(sim_t* sim, void* cuda_stream);
@@ -138,30 +149,34 @@ sim_status sim_set_stream(sim_t* sim, void* cuda_stream);
 sim_status sim_apply_gate(sim_t* sim, const sim_gate* gate);
 
 /* Applies n_gates gates in order.  All gates are validated first (none runs if one
- * is invalid).  `gates` is a host array.  The launches of the sequence are captured
- * once into a CUDA graph and replayed.  Synchronises the stream at the end and
+ * is invalid).  `gates` is a host array.  Synchronises the stream at the end and
  * returns any device-side error. */
 sim_status sim_apply_circuit(sim_t* sim, const sim_gate* gates, size_t n_gates);
 
 /* Batched form: runs `count` circuits, circuits[k] (n_gates[k] gates) on handle
  * sims[k], together.  Gate step t applies gate t of every circuit that has one with a
  * single fused-kernel launch covering the work items of all of them (and one
- * bookkeeping launch); with use_graph != 0 the whole launch sequence is captured once
- * into a CUDA graph and replayed.  Each handle keeps its own pool, controller and
- * statistics, and ends in exactly the state sim_apply_circuit would give it.  The
+ * bookkeeping launch); with use_graph != 0 the whole launch sequence is captured into a
+ * CUDA graph, launched, and kept by sims[0]: a later call whose launches are the same
+ * (same handles and settings, same gates; e.g. after sim_reset) replays it without
+ * capturing or uploading again (sim_stats_t.graph_replays).  Each handle keeps its own
+ * pool, controller and statistics, and ends in exactly the state sim_apply_circuit
+ * would give it.  The
  * handles must be distinct and share chunk_log2; launches go to sims[0]'s stream.
  * All gates are validated first.  Synchronises; returns the first device error. */
 sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const* circuits, const size_t* n_gates,
                            int use_graph);
 
 /* Runs n_circ independent circuits (n_qubits[k] qubits, circ[k][0..n_gates[k]) each)
- * through the batched path and writes each one's statistics to out[k]: one chunk size
- * for the batch (autotuned among 8..10 on the largest circuit when it has at least 4
- * gates and every circuit has at least 8 qubits; else min(10, smallest n)), blocks of
- * 2^min(n, 20), bound err_bound reached after the lossless stage at budget raw/4, page
- * pool raw + 1/8 + 8 MiB, the gates advanced one step at a time across all circuits in
- * one persistent launch replayed from a CUDA graph (sim_batch_apply).  The handles are
- * created and destroyed inside the call.  Errors as sim_create_ex / sim_batch_apply. */
+ * through the batched path and writes each one's statistics to out[k].  One setting
+ * for the batch, from sim_autotune on the largest circuit when it has at least 4
+ * gates and every circuit at least 8 qubits (blocks 2^10..2^16, chunks 2^8..2^10 up to
+ * the smallest circuit, ladders 0..2, mode sets Solution C and Solution C + PALETTE);
+ * else blocks 2^20, chunks 2^min(10, smallest n), the jump ladder, Solution C.  Bound
+ * err_bound after the lossless stage at budget raw/4, page pool raw + 1/8 + 8 MiB, the
+ * gates advanced one step at a time across all circuits in one persistent launch
+ * replayed from a CUDA graph (sim_batch_apply).  The handles are created and destroyed
+ * inside the call.  Errors as sim_create_ex / sim_autotune / sim_batch_apply. */
 sim_status sim_batch_run(int n_circ, const int* n_qubits, const sim_gate* const* circ, const size_t* n_gates,
                          double err_bound, sim_stats_t* out);
 
@@ -171,6 +186,32 @@ sim_status sim_batch_run(int n_circ, const int* n_qubits, const sim_gate* const*
  * updates per second of kernel time, rates[i] (if not NULL) each candidate's rate. */
 sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,
                               const int* candidates, int n_candidates, int* best, double* rates);
+
+/* One point of the autotuner's search space and what it measured. */
+typedef struct {
+  int32_t block_log2;      /* blocks of 2^block_log2 amplitudes (Section 3.1; the controller's in-flight bytes) */
+  int32_t chunk_log2;      /* the coding tile: 2^chunk_log2 amplitudes decoded and encoded as one unit */
+  int32_t ladder;          /* codec schedule: bound ladder 0 jump, 1 the paper's ladder, 2 guarded */
+  uint32_t modes;          /* codec schedule: the chunk modes the encoder may choose */
+  double rate;             /* amplitude updates per second of gate-kernel time over the probe's second half */
+  double ratio;            /* raw bytes over the peak encoded bytes of the probe run */
+  double fidelity_lb_sum;  /* the probe run's provable fidelity bound */
+} sim_tune_point;
+
+/* Autotuner over block size, tile size and codec schedule: coordinate descent from the
+ * first value of each list, sweeping the chunk sizes, then the block sizes, the
+ * ladders and the mode sets with the other settings at their best so far, until a
+ * sweep changes nothing (3 sweeps at most).  Each point is measured as in
+ * sim_autotune_chunk: a fresh handle (budget raw/4, pool raw + 1/8 + 64 MiB) runs the
+ * first half of the probe, then the second half with gate-kernel timing; the best
+ * point has the highest rate (every point keeps the bound err_bound).  Blocks clamp to
+ * n_qubits and chunks to the block, as sim_create_ex does; points that coincide after
+ * clamping are measured once.  *best receives the winner; tried (cap_tried entries,
+ * may be NULL) every measured point in order, *n_tried (may be NULL) their number. */
+sim_status sim_autotune(int n_qubits, double err_bound, const sim_gate* probe, size_t n_probe,
+                        const int32_t* block_log2s, int n_b, const int32_t* chunk_log2s, int n_c, const int32_t* ladders,
+                        int n_l, const uint32_t* mode_sets, int n_m, sim_tune_point* best, sim_tune_point* tried,
+                        size_t cap_tried, size_t* n_tried);
 
 /* Changes the budget the controller compares with (Section 3.7; threshold floor(tau *
  * bytes)) from the next gate on; the page arena keeps the size it was created with.

@@ -6,6 +6,7 @@
 // has no remote-rank segment).  A control on a chunk-index bit removes whole chunks
 // from the work (the paper's block-level skip); controls below kc are tested per
 // amplitude pair inside the kernel.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -158,6 +159,24 @@ struct sim {
   bool fast = true;                  // gates try the streaming kernel first
   uint64_t kernel_launches = 0;      // gate, streaming and post kernels enqueued
   uint64_t trace_cap = 0;
+  // the graph of the last sim_batch_apply call this handle led, kept for replay
+  cudaGraphExec_t bexec = nullptr;
+  qc::BatchJob* bjobs = nullptr;     // its job list (device)
+  std::vector<uint8_t> bkey;         // what its launches depend on
+  std::vector<uint64_t> bupd;        // the amplitude updates it makes, per handle
+  uint64_t uid = 0;                  // creation number (never reused)
+  uint64_t cfg_gen = 0;              // bumped by every setting that can change a gate's launch
+  cudaStream_t bstream = nullptr;    // private capture / replay stream
+  cudaEvent_t bready = nullptr;
+  uint64_t graph_replays = 0;
+  void drop_graph() {
+    if (bexec) cudaGraphExecDestroy(bexec);
+    cudaFree(bjobs);
+    bexec = nullptr;
+    bjobs = nullptr;
+    bkey.clear();
+    bupd.clear();
+  }
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   size_t ev_next = 0;
@@ -166,6 +185,9 @@ struct sim {
   unsigned long long t_bytes_in0 = 0, t_bytes_out0 = 0;
 
   ~sim() {
+    drop_graph();
+    if (bready) cudaEventDestroy(bready);
+    if (bstream) cudaStreamDestroy(bstream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     cudaFree(d_tlog);
     cudaFree(d_defer);
@@ -259,6 +281,8 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
   s->budget = budget;
   s->ladder = ladder;
   s->nchunks = 1ull << (s->n - s->kc);
+  static std::atomic<uint64_t> creations{0};
+  s->uid = ++creations;
 
   // controller parameters (Section 3.7, Eq. totalnbBytes with r = 1)
   CtlParams& cp = s->cp;
@@ -298,6 +322,20 @@ sim_status sim_create_ex(int n_qubits, int block_log2, int chunk_log2, double er
   if (s->npages >= (1ull << 32)) {
     delete s;
     return fail(SIM_ERR_INVALID, "budget too large for 32-bit page ids");
+  }
+  if (s->fast_grid) {
+    // no more CTAs of the streaming kernel than the largest gate has items for, and,
+    // in a pool sized by the caller, no more than let its warps' free-page caches (each
+    // up to its capacity plus one refill, and one chunk's output pages) hold a quarter
+    // of the pool; none if not even one CTA fits
+    const uint64_t need = ((s->nchunks + 1) / 2 + qc::fast_pairs() - 1) / qc::fast_pairs();
+    uint64_t cap = need;
+    if (pool_bytes) {
+      const uint64_t per_cta = (uint64_t)qc::fast_warps() * (qc::fast_warp_cache() + 32 + qc::max_pages(s->kc));
+      const uint64_t fit = s->npages / 4 / per_cta;
+      cap = fit < cap ? fit : cap;
+    }
+    s->fast_grid = (uint64_t)s->fast_grid < cap ? s->fast_grid : (int)cap;
   }
   Pool& P = s->P;
   P.kc = s->kc;
@@ -378,6 +416,30 @@ sim_status sim_destroy(sim_t* s) {
   cudaStreamSynchronize(s->st);
   delete s;
   return SIM_OK;
+}
+
+sim_status sim_reset(sim_t* s) {
+  if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
+  if (sim_status r = s->guard()) return r;
+  DevCtl h{};
+  h.top = (long long)s->npages;
+  h.switch_gate = -1;
+  h.lb_prod = 1.0;
+  h.S_last = 64;
+  const size_t nwc = (size_t)(s->fast_grid ? s->fast_grid : 1) * qc::fast_warps();
+  cudaError_t e = cudaMemcpyAsync(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->P.cache_n, 0, (size_t)s->grid * 4, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->P.wcache_n, 0, nwc * 4, s->st);
+  if (e == cudaSuccess && s->d_bc)  // lines are tagged by gate serial, which starts over
+    e = cudaMemsetAsync(s->d_bc, 0, (size_t)qc::kBcLines * qc::bc_line_bytes(qc::round16(qc::max_image_bytes(s->kc))),
+                        s->st);
+  if (e == cudaSuccess) e = qc::launch_pool_init(s->P, s->nchunks, s->st);
+  if (e == cudaSuccess) e = qc::launch_init_chunk0(s->P, s->nchunks, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);  // h is read from the host stack
+  if (e != cudaSuccess) return cuda_fail(e, "reset");
+  s->amp_updates = 0;
+  s->kernel_launches = 0;
+  return s->check_device();
 }
 
 sim_status sim_set_stream(sim_t* s, void* stream) {
@@ -580,6 +642,7 @@ static sim_status read_traffic(sim* s, unsigned long long* in, unsigned long lon
 }
 
 sim_status sim_set_timing(sim_t* s, int on) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
   CK(cudaStreamSynchronize(s->st), "sync");
   s->timing = on != 0;
@@ -638,6 +701,7 @@ sim_status sim_timing(sim_t* s, double* ms, uint64_t* launches, uint64_t* bytes_
 }
 
 sim_status sim_set_budget(sim_t* s, uint64_t bytes) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
   if (bytes == 0) return fail(SIM_ERR_INVALID, "budget must be > 0");
   if (sim_status r = s->guard()) return r;
@@ -648,6 +712,7 @@ sim_status sim_set_budget(sim_t* s, uint64_t bytes) {
 }
 
 sim_status sim_set_option(sim_t* s, const char* key, int64_t value) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s || !key) return fail(SIM_ERR_INVALID, "NULL argument");
   if (sim_status r = s->guard()) return r;
   const std::string k(key);
@@ -700,6 +765,7 @@ sim_status sim_set_option(sim_t* s, const char* key, int64_t value) {
 }
 
 sim_status sim_set_block_cache(sim_t* s, int on) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s) return fail(SIM_ERR_INVALID, "NULL argument");
   if (sim_status r = s->guard()) return r;
   CK(cudaStreamSynchronize(s->st), "sync");
@@ -722,6 +788,7 @@ sim_status sim_set_block_cache(sim_t* s, int on) {
 }
 
 sim_status sim_set_modes(sim_t* s, uint32_t modes) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
   if ((modes & qc::kDefaultModes) != qc::kDefaultModes || (modes >> qc::M_NMODES))
     return fail(SIM_ERR_INVALID, "the mode set must contain ZERO..RAW (0x1F) and only known modes");
@@ -730,6 +797,7 @@ sim_status sim_set_modes(sim_t* s, uint32_t modes) {
 }
 
 sim_status sim_set_selector(sim_t* s, int selector, const uint16_t* bf16_params) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
   if (selector < 0 || selector > 2) return fail(SIM_ERR_INVALID, "selector must be 0, 1 or 2");
   if (selector == 2) {
@@ -744,6 +812,7 @@ sim_status sim_set_selector(sim_t* s, int selector, const uint16_t* bf16_params)
 }
 
 sim_status sim_trace(sim_t* s, uint64_t capacity) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s) return fail(SIM_ERR_INVALID, "NULL handle");
   CK(cudaStreamSynchronize(s->st), "sync");
   cudaFree(s->d_trace);
@@ -918,6 +987,9 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->fast_deferred = h.fast_deferred;
   o->kernel_launches = s->kernel_launches;
   o->palette_trials = h.palette_trials;
+  o->graph_replays = s->graph_replays;
+  o->ladder = s->ladder;
+  o->modes = s->modes;
   if (h.err) return s->check_device();
   return SIM_OK;
 }
@@ -959,81 +1031,118 @@ sim_status sim_batch_apply(sim_t* const* sims, int count, const sim_gate* const*
     if (n_gates[k] > steps) steps = n_gates[k];
   }
   if (steps == 0) return SIM_OK;
-  // step t holds gate t of every circuit that has one; its jobs' items are numbered
-  // consecutively
-  std::vector<qc::BatchJob> jobs;
-  std::vector<sim*> job_sim;  // the handle of each job
-  std::vector<size_t> off(steps + 1, 0);
-  std::vector<unsigned long long> total(steps, 0);
-  int grid = sims[0]->grid;
-  for (int k = 1; k < count; ++k) grid = sims[k]->grid < grid ? sims[k]->grid : grid;
-  for (size_t t = 0; t < steps; ++t) {
-    off[t] = jobs.size();
-    unsigned long long begin = 0;
-    for (int k = 0; k < count; ++k) {
-      if (t >= n_gates[k]) continue;
-      qc::BatchJob j;
-      j.L = make_launch(sims[k], circuits[k] + t);
-      j.begin = begin;
-      begin += j.L.items;
-      jobs.push_back(j);
-      job_sim.push_back(sims[k]);
-    }
-    total[t] = begin;
-  }
-  off[steps] = jobs.size();
   cudaStream_t st = sims[0]->st;
-  qc::BatchJob* d_jobs = nullptr;
-  CK(cudaMalloc(&d_jobs, jobs.size() * sizeof(qc::BatchJob)), "batch job list");
-  cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(qc::BatchJob), cudaMemcpyHostToDevice, st);
-  // A graph is captured on a private stream (the legacy default stream cannot be
-  // captured), ordered after the work already queued on the handles' stream.
-  cudaStream_t cs = st;
-  cudaEvent_t ready = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  if (e == cudaSuccess && use_graph) {
-    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ready, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-  }
-  for (size_t t = 0; t < steps && e == cudaSuccess; ++t) {
-    const int n = (int)(off[t + 1] - off[t]);
-    const int g = (unsigned long long)grid < total[t] ? grid : (int)total[t];
-    // the selector's decisions of every handle that runs the network, before the step
-    for (size_t j = off[t]; j < off[t + 1] && e == cudaSuccess; ++j) {
-      const GateLaunch& L = jobs[j].L;
-      if (!L.sel_dec) continue;
-      const unsigned long long na = L.pair ? 2ull * L.items : L.nact;
-      const int sg = (unsigned long long)grid < (na + 255ull) / 256ull ? grid : (int)((na + 255ull) / 256ull);
-      e = qc::launch_select(L, job_sim[j]->d_mlp, const_cast<uint8_t*>(L.sel_dec), sg, cs);
+  sim* lead = sims[0];
+  // What the launch sequence depends on: the handles (by creation number, so that a
+  // new handle at a freed address never matches) with the generation of their
+  // settings, and the gates.  A call with the same key makes the same launches, so the
+  // graph the lead handle kept can be replayed as it stands.
+  std::vector<uint8_t> key;
+  if (use_graph) {
+    auto put = [&key](const void* p, size_t n) {
+      const uint8_t* b = static_cast<const uint8_t*>(p);
+      key.insert(key.end(), b, b + n);
+    };
+    put(&count, sizeof count);
+    for (int k = 0; k < count; ++k) {
+      put(&sims[k]->uid, sizeof(uint64_t));
+      put(&sims[k]->cfg_gen, sizeof(uint64_t));
+      put(&n_gates[k], sizeof(size_t));
     }
-    if (e == cudaSuccess) e = qc::launch_gate_batch(d_jobs + off[t], n, total[t], kc, g, cs);
-    if (e == cudaSuccess) e = qc::launch_post_batch(d_jobs + off[t], n, grid, cs);
+    for (int k = 0; k < count; ++k) put(circuits[k], n_gates[k] * sizeof(sim_gate));
   }
-  if (use_graph && cs != st) {
-    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cudaError_t e = cudaSuccess;
+  std::vector<uint64_t> upd(count, 0);  // amplitude updates each circuit makes
+  if (use_graph && lead->bexec && key == lead->bkey) {
+    // the job list is still on the device, unchanged: launch the instantiated graph
+    upd = lead->bupd;
+    e = cudaEventRecord(lead->bready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(lead->bstream, lead->bready, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(lead->bexec, lead->bstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lead->bstream);
+    if (e == cudaSuccess) ++lead->graph_replays;
+  } else {
+    if (use_graph) lead->drop_graph();
+    // step t holds gate t of every circuit that has one; its jobs' items are numbered
+    // consecutively
+    std::vector<qc::BatchJob> jobs;
+    std::vector<sim*> job_sim;  // the handle of each job
+    std::vector<size_t> off(steps + 1, 0);
+    std::vector<unsigned long long> total(steps, 0);
+    int grid = sims[0]->grid;
+    for (int k = 1; k < count; ++k) grid = sims[k]->grid < grid ? sims[k]->grid : grid;
+    for (size_t t = 0; t < steps; ++t) {
+      off[t] = jobs.size();
+      unsigned long long begin = 0;
+      for (int k = 0; k < count; ++k) {
+        if (t >= n_gates[k]) continue;
+        qc::BatchJob j;
+        j.L = make_launch(sims[k], circuits[k] + t);
+        j.begin = begin;
+        begin += j.L.items;
+        upd[k] += j.L.nact << sims[k]->kc;
+        jobs.push_back(j);
+        job_sim.push_back(sims[k]);
+      }
+      total[t] = begin;
+    }
+    off[steps] = jobs.size();
+    qc::BatchJob* d_jobs = nullptr;
+    CK(cudaMalloc(&d_jobs, jobs.size() * sizeof(qc::BatchJob)), "batch job list");
+    e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(qc::BatchJob), cudaMemcpyHostToDevice, st);
+    // A graph is captured on a private stream (the legacy default stream cannot be
+    // captured), ordered after the work already queued on the handles' stream.
+    cudaStream_t cs = st;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && use_graph) {
+      if (!lead->bstream) e = cudaStreamCreateWithFlags(&lead->bstream, cudaStreamNonBlocking);
+      if (e == cudaSuccess && !lead->bready) e = cudaEventCreateWithFlags(&lead->bready, cudaEventDisableTiming);
+      if (e == cudaSuccess) cs = lead->bstream;
+      if (e == cudaSuccess) e = cudaEventRecord(lead->bready, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, lead->bready, 0);
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    }
+    for (size_t t = 0; t < steps && e == cudaSuccess; ++t) {
+      const int n = (int)(off[t + 1] - off[t]);
+      const int g = (unsigned long long)grid < total[t] ? grid : (int)total[t];
+      // the selector's decisions of every handle that runs the network, before the step
+      for (size_t j = off[t]; j < off[t + 1] && e == cudaSuccess; ++j) {
+        const GateLaunch& L = jobs[j].L;
+        if (!L.sel_dec) continue;
+        const unsigned long long na = L.pair ? 2ull * L.items : L.nact;
+        const int sg = (unsigned long long)grid < (na + 255ull) / 256ull ? grid : (int)((na + 255ull) / 256ull);
+        e = qc::launch_select(L, job_sim[j]->d_mlp, const_cast<uint8_t*>(L.sel_dec), sg, cs);
+      }
+      if (e == cudaSuccess) e = qc::launch_gate_batch(d_jobs + off[t], n, total[t], kc, g, cs);
+      if (e == cudaSuccess) e = qc::launch_post_batch(d_jobs + off[t], n, grid, cs);
+    }
+    if (use_graph && cs != st) {
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess && exec) {
+      // kept for the next call with the same key (the job list stays with it)
+      lead->bexec = exec;
+      lead->bjobs = d_jobs;
+      lead->bkey.swap(key);
+      lead->bupd = upd;
+    } else {
+      if (exec) cudaGraphExecDestroy(exec);
+      cudaFree(d_jobs);
+    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (ready) cudaEventDestroy(ready);
-  if (cs != st) cudaStreamDestroy(cs);
-  cudaFree(d_jobs);
   if (e != cudaSuccess) {
     for (int k = 0; k < count; ++k) sims[k]->poisoned = SIM_ERR_CUDA;
     return cuda_fail(e, "batched launch");
   }
-  for (int k = 0; k < count; ++k) {
-    const uint64_t A = 1ull << sims[k]->kc;
-    for (size_t i = 0; i < n_gates[k]; ++i) sims[k]->amp_updates += make_launch(sims[k], circuits[k] + i).nact * A;
-  }
+  for (int k = 0; k < count; ++k) sims[k]->amp_updates += upd[k];
   sim_status worst = SIM_OK;
   for (int k = 0; k < count; ++k) {
     sim_status r = sims[k]->check_device();
@@ -1051,23 +1160,31 @@ sim_status sim_batch_run(int n_circ, const int* n_qubits, const sim_gate* const*
     if (n_qubits[k] < nmin) nmin = n_qubits[k];
     if (n_qubits[k] > n_qubits[big] || (n_qubits[k] == n_qubits[big] && n_gates[k] > n_gates[big])) big = k;
   }
-  // one chunk size for the whole batch, autotuned on the largest circuit when it is long enough
-  int kc = nmin < 10 ? nmin : 10;
+  // one setting for the whole batch, autotuned on the largest circuit when it is long
+  // enough: block size 2^10..2^16, chunk (tile) size 2^8..2^10, bound ladder, mode set
+  sim_tune_point cfg{};
+  cfg.block_log2 = 20;
+  cfg.chunk_log2 = nmin < 10 ? nmin : 10;
+  cfg.ladder = 0;
+  cfg.modes = qc::kDefaultModes;
   if (n_gates[big] >= 4 && nmin >= 8) {
-    int cand[3], nc = 0;
-    for (int c = 8; c <= 10 && c <= nmin; ++c) cand[nc++] = c;
-    if (nc > 1) {
-      const int nb = n_qubits[big] < 20 ? n_qubits[big] : 20;
-      if (sim_status r = sim_autotune_chunk(n_qubits[big], nb, err_bound, circ[big], n_gates[big], cand, nc, &kc, nullptr))
-        return r;
-    }
+    const int32_t bs[7] = {16, 10, 11, 12, 13, 14, 15}, ls[3] = {0, 1, 2};
+    const uint32_t ms[2] = {qc::kDefaultModes, qc::kDefaultModes | (1u << qc::M_PALETTE)};
+    int32_t cs[3];
+    int nc = 0;
+    for (int c = 10; c >= 8 && nc < 3; --c)
+      if (c <= nmin) cs[nc++] = c;
+    if (sim_status r = sim_autotune(n_qubits[big], err_bound, circ[big], n_gates[big], bs, 7, cs, nc, ls, 3, ms, 2, &cfg,
+                                    nullptr, 0, nullptr))
+      return r;
   }
   std::vector<sim_t*> sims(n_circ, nullptr);
   sim_status r = SIM_OK;
   for (int k = 0; k < n_circ && r == SIM_OK; ++k) {
     const uint64_t raw = 16ull << n_qubits[k];
-    const int b = n_qubits[k] < 20 ? n_qubits[k] : 20;
-    r = sim_create_ex(n_qubits[k], b, kc, err_bound, raw / 4 ? raw / 4 : 1, 0.9, 0, raw + raw / 8 + (8ull << 20), &sims[k]);
+    r = sim_create_ex(n_qubits[k], cfg.block_log2, cfg.chunk_log2, err_bound, raw / 4 ? raw / 4 : 1, 0.9, cfg.ladder,
+                      raw + raw / 8 + (8ull << 20), &sims[k]);
+    if (r == SIM_OK) r = sim_set_modes(sims[k], cfg.modes);
   }
   if (r == SIM_OK) r = sim_batch_apply(sims.data(), n_circ, circ, n_gates, 1);
   for (int k = 0; k < n_circ && r == SIM_OK; ++k) r = sim_stats(sims[k], &out[k]);
@@ -1076,34 +1193,125 @@ sim_status sim_batch_run(int n_circ, const int* n_qubits, const sim_gate* const*
   return r;
 }
 
+// One autotuner measurement: a handle with the point's settings (budget raw/4, pool
+// raw + 1/8 + 64 MiB) runs the first half of the probe untimed, then the second half
+// with gate-kernel timing; fills rate, ratio (raw over the peak encoded bytes) and the
+// fidelity bound.
+static sim_status tune_eval(int n_qubits, double err_bound, const sim_gate* probe, size_t n_probe, sim_tune_point& p) {
+  const uint64_t raw = 16ull << n_qubits;
+  sim_t* s = nullptr;
+  sim_status r = sim_create_ex(n_qubits, p.block_log2, p.chunk_log2, err_bound, raw / 4 ? raw / 4 : 1, 0.9, p.ladder,
+                               raw + raw / 8 + (64ull << 20), &s);
+  if (r != SIM_OK) return r;
+  r = sim_set_modes(s, p.modes);
+  const size_t half = n_probe / 2;
+  if (r == SIM_OK) r = sim_apply_circuit(s, probe, half);
+  if (r == SIM_OK) r = sim_set_timing(s, 1);
+  const uint64_t before = s->amp_updates;
+  if (r == SIM_OK) r = sim_apply_circuit(s, probe + half, n_probe - half);
+  double ms = 0.0;
+  if (r == SIM_OK) r = sim_timing(s, &ms, nullptr, nullptr, nullptr);
+  sim_stats_t st{};
+  if (r == SIM_OK) r = sim_stats(s, &st);
+  p.rate = (r == SIM_OK && ms > 0.0) ? (double)(s->amp_updates - before) / (ms * 1e-3) : 0.0;
+  p.ratio = st.min_ratio;
+  p.fidelity_lb_sum = st.fidelity_lb_sum;
+  sim_destroy(s);
+  return r;
+}
+
 sim_status sim_autotune_chunk(int n_qubits, int block_log2, double err_bound, const sim_gate* probe, size_t n_probe,
                               const int* candidates, int n_candidates, int* best, double* rates) {
   if (!probe || !candidates || !best || n_candidates < 1 || n_probe < 2)
     return fail(SIM_ERR_INVALID, "bad autotune arguments");
-  const uint64_t raw = 16ull << n_qubits;
   double best_rate = -1.0;
   *best = candidates[0];
   for (int i = 0; i < n_candidates; ++i) {
-    sim_t* s = nullptr;
-    sim_status r = sim_create_ex(n_qubits, block_log2, candidates[i], err_bound, raw / 4 ? raw / 4 : 1, 0.9, 0,
-                                 raw + raw / 8 + (64ull << 20), &s);
-    if (r != SIM_OK) return r;
-    const size_t half = n_probe / 2;
-    r = sim_apply_circuit(s, probe, half);
-    if (r == SIM_OK) r = sim_set_timing(s, 1);
-    const uint64_t before = s->amp_updates;
-    if (r == SIM_OK) r = sim_apply_circuit(s, probe + half, n_probe - half);
-    double ms = 0.0;
-    if (r == SIM_OK) r = sim_timing(s, &ms, nullptr, nullptr, nullptr);
-    const double rate = (r == SIM_OK && ms > 0.0) ? (double)(s->amp_updates - before) / (ms * 1e-3) : 0.0;
-    sim_destroy(s);
-    if (r != SIM_OK) return r;
-    if (rates) rates[i] = rate;
-    if (rate > best_rate) {
-      best_rate = rate;
+    sim_tune_point p{};
+    p.block_log2 = block_log2;
+    p.chunk_log2 = candidates[i];
+    p.ladder = 0;
+    p.modes = qc::kDefaultModes;
+    if (sim_status r = tune_eval(n_qubits, err_bound, probe, n_probe, p)) return r;
+    if (rates) rates[i] = p.rate;
+    if (p.rate > best_rate) {
+      best_rate = p.rate;
       *best = candidates[i];
     }
   }
+  return SIM_OK;
+}
+
+sim_status sim_autotune(int n_qubits, double err_bound, const sim_gate* probe, size_t n_probe,
+                        const int32_t* block_log2s, int n_b, const int32_t* chunk_log2s, int n_c, const int32_t* ladders,
+                        int n_l, const uint32_t* mode_sets, int n_m, sim_tune_point* best, sim_tune_point* tried,
+                        size_t cap_tried, size_t* n_tried) {
+  if (!probe || n_probe < 2 || !block_log2s || !chunk_log2s || !ladders || !mode_sets || n_b < 1 || n_c < 1 ||
+      n_l < 1 || n_m < 1 || !best || n_qubits < 1 || n_qubits > 40)
+    return fail(SIM_ERR_INVALID, "bad autotune arguments");
+  std::string why;
+  for (size_t i = 0; i < n_probe; ++i)
+    if (!gate_ok(probe + i, n_qubits, &why)) return fail(SIM_ERR_INVALID, "probe gate %zu: %s", i, why.c_str());
+  for (int i = 0; i < n_b; ++i)
+    if (block_log2s[i] < 0) return fail(SIM_ERR_INVALID, "block_log2 must be >= 0");
+  for (int i = 0; i < n_c; ++i)
+    if (chunk_log2s[i] < 0 || chunk_log2s[i] > 11) return fail(SIM_ERR_INVALID, "chunk_log2 must be in [0, 11]");
+  for (int i = 0; i < n_l; ++i)
+    if (ladders[i] < 0 || ladders[i] > 2) return fail(SIM_ERR_INVALID, "ladder must be 0, 1 or 2");
+  for (int i = 0; i < n_m; ++i)
+    if ((mode_sets[i] & qc::kDefaultModes) != qc::kDefaultModes || (mode_sets[i] >> qc::M_NMODES))
+      return fail(SIM_ERR_INVALID, "a mode set must contain 0x1F and only known modes");
+  // the settings as the handle applies them: blocks clamp to n, chunks to the block
+  auto canon = [n_qubits](sim_tune_point p) {
+    p.block_log2 = p.block_log2 < n_qubits ? p.block_log2 : n_qubits;
+    p.chunk_log2 = p.chunk_log2 < p.block_log2 ? p.chunk_log2 : p.block_log2;
+    return p;
+  };
+  std::vector<sim_tune_point> seen;
+  auto eval = [&](sim_tune_point p, sim_tune_point& out) -> sim_status {
+    p = canon(p);
+    for (const sim_tune_point& q : seen)
+      if (q.block_log2 == p.block_log2 && q.chunk_log2 == p.chunk_log2 && q.ladder == p.ladder && q.modes == p.modes) {
+        out = q;
+        return SIM_OK;
+      }
+    if (sim_status r = tune_eval(n_qubits, err_bound, probe, n_probe, p)) return r;
+    seen.push_back(p);
+    out = p;
+    return SIM_OK;
+  };
+  // coordinate descent from the first value of every axis: the tile (chunk) size, the
+  // block size, the bound ladder, the mode set; repeated until a sweep changes nothing
+  sim_tune_point cur{};
+  cur.block_log2 = block_log2s[0];
+  cur.chunk_log2 = chunk_log2s[0];
+  cur.ladder = ladders[0];
+  cur.modes = mode_sets[0];
+  if (sim_status r = eval(cur, cur)) return r;
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    const sim_tune_point start = cur;
+    for (int axis = 0; axis < 4; ++axis) {
+      const int n = axis == 0 ? n_c : axis == 1 ? n_b : axis == 2 ? n_l : n_m;
+      sim_tune_point pick = cur;
+      for (int i = 0; i < n; ++i) {
+        sim_tune_point p = cur;
+        if (axis == 0) p.chunk_log2 = chunk_log2s[i];
+        if (axis == 1) p.block_log2 = block_log2s[i];
+        if (axis == 2) p.ladder = ladders[i];
+        if (axis == 3) p.modes = mode_sets[i];
+        sim_tune_point got{};
+        if (sim_status r = eval(p, got)) return r;
+        if (got.rate > pick.rate) pick = got;
+      }
+      cur = pick;
+    }
+    if (cur.block_log2 == start.block_log2 && cur.chunk_log2 == start.chunk_log2 && cur.ladder == start.ladder &&
+        cur.modes == start.modes)
+      break;
+  }
+  *best = cur;
+  if (n_tried) *n_tried = seen.size();
+  for (size_t i = 0; tried && i < seen.size() && i < cap_tried; ++i) tried[i] = seen[i];
   return SIM_OK;
 }
 
@@ -1220,6 +1428,7 @@ sim_status sim_checkpoint_save(sim_t* s, void* out, uint64_t cap, int out_on_dev
 }
 
 sim_status sim_checkpoint_load(sim_t* s, const void* in, uint64_t in_len, int in_on_device) {
+  if (s) ++s->cfg_gen;  // a kept batch graph no longer matches
   if (!s || !in) return fail(SIM_ERR_INVALID, "NULL argument");
   if (in_len < kCkHead) return fail(SIM_ERR_INVALID, "checkpoint shorter than its header");
   const uint8_t* base = reinterpret_cast<const uint8_t*>(in);

@@ -43,7 +43,8 @@ class Stats(C.Structure):
         ("split_trials", C.c_uint64),
         ("cache_lookups", C.c_uint64), ("cache_hits", C.c_uint64),
         ("fast_items", C.c_uint64), ("fast_deferred", C.c_uint64), ("kernel_launches", C.c_uint64),
-        ("palette_trials", C.c_uint64),
+        ("palette_trials", C.c_uint64), ("graph_replays", C.c_uint64), ("ladder", C.c_int32),
+        ("modes", C.c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -51,6 +52,14 @@ class Stats(C.Structure):
         d["chunks_by_mode"] = list(self.chunks_by_mode)
         d["phase_cycles"] = list(self.phase_cycles)
         return d
+
+
+class TunePoint(C.Structure):
+    _fields_ = [("block_log2", C.c_int32), ("chunk_log2", C.c_int32), ("ladder", C.c_int32), ("modes", C.c_uint32),
+                ("rate", C.c_double), ("ratio", C.c_double), ("fidelity_lb_sum", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -94,6 +103,9 @@ def lib():
             "sim_codec_encode_noalloc": [vp, u64, i32, dbl, i32, vp, u64, vp],
             "sim_batch_apply": [vp, i32, vp, vp, i32],
             "sim_autotune_chunk": [i32, i32, dbl, vp, sz, vp, i32, C.POINTER(C.c_int), vp],
+            "sim_autotune": [i32, dbl, vp, sz, vp, i32, vp, i32, vp, i32, vp, i32, C.POINTER(TunePoint), vp, sz,
+                             C.POINTER(C.c_size_t)],
+            "sim_reset": [vp],
             "sim_set_timing": [vp, i32],
             "sim_set_selector": [vp, i32, vp],
             "sim_trace": [vp, u64],
@@ -172,6 +184,10 @@ class Sim:
         if self._h:
             _check(lib().sim_destroy(self._h), "sim_destroy")
             self._h = None
+
+    def reset(self) -> None:
+        """Back to |0...0>, the lossless stage and zero statistics; settings kept."""
+        _check(lib().sim_reset(self._h), "sim_reset")
 
     def __del__(self):
         try:
@@ -361,6 +377,26 @@ def autotune_chunk(n_qubits: int, block_log2: int, err_bound: float, probe, cand
                                     C.cast(cand, C.c_void_p), len(candidates), C.byref(best), C.c_void_p(_ptr(rates))),
            "sim_autotune_chunk")
     return int(best.value), dict(zip(candidates, rates.tolist()))
+
+
+def autotune(n_qubits: int, err_bound: float, probe, block_log2s=(16, 10, 11, 12, 13, 14, 15), chunk_log2s=(10, 9, 8),
+             ladders=(0, 1, 2), mode_sets=(0x1F, 0x5F)):
+    """Coordinate-descent autotuner over block size, tile (chunk) size and codec
+    schedule (sim_autotune); returns (best point, every measured point) as dicts."""
+    g = gates_array(probe)
+    bs = (C.c_int32 * len(block_log2s))(*block_log2s)
+    cs = (C.c_int32 * len(chunk_log2s))(*chunk_log2s)
+    ls = (C.c_int32 * len(ladders))(*ladders)
+    ms = (C.c_uint32 * len(mode_sets))(*mode_sets)
+    best = TunePoint()
+    cap = len(block_log2s) * len(chunk_log2s) * len(ladders) * len(mode_sets)
+    tried = (TunePoint * cap)()
+    n = C.c_size_t()
+    _check(lib().sim_autotune(int(n_qubits), float(err_bound), C.c_void_p(_ptr(g)), g.shape[0], C.cast(bs, C.c_void_p),
+                              len(block_log2s), C.cast(cs, C.c_void_p), len(chunk_log2s), C.cast(ls, C.c_void_p),
+                              len(ladders), C.cast(ms, C.c_void_p), len(mode_sets), C.byref(best),
+                              C.cast(tried, C.c_void_p), cap, C.byref(n)), "sim_autotune")
+    return best.as_dict(), [tried[i].as_dict() for i in range(min(n.value, cap))]
 
 
 def mlp_grad(params, x, mode, sizes):

@@ -68,19 +68,85 @@ def test_autotune_returns_fastest_candidate():
     assert rates[best] == max(rates.values())
 
 
+def test_autotune_searches_block_tile_and_schedule():
+    """Coordinate descent over block size, chunk size, ladder and mode set: every
+    measured point is a distinct setting as the handle applies it (blocks clamped to n,
+    chunks to the block), every rate is positive, and the winner has the highest rate
+    measured."""
+    n = 14
+    probe = Cc.rcs_n(n, 6, seed=8)
+    best, tried = qc().autotune(n, 1e-4, probe, block_log2s=(16, 10, 12, 14), chunk_log2s=(9, 8, 7),
+                                ladders=(0, 1, 2), mode_sets=(0x1F, 0x5F))
+    keys = [(p["block_log2"], p["chunk_log2"], p["ladder"], p["modes"]) for p in tried]
+    assert len(keys) == len(set(keys)) >= 1 + 2 + 2 + 2 + 1
+    for b, kc, lad, m in keys:
+        assert b <= n and kc <= b and lad in (0, 1, 2) and m in (0x1F, 0x5F)
+    assert all(p["rate"] > 0 and p["ratio"] > 1 for p in tried)
+    assert best["rate"] == max(p["rate"] for p in tried)
+    assert (best["block_log2"], best["chunk_log2"], best["ladder"], best["modes"]) in keys
+
+
+def test_reset_then_rerun_is_a_fresh_run():
+    """sim_reset returns the handle to |0...0> with zero statistics; the same circuit
+    run again (block cache on) gives the bytes of a fresh handle."""
+    n, kc, eps = 13, 8, 1e-4
+    gates = Cc.rcs_n(n, 6, seed=9)
+    s = make(n, kc, eps)
+    s.set_block_cache(True)
+    s.apply_circuit(Cc.qft(n, seed=3)[0])
+    s.reset()
+    fresh = make(n, kc, eps)
+    assert images(s) == images(fresh)
+    st = s.stats()
+    assert st["gates"] == 0 and st["amp_updates"] == 0 and st["eps_switch_gate"] == -1 and st["level"] == 0
+    s.apply_circuit(gates)
+    fresh.apply_circuit(gates)
+    assert images(s) == images(fresh)
+    for key in ("gates", "encoded_bytes", "max_encoded_bytes", "eps_switch_gate", "amp_updates", "pages_in_use_bytes"):
+        assert s.stats()[key] == fresh.stats()[key], key
+
+
+def test_batch_graph_is_kept_and_replayed():
+    """The graph of a batched call stays with the first handle: after sim_reset the same
+    call replays it (same bytes as the first run); a changed circuit is captured anew
+    and still equals the circuits run alone."""
+    kc, eps = 7, 1e-4
+    specs = [(11, 5), (13, 4), (12, 6), (10, 3)]
+    circuits = [Cc.rcs_n(n, d, seed=300 + k) for k, (n, d) in enumerate(specs)]
+    batch = [make(n, kc, eps) for n, _ in specs]
+    qc().batch_apply(batch, circuits, use_graph=True)
+    first = [images(s) for s in batch]
+    for s in batch:
+        s.reset()
+    qc().batch_apply(batch, circuits, use_graph=True)
+    assert batch[0].stats()["graph_replays"] == 1
+    assert [images(s) for s in batch] == first
+    for s in batch:
+        s.reset()
+    circuits[2] = Cc.rcs_n(12, 6, seed=399)
+    qc().batch_apply(batch, circuits, use_graph=True)
+    assert batch[0].stats()["graph_replays"] == 1
+    for k, (n, _) in enumerate(specs):
+        solo = make(n, kc, eps)
+        solo.apply_circuit(circuits[k])
+        assert images(batch[k]) == images(solo), k
+
+
 def test_batch_run_matches_individual_runs():
     """sim_batch_run: handles created, run batched and destroyed inside the call; each
     circuit's statistics equal those of the same circuit run alone with the same
-    settings (chunk size as the call reports it)."""
+    settings (block and chunk size, ladder and mode set as the call reports them)."""
     rng = np.random.default_rng(11)
     eps = 1e-4
     sizes = [int(rng.integers(9, 14)) for _ in range(6)]
     circuits = [Cc.rcs_n(n, int(rng.integers(3, 7)), seed=200 + k) for k, n in enumerate(sizes)]
     stats = qc().batch_run(circuits, sizes, eps)
     for k, n in enumerate(sizes):
-        kc = stats[k]["chunk_log2"]
+        kc, b = stats[k]["chunk_log2"], stats[k]["block_log2"]
         raw = 16 << n
-        solo = qc().Sim(n, min(n, 20), eps, chunk_log2=kc, budget=raw // 4, pool_bytes=raw + raw // 8 + (8 << 20))
+        solo = qc().Sim(n, b, eps, chunk_log2=kc, budget=raw // 4, ladder=stats[k]["ladder"],
+                        pool_bytes=raw + raw // 8 + (8 << 20))
+        solo.set_modes(stats[k]["modes"])
         solo.apply_circuit(circuits[k])
         st = solo.stats()
         for key in ("gates", "encoded_bytes", "max_encoded_bytes", "eps_switch_gate", "level", "amp_updates"):

@@ -184,7 +184,7 @@ def test_paired_and_chunk_by_chunk_coding_agree(kc):
             a, b = sims
             assert [a.chunk_image(c) for c in range(a.n_chunks)] == [b.chunk_image(c) for c in range(b.n_chunks)], k
         recs = sims[1].trace_read()
-        assert recs.shape[0] == 1 << 10
+        assert 0 < recs.shape[0] <= 1 << 10
         assert set(np.unique(recs[:, 16]).astype(int)) <= {0, 1, 2, 3, 4}
         orc = O.CSim(n, n, kc, eps, (16 << n) // 4)
         orc.apply(gates)
