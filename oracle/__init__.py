@@ -66,6 +66,8 @@ class _Stats(C.Structure):
         ("eps_switch_gate", C.c_int64),
         ("S_current", C.c_int32),
         ("level", C.c_int32),
+        ("guard_fit", C.c_int32),
+        ("pad", C.c_int32),
     ]
 
 

@@ -774,6 +774,8 @@ typedef struct {
   double min_ratio, eps_current, fid_lb_sum, fid_lb_prod;
   int64_t eps_switch_gate;
   int32_t S_current, level;
+  int32_t guard_fit; /* guarded ladder: 1 if the last gate's level was chosen because its worst case fits */
+  int32_t pad;
 } orc_stats;
 
 typedef struct {
@@ -786,6 +788,7 @@ typedef struct {
   uint64_t budget, thresh, inflight, nchunks, E, Emax, gates;
   int64_t switch_gate;
   double lb_sum, lb_prod;
+  int guard_fit;
   uint8_t** img;
   uint32_t* len;
   int poisoned;
@@ -883,14 +886,16 @@ static uint64_t max_level_image(int kc, int S) {
  * -- the gate ends with at most touched x (largest image) bytes if it rewrites every
  * chunk, else with at most E + touched x (largest image). */
 static void controller(orc_csim* s, uint64_t touched) {
-  if (s->nlevels == 0 || s->level >= s->nlevels) return;
+  if (s->nlevels == 0 || (s->ladder != 2 && s->level >= s->nlevels)) return;
   int lvl = s->level;
   if (s->ladder == 2) {
     lvl = s->nlevels;
-    for (int l = s->level; l < s->nlevels; ++l) {
+    s->guard_fit = 0;
+    for (int l = s->level; l <= s->nlevels; ++l) {
       uint64_t worst = touched * max_level_image(s->kc, l == 0 ? 64 : orc_sig_bits(s->levels[l - 1]));
       if ((touched >= s->nchunks ? worst : s->E + worst) <= s->thresh) {
         lvl = l;
+        s->guard_fit = 1;
         break;
       }
     }
@@ -1022,6 +1027,7 @@ void orc_csim_stats(const orc_csim* s, orc_stats* st) {
   st->eps_switch_gate = s->switch_gate;
   st->S_current = s->S_cur;
   st->level = s->level;
+  st->guard_fit = s->guard_fit;
 }
 
 uint64_t orc_csim_nchunks(const orc_csim* s) { return s->nchunks; }
