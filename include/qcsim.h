@@ -101,6 +101,7 @@ typedef struct sim_stats_t {
   uint64_t graph_replays;     /* sim_batch_apply calls led by this handle that replayed its kept graph */
   int32_t ladder;             /* the controller's bound ladder (0 jump, 1 the paper's, 2 guarded) */
   uint32_t modes;             /* the mode set of sim_set_modes / sim_set_selector */
+  uint64_t wide_images;       /* chunk images coded at 64 bits (the lossless stage, or a subnormal) */
 } sim_stats_t;
 
 /* Creates the state |0...0> of n_qubits (1..40) split into blocks of 2^block_log2

@@ -68,6 +68,7 @@ class _Stats(C.Structure):
         ("level", C.c_int32),
         ("guard_fit", C.c_int32),
         ("pad", C.c_int32),
+        ("wide_images", C.c_uint64),
     ]
 
 

@@ -776,6 +776,7 @@ typedef struct {
   int32_t S_current, level;
   int32_t guard_fit; /* guarded ladder: 1 if the last gate's level was chosen because its worst case fits */
   int32_t pad;
+  uint64_t wide_images; /* images whose header says S = 64 */
 } orc_stats;
 
 typedef struct {
@@ -789,6 +790,7 @@ typedef struct {
   int64_t switch_gate;
   double lb_sum, lb_prod;
   int guard_fit;
+  uint64_t n64; /* images whose header says S = 64 */
   uint8_t** img;
   uint32_t* len;
   int poisoned;
@@ -803,9 +805,14 @@ static int csim_store(orc_csim* s, uint64_t c, const uint64_t* vals, unsigned ma
   if (L < 0) { free(buf); return (int)L; }
   uint8_t* fit = (uint8_t*)realloc(buf, (size_t)L);
   if (fit) buf = fit;
-  if (s->img[c]) { s->E -= s->len[c]; free(s->img[c]); }
+  if (s->img[c]) {
+    s->E -= s->len[c];
+    s->n64 -= s->img[c][1] == 64;
+    free(s->img[c]);
+  }
   s->img[c] = buf;
   s->len[c] = (uint32_t)L;
+  s->n64 += buf[1] == 64;
   s->E += (uint64_t)L;
   return ORC_OK;
 }
@@ -883,16 +890,26 @@ static uint64_t max_level_image(int kc, int S) {
  * relax when E + two decompressed blocks (Eq. totalnbBytes) exceed floor(tau budget).
  * Ladder 2 reads the rule for a device that rewrites all of a gate's chunks at once:
  * take the smallest level, never below the current one, whose worst case still fits
- * -- the gate ends with at most touched x (largest image) bytes if it rewrites every
- * chunk, else with at most E + touched x (largest image). */
-static void controller(orc_csim* s, uint64_t touched) {
+ * -- the gate ends with at most the sum of the largest images of the chunks it
+ * rewrites if it rewrites every chunk, else with at most E plus that sum.  A chunk
+ * holding a subnormal is coded at 64 bits at any level (Eq. sigbits cannot truncate
+ * it), so its largest image is the 64-bit one: once the run is lossy, every image
+ * still at 64 bits is assumed to be among the rewritten chunks; and a gate with a
+ * nonzero coefficient below 2^-52 in magnitude may make subnormals of normal values,
+ * so all of its chunks count at 64 bits. */
+static void controller(orc_csim* s, uint64_t touched, int wide_gate) {
   if (s->nlevels == 0 || (s->ladder != 2 && s->level >= s->nlevels)) return;
   int lvl = s->level;
   if (s->ladder == 2) {
+    uint64_t wide = 0;
+    if (wide_gate) wide = touched;
+    else if (s->level > 0) wide = s->n64 < touched ? s->n64 : touched;
+    const uint64_t full = max_level_image(s->kc, 64);
     lvl = s->nlevels;
     s->guard_fit = 0;
     for (int l = s->level; l <= s->nlevels; ++l) {
-      uint64_t worst = touched * max_level_image(s->kc, l == 0 ? 64 : orc_sig_bits(s->levels[l - 1]));
+      uint64_t worst = (touched - wide) * max_level_image(s->kc, l == 0 ? 64 : orc_sig_bits(s->levels[l - 1])) +
+                       wide * full;
       if ((touched >= s->nchunks ? worst : s->E + worst) <= s->thresh) {
         lvl = l;
         s->guard_fit = 1;
@@ -909,6 +926,13 @@ static void controller(orc_csim* s, uint64_t touched) {
   if (s->switch_gate < 0) s->switch_gate = (int64_t)s->gates;
 }
 
+/* A coefficient that can turn a normal value into a subnormal: nonzero, below 2^-52. */
+static int gate_is_wide(const orc_gate* g) {
+  for (int k = 0; k < 8; ++k)
+    if (g->u[k] != 0.0 && fabs(g->u[k]) < 0x1p-52) return 1;
+  return 0;
+}
+
 int orc_csim_apply(orc_csim* s, const orc_gate* g) {
   if (s->poisoned) return ORC_ERR_STATE;
   int rc = orc_gate_check(g, s->n);
@@ -916,7 +940,7 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
   int kc = s->kc, t = g->target;
   size_t A = (size_t)1 << kc, N = 2 * A;
   uint64_t hi_mask = g->ctrl_mask >> kc, hi_vals = g->ctrl_vals >> kc;
-  controller(s, s->nchunks >> __builtin_popcountll(hi_mask & (s->nchunks - 1)));
+  controller(s, s->nchunks >> __builtin_popcountll(hi_mask & (s->nchunks - 1)), gate_is_wide(g));
   uint64_t lo_mask = g->ctrl_mask & (A - 1), lo_vals = g->ctrl_vals & (A - 1);
   uint64_t* x0 = (uint64_t*)malloc(N * 8);
   uint64_t* x1 = (uint64_t*)malloc(N * 8);
@@ -1028,6 +1052,7 @@ void orc_csim_stats(const orc_csim* s, orc_stats* st) {
   st->S_current = s->S_cur;
   st->level = s->level;
   st->guard_fit = s->guard_fit;
+  st->wide_images = s->n64;
 }
 
 uint64_t orc_csim_nchunks(const orc_csim* s) { return s->nchunks; }

@@ -471,6 +471,10 @@ static GateLaunch make_launch(sim* s, const sim_gate* g) {
     const bool diag = u[2] == 0 && u[3] == 0 && u[4] == 0 && u[5] == 0;
     const bool perm = u[0] == 0 && u[1] == 0 && u[6] == 0 && u[7] == 0;
     L.gfeat = (real ? 1u : 0u) | (diag ? 2u : 0u) | (perm ? 4u : 0u) | (t < kc ? 8u : 0u);
+    // a coefficient that can turn a normal value into a subnormal (see next_level)
+    L.ctl.wide_gate = 0;
+    for (int k = 0; k < 8; ++k)
+      if (u[k] != 0.0 && std::fabs(u[k]) < 0x1p-52) L.ctl.wide_gate = 1;
   }
   L.bc = s->d_trace ? nullptr : s->d_bc;
   L.trace = s->d_trace;
@@ -953,7 +957,7 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   DevCtl h{};
   unsigned long long counts[8] = {0};
   CK(cudaMemsetAsync(s->d_counts, 0, sizeof(counts), s->st), "memset");
-  CK(qc::launch_mode_counts(s->P, s->nchunks, s->d_counts, s->st), "mode count launch");
+  CK(qc::launch_mode_counts(s->P, s->nchunks, s->d_counts, nullptr, s->st), "mode count launch");
   CK(cudaMemcpyAsync(&h, s->d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s->st), "copy counters");
   CK(cudaMemcpyAsync(counts, s->d_counts, sizeof(counts), cudaMemcpyDeviceToHost, s->st), "copy counts");
   CK(cudaStreamSynchronize(s->st), "sync");
@@ -990,6 +994,7 @@ sim_status sim_stats(sim_t* s, sim_stats_t* o) {
   o->graph_replays = s->graph_replays;
   o->ladder = s->ladder;
   o->modes = s->modes;
+  o->wide_images = h.n64 < 0 ? 0 : (uint64_t)h.n64;
   if (h.err) return s->check_device();
   return SIM_OK;
 }
@@ -1491,8 +1496,14 @@ sim_status sim_checkpoint_load(sim_t* s, const void* in, uint64_t in_len, int in
     h.level = k.level;
     h.S_last = k.S_last;
     h.err = 0;
+    h.n64 = 0;  // counted from the loaded images below
+    h.dn64 = 0;
     e = cudaMemcpyAsync(s->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
   }
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counts, 0, 8 * sizeof(unsigned long long), s->st);
+  if (e == cudaSuccess)
+    e = qc::launch_mode_counts(s->P, s->nchunks, s->d_counts,
+                               reinterpret_cast<unsigned long long*>(&s->d_ctl->n64), s->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->P.cache_n, 0, (size_t)s->grid * sizeof(uint32_t), s->st);
   if (e == cudaSuccess)  // the streaming kernel's warp caches held pages of the replaced arena
     e = cudaMemsetAsync(s->P.wcache_n, 0, (size_t)(s->fast_grid ? s->fast_grid : 1) * qc::fast_warps() * 4, s->st);

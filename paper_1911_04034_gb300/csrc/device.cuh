@@ -95,6 +95,8 @@ struct DevCtl {
   unsigned int timeout_pad;
   unsigned long long wc_pages;         // free pages the streaming kernel's warps keep in their caches
   unsigned long long palette_trials;   // chunk encodes that ran the PALETTE trial
+  long long n64;                       // images whose header says S = 64 (as of the last gate)
+  long long dn64;                      // ... its change during the running gate
 };
 
 // Controller parameters (host-computed, constant for the handle).
@@ -108,18 +110,27 @@ struct CtlParams {
   unsigned long long nchunks;   // chunks of the state
   unsigned long long touched;   // chunks the running gate rewrites (set per gate)
   unsigned long long maxb[9];   // largest image the encoder can write at level l (0 = lossless)
+  int wide_gate;                // the running gate has a nonzero coefficient below 2^-52 (set per gate)
+  int pad;
 };
 
 // Section 3.7: before a gate, relax the bound if E + inflight > floor(tau * budget).
 // Guarded ladder: the smallest level (never below the current one) at which even
 // the largest images on every chunk the gate rewrites keep E within floor(tau *
-// budget): a gate rewriting every chunk ends with at most touched * maxb bytes,
-// otherwise E grows by at most touched * maxb.
-__host__ __device__ __forceinline__ int next_level(const CtlParams& p, unsigned long long E, int level) {
+// budget): a gate rewriting every chunk ends with at most the sum of those images,
+// otherwise E grows by at most that sum.  A chunk holding a subnormal is coded at 64
+// bits at any level (Eq. sigbits cannot truncate it): once the run is lossy, the n64
+// images still at 64 bits are assumed to be among the rewritten chunks, and a gate
+// that may make subnormals of normal values (a nonzero coefficient below 2^-52)
+// counts all of its chunks at 64 bits.
+__host__ __device__ __forceinline__ int next_level(const CtlParams& p, unsigned long long E, int level, long long n64) {
   if (p.nlevels == 0 || level >= p.nlevels) return level;
   if (p.ladder == 2) {
+    unsigned long long wide = 0;
+    if (p.wide_gate) wide = p.touched;
+    else if (level > 0) wide = n64 < 0 ? 0ull : ((unsigned long long)n64 < p.touched ? (unsigned long long)n64 : p.touched);
     for (int l = level; l < p.nlevels; ++l) {
-      const unsigned long long worst = p.touched * p.maxb[l];
+      const unsigned long long worst = (p.touched - wide) * p.maxb[l] + wide * p.maxb[0];
       if ((p.touched >= p.nchunks ? worst : E + worst) <= p.thresh) return l;
     }
     return p.nlevels;

@@ -17,7 +17,7 @@ __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.w
 // Section 3.7: the bound of the running gate, from E after the previous gate.  Every
 // CTA evaluates the same rule on the same values (only the post kernel writes them).
 __device__ __forceinline__ uint32_t gate_bits(const GateLaunch& L) {
-  return (uint32_t)level_bits(L.ctl, next_level(L.ctl, L.P.ctl->E, L.P.ctl->level));
+  return (uint32_t)level_bits(L.ctl, next_level(L.ctl, L.P.ctl->E, L.P.ctl->level, L.P.ctl->n64));
 }
 
 // The chunk index of the k-th active chunk (or pair): the bits of k deposited into the

@@ -57,6 +57,7 @@ struct GateSmem {
 // hold no registers during the codec phases).
 struct CtaAcc {
   long long dE;
+  long long dn64;          // change in the number of images at S = 64
   unsigned long long rd, wr;
   unsigned long long key;  // block-cache key of the running item
 };
@@ -155,6 +156,7 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
   }
   if (threadIdx.x == 0) {
     st.acc->dE = 0;
+    st.acc->dn64 = 0;
     st.acc->rd = st.acc->wr = 0;
   }
   st.err = 0u;
@@ -179,6 +181,7 @@ __device__ __forceinline__ void cta_end(const GateLaunch& L, GateCta& st, const 
       if (ph[k]) atomicAdd(&ctl->phase_cycles[k], (unsigned long long)ph[k]);
   L.P.cache_n[blockIdx.x] = n;
   if (st.acc->dE) atomicAdd(&ctl->dE, (unsigned long long)st.acc->dE);
+  if (st.acc->dn64) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->dn64), (unsigned long long)st.acc->dn64);
   if (st.acc->rd) atomicAdd(&ctl->bytes_in, st.acc->rd);
   if (st.acc->wr) atomicAdd(&ctl->bytes_out, st.acc->wr);
 }
@@ -306,6 +309,8 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
         w0[0] = n0;
         w1[0] = n1;
         st.acc->dE += (long long)n0 + (long long)n1 - (long long)b0 - (long long)b1;
+        auto wide = [](uint32_t h) { return ((h >> 8) & 0xffu) == 64u ? 1ll : 0ll; };
+        st.acc->dn64 += wide(h0[0]) + wide(h1[0]) - (z0 ? 0ll : wide(ent0[4])) - (z1 ? 0ll : wide(ent1[4]));
         st.acc->wr += n0 + n1;
       }
     }
@@ -331,6 +336,8 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   __syncthreads();
   if (threadIdx.x < 32u) free_pages_warp(P, st.cc, ent0 + 4, np0, ent1 + 4, has1 ? np1 : 0u);
   QC_PHASE(0);
+  // the input images coded at 64 bits (thread 0), for the controller's count
+  const long long old64 = threadIdx.x == 0 ? (long long)(m.img0[1] == 64u) + (long long)(has1 && m.img1[1] == 64u) : 0ll;
   // the next item's pages into L2: warp 0 for its first chunk, warp 1 for its second
   // (each warp waits only for the entry copies it issued itself)
   auto prefetch_next = [&]() {
@@ -528,6 +535,7 @@ __device__ __forceinline__ bool gate_item(const GateLaunch& L, unsigned long lon
   if (threadIdx.x == 0) {
     const uint32_t i0 = ent0[0], i1 = has1 ? ent1[0] : 0u;  // the old image lengths (entry copies)
     st.acc->dE += (long long)n0 - (long long)i0 + (has1 ? (long long)n1 - (long long)i1 : 0ll);
+    st.acc->dn64 += (long long)(m.img0[1] == 64u) + (long long)(has1 && m.img1[1] == 64u) - old64;
     st.acc->wr += n0 + (has1 ? n1 : 0u);
   }
   __syncthreads();
@@ -647,7 +655,7 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
     ctl->nfreed = 0;
     ctl->ndefer = 0;
     ctl->fast_all = 0u;
-    const int lvl = next_level(cp, ctl->E, ctl->level);
+    const int lvl = next_level(cp, ctl->E, ctl->level, ctl->n64);
     const int S = level_bits(cp, lvl);
     if (lvl > 0 && ctl->switch_gate < 0) ctl->switch_gate = (long long)ctl->gates;
     if (S < 64) {
@@ -658,6 +666,8 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
     ctl->S_last = S;
     ctl->E += ctl->dE;
     ctl->dE = 0;
+    ctl->n64 += ctl->dn64;
+    ctl->dn64 = 0;
     if (ctl->E > ctl->Emax) ctl->Emax = ctl->E;
     ctl->gates += 1;
     // block cache: pause it after kBcZeroGates gates in a row with lookups and no hit
@@ -742,6 +752,7 @@ __global__ void __launch_bounds__(kThreads) k_init_chunk0(const Pool P, unsigned
   if (threadIdx.x == 0) {
     P.ctl->E = 16ull * (nchunks - 1ull) + n0;
     P.ctl->Emax = P.ctl->E;
+    P.ctl->n64 = ((reinterpret_cast<const uint32_t*>(img)[0] >> 8) & 0xffu) == 64u ? 1 : 0;
     P.ctl->peak_pages = P.npages - (unsigned long long)P.ctl->top;
   }
 }
@@ -897,9 +908,12 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__global__ void k_mode_counts(const Pool P, unsigned long long nchunks, unsigned long long* counts) {
-  __shared__ unsigned long long sc[8];
-  if (threadIdx.x < 8) sc[threadIdx.x] = 0;
+// Chunks per mode (counts[8]) and, if wide is not null, the images whose header says
+// S = 64 (added to *wide).
+__global__ void k_mode_counts(const Pool P, unsigned long long nchunks, unsigned long long* counts,
+                              unsigned long long* wide) {
+  __shared__ unsigned long long sc[9];
+  if (threadIdx.x < 9) sc[threadIdx.x] = 0;
   __syncthreads();
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nchunks; c += stride) {
@@ -907,9 +921,11 @@ __global__ void k_mode_counts(const Pool P, unsigned long long nchunks, unsigned
     uint32_t h = e[4];
     if (e[1] != 0u) h = *reinterpret_cast<const uint32_t*>(P.pages + (unsigned long long)e[4] * kPage);
     atomicAdd(&sc[h & 7u], 1ull);
+    if (((h >> 8) & 0xffu) == 64u) atomicAdd(&sc[8], 1ull);
   }
   __syncthreads();
   if (threadIdx.x < 8 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+  if (threadIdx.x == 8 && wide && sc[8]) atomicAdd(wide, sc[8]);
 }
 
 __global__ void k_copy_image(const Pool P, unsigned long long chunk, uint8_t* out) {
@@ -1162,10 +1178,10 @@ cudaError_t launch_chunk_dots(const Pool& P, unsigned long long cfirst, unsigned
 }
 
 cudaError_t launch_mode_counts(const Pool& P, unsigned long long nchunks, unsigned long long* counts,
-                               cudaStream_t st) {
+                               unsigned long long* wide, cudaStream_t st) {
   const unsigned long long blocks = (nchunks + 255ull) / 256ull;
   const unsigned g = (unsigned)(blocks < (unsigned long long)num_sms() * 8 ? blocks : (unsigned long long)num_sms() * 8);
-  k_mode_counts<<<g, 256, 0, st>>>(P, nchunks, counts);
+  k_mode_counts<<<g, 256, 0, st>>>(P, nchunks, counts, wide);
   return cudaGetLastError();
 }
 

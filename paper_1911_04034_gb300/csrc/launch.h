@@ -101,7 +101,7 @@ cudaError_t launch_chunk_norms(const Pool& P, unsigned long long cfirst, unsigne
 cudaError_t launch_chunk_dots(const Pool& P, unsigned long long cfirst, unsigned long long nchunks, const double* ref,
                              double* out, cudaStream_t st);
 cudaError_t launch_mode_counts(const Pool& P, unsigned long long nchunks, unsigned long long* counts,
-                               cudaStream_t st);
+                               unsigned long long* wide, cudaStream_t st);
 cudaError_t launch_copy_image(const Pool& P, unsigned long long chunk, uint8_t* out, cudaStream_t st);
 
 cudaError_t launch_sv_init(double* psi, unsigned long long amps, cudaStream_t st);

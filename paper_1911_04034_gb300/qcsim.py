@@ -44,7 +44,7 @@ class Stats(C.Structure):
         ("cache_lookups", C.c_uint64), ("cache_hits", C.c_uint64),
         ("fast_items", C.c_uint64), ("fast_deferred", C.c_uint64), ("kernel_launches", C.c_uint64),
         ("palette_trials", C.c_uint64), ("graph_replays", C.c_uint64), ("ladder", C.c_int32),
-        ("modes", C.c_uint32),
+        ("modes", C.c_uint32), ("wide_images", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:

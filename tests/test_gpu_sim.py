@@ -40,6 +40,7 @@ def stats_match(gs, os_):
     assert gs["fidelity_lb_sum"] == pytest.approx(os_["fid_lb_sum"], abs=1e-12)
     assert gs["fidelity_lb_prod"] == pytest.approx(os_["fid_lb_prod"], rel=1e-12)
     assert gs["chunks_by_mode"][:7] == os_["chunks_by_mode"][:7]
+    assert gs["wide_images"] == os_["wide_images"]
 
 
 @pytest.mark.parametrize("kc", [0, 1, 4, 7, 8, 9, 10, 11])
@@ -243,6 +244,27 @@ def test_guarded_ladder_switches_mid_run_like_the_oracle():
         stats_match(gpu.stats(), orc.stats())
         levels.append(gpu.stats()["level"])
     assert levels[0] == 0 and levels[-1] > 0
+
+
+@pytest.mark.parametrize("thresh", [12000, 15000, 17500])
+def test_guarded_ladder_counts_subnormal_chunks_like_the_oracle(thresh):
+    """Ladder 2 on a random state whose chunks all come to hold subnormals (coded at 64
+    bits at any level): the gate with the subnormal coefficient and every later gate
+    count the 64-bit images at RAW size, as the oracle does; images, the 64-bit image
+    count and the controller state match gate by gate."""
+    from test_oracle_sim import wide_chunk_circuit
+
+    n, kc = 10, 4
+    gates = wide_chunk_circuit()
+    budget = -(-thresh * 10 // 9)
+    orc = O.CSim(n, n, kc, 1e-4, budget, ladder=2)
+    gpu = qc().Sim(n, n, 1e-4, chunk_log2=kc, budget=budget, ladder=2, pool_bytes=64 << 20)
+    for g in gates:
+        gpu.apply_circuit([g])
+        orc.apply([g])
+        assert images_equal(gpu, orc) == []
+        stats_match(gpu.stats(), orc.stats())
+    assert gpu.stats()["wide_images"] == 1 << (n - kc)
 
 
 def test_solution_d_mode_bit_exact():

@@ -372,7 +372,6 @@ def wide_chunk_circuit():
     return np.concatenate([remap(Cc.rcs_n(9, 8, seed=41), rest), rot, remap(Cc.rcs_n(3, 6, seed=42), [0, 1, 2])])
 
 
-@pytest.mark.xfail(strict=True, reason="the guarded worst case counts every rewritten chunk at the level's width")
 def test_guarded_ladder_bounds_chunks_coded_at_full_width():
     """Section 3.7, guarded ladder: a chunk holding a subnormal is coded at 64 bits
     whatever the level (Eq. sigbits cannot truncate it), so its image may be as large
