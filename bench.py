@@ -104,13 +104,13 @@ def fp64_flops(gates: np.ndarray, n: int, kc: int) -> float:
 
 
 def gate_class(g) -> str:
-    """dense: all four entries of the 2x2 matrix nonzero (sqrt(X), sqrt(Y), H);
-    diagonal: zero off-diagonal (T, CZ, phases); permutation: zero diagonal (X, CNOT);
-    other: one zero entry."""
+    """dense: all four entries of the 2x2 matrix nonzero, some complex (sqrt(X));
+    real: all four nonzero and real (sqrt(Y), H); diagonal: zero off-diagonal (T, CZ,
+    phases); permutation: zero diagonal (X, CNOT); other: one zero entry."""
     u = [float(x) for x in g["u"]]
     z = [u[2 * k] == 0.0 and u[2 * k + 1] == 0.0 for k in range(4)]
     if not any(z):
-        return "dense"
+        return "real" if all(u[2 * k + 1] == 0.0 for k in range(4)) else "dense"
     if z[1] and z[2]:
         return "diagonal"
     if z[0] and z[3]:
@@ -124,7 +124,7 @@ def per_class(gates: np.ndarray, tl: dict, n: int, kc: int, hbm: float | None) -
     out = {}
     cls = [gate_class(g) for g in gates]
     assert len(cls) == len(tl["ms"])
-    for c in ("dense", "diagonal", "permutation", "other"):
+    for c in ("dense", "real", "diagonal", "permutation", "other"):
         idx = [i for i, x in enumerate(cls) if x == c]
         if not idx:
             continue

@@ -538,8 +538,23 @@ static bool fast_applies(const sim* s, const sim_gate* g, GateLaunch& L) {
   const double cf[16] = {u[0], -u[1], u[2], -u[3], u[0], u[1], u[2], u[3],
                          u[4], -u[5], u[6], -u[7], u[4], u[5], u[6], u[7]};
   for (int k = 0; k < 16; ++k) L.cf[k] = cf[k];
-  L.arith = diag ? 1 : (anti ? 2 : 0);
-  if (L.arith) {
+  const bool real = u[1] == 0.0 && u[3] == 0.0 && u[5] == 0.0 && u[7] == 0.0;
+  L.arith = diag ? 1 : (anti ? 2 : (real ? 3 : 0));
+  if (L.arith == 0) {
+    // every coefficient part of the same magnitude 2^k, none zero: exact products
+    const double c = std::fabs(cf[0]);
+    bool pow2 = c > 0.0;
+    for (int k = 1; k < 16 && pow2; ++k) pow2 = std::fabs(cf[k]) == c;
+    int e = 0;
+    if (pow2 && std::frexp(c, &e) == 0.5 && e - 1 >= -64 && e - 1 <= 0) {
+      L.arith = 4;
+      L.sk = e - 1;
+      L.sgn = 0;
+      for (int k = 0; k < 16; ++k)
+        if (cf[k] < 0.0) L.sgn |= 1u << k;
+    }
+  }
+  if (L.arith == 1 || L.arith == 2) {
     // the one nonzero entry of each row: a' = d0 x, b' = d1 y (x, y = a, b or b, a)
     const double d[4] = {diag ? u[0] : u[2], diag ? u[1] : u[3], diag ? u[6] : u[4], diag ? u[7] : u[5]};
     for (int r = 0; r < 2; ++r) {

@@ -350,6 +350,41 @@ __device__ __forceinline__ double2 dense_rows(const double* cf, double2 a, doubl
                       __fma_rn(cf[7], b.x, __fma_rn(cf[6], b.y, __fma_rn(cf[5], a.x, __dmul_rn(cf[4], a.y)))));
 }
 
+// The same output for a real matrix (every imaginary coefficient zero): the chains
+// above with their zero terms left out -- each dropped term adds an exact zero -- so
+// the products of the real parts alone, in the same order (cf[0] = cf[4] = the row's
+// first real coefficient, cf[2] = cf[6] its second).
+__device__ __forceinline__ double2 real_rows(const double* cf, double2 a, double2 b) {
+  return make_double2(__fma_rn(cf[2], b.x, __dmul_rn(cf[0], a.x)), __fma_rn(cf[2], b.y, __dmul_rn(cf[0], a.y)));
+}
+
+// The same output for a gate whose coefficient parts are all +-2^k, none zero (sqrt(X),
+// sqrt(Y)): every product of the chains above is exact, so each chain equals 2^k times
+// the chain of the signed inputs in the same order (scaling by a power of two commutes
+// with rounding while no partial sum leaves the normal range): three additions per
+// output part, then the scale added to the exponent field.  An input below 2^-959 could
+// put a partial sum out of the normal range: such an item goes to the general kernel,
+// as does an output out of range.  Bit q of L.sgn is the sign of coefficient cf[q].
+__device__ __forceinline__ void signed_rows(const GateLaunch& L, uint32_t r, uint32_t ar, uint32_t ai, uint32_t br,
+                                            uint32_t bi, uint32_t mh, uint32_t& outr, uint32_t& outi, bool& spec) {
+  const uint32_t sg = L.sgn >> (8u * r);
+  auto t = [&](int q, uint32_t h) { return hi_as_double(h ^ ((sg >> q) << 31)); };
+  auto tiny = [](uint32_t h) { return (h & 0x7fffffffu) != 0u && (h & 0x7ff00000u) < (64u << 20); };
+  spec |= tiny(ar) || tiny(ai) || tiny(br) || tiny(bi);
+  const double re = __dadd_rn(__dadd_rn(__dadd_rn(t(0, ar), t(1, ai)), t(2, br)), t(3, bi));
+  const double im = __dadd_rn(__dadd_rn(__dadd_rn(t(4, ai), t(5, ar)), t(6, bi)), t(7, br));
+  auto scaled = [&](double y) -> uint32_t {
+    const uint64_t u = (uint64_t)__double_as_longlong(y);
+    const uint32_t hi = (uint32_t)(u >> 32), e = (hi >> 20) & 0x7ffu;
+    if ((hi & 0x7fffffffu) == 0u && (uint32_t)u == 0u) return 0u;
+    const int es = (int)e + L.sk;
+    spec |= e == 0u || e == 0x7ffu || es < 1 || es > 2046;
+    return (hi + ((uint32_t)L.sk << 20)) & mh;
+  };
+  outr = scaled(re);
+  outi = scaled(im);
+}
+
 // Row r of a diagonal (x = the amplitude itself) or anti-diagonal (x = its partner)
 // gate on x, given as high words: a complex product in the order of the kept-term sums,
 // or an exact copy / negation done on the high words (no FP64); results truncated.
@@ -377,9 +412,13 @@ __device__ __forceinline__ void fast_pair_in_lane(const GateLaunch& L, uint32_t 
   const uint32_t ar = v[2 * k0], ai = v[2 * k0 + 1], br = v[2 * k1], bi = v[2 * k1 + 1];
   uint32_t o[4] = {ar & mh, ai & mh, br & mh, bi & mh};
   if (((ibase + (uint32_t)k0) & L.lo_mask) == L.lo_vals) {
-    if constexpr (ARITH == 0) {
+    if constexpr (ARITH == 4) {
+      signed_rows(L, 0u, ar, ai, br, bi, mh, o[0], o[1], spec);
+      signed_rows(L, 1u, ar, ai, br, bi, mh, o[2], o[3], spec);
+    } else if constexpr (ARITH == 0 || ARITH == 3) {
       const double2 a = make_double2(hi_as_double(ar), hi_as_double(ai)), b = make_double2(hi_as_double(br), hi_as_double(bi));
-      const double2 x = dense_rows(L.cf, a, b), y = dense_rows(L.cf + 8, a, b);
+      const double2 x = ARITH == 0 ? dense_rows(L.cf, a, b) : real_rows(L.cf, a, b);
+      const double2 y = ARITH == 0 ? dense_rows(L.cf + 8, a, b) : real_rows(L.cf + 8, a, b);
       o[0] = fast_trunc(x.x, mh, spec);
       o[1] = fast_trunc(x.y, mh, spec);
       o[2] = fast_trunc(y.x, mh, spec);
@@ -574,12 +613,17 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
         const uint32_t i0 = i & ~(1u << (KIND == 0 ? 31u : (uint32_t)L.target));
         uint32_t outr = v[2 * k] & mh, outi = v[2 * k + 1] & mh;  // unchanged amplitude, truncated
         if ((i0 & L.lo_mask) == L.lo_vals) {
-          if constexpr (ARITH == 0) {
+          if constexpr (ARITH == 4) {
+            const uint32_t ar = row ? w[2 * k] : v[2 * k], ai = row ? w[2 * k + 1] : v[2 * k + 1];
+            const uint32_t br = row ? v[2 * k] : w[2 * k], bi = row ? v[2 * k + 1] : w[2 * k + 1];
+            signed_rows(L, row, ar, ai, br, bi, mh, outr, outi, spec);
+          } else if constexpr (ARITH == 0 || ARITH == 3) {
             // a = the pair's first amplitude, b = its second
             const uint32_t ar = row ? w[2 * k] : v[2 * k], ai = row ? w[2 * k + 1] : v[2 * k + 1];
             const uint32_t br = row ? v[2 * k] : w[2 * k], bi = row ? v[2 * k + 1] : w[2 * k + 1];
-            const double2 out = dense_rows(L.cf + 8u * row, make_double2(hi_as_double(ar), hi_as_double(ai)),
-                                           make_double2(hi_as_double(br), hi_as_double(bi)));
+            const double2 a = make_double2(hi_as_double(ar), hi_as_double(ai));
+            const double2 b = make_double2(hi_as_double(br), hi_as_double(bi));
+            const double2 out = ARITH == 0 ? dense_rows(L.cf + 8u * row, a, b) : real_rows(L.cf + 8u * row, a, b);
             outr = fast_trunc(out.x, mh, spec);
             outi = fast_trunc(out.y, mh, spec);
           } else if constexpr (ARITH == 1) {
@@ -796,18 +840,24 @@ static cudaError_t launch_fast_as(const GateLaunch& L, int grid, size_t smem, cu
 }
 
 // Kinds and arithmetic forms that occur: cross-chunk pairs of any gate class, in-chunk
-// partners of dense or anti-diagonal gates, in-chunk diagonal gates.
+// partners of dense, real, power-of-two or anti-diagonal gates, in-chunk diagonal gates.
 cudaError_t launch_gate_fast(const GateLaunch& L, int grid, cudaStream_t st) {
   const size_t smem = fast_smem_bytes(L.P.kc);
-  switch (L.fast_kind * 4 + L.arith) {
+  switch (L.fast_kind * 8 + L.arith) {
     case 0: return launch_fast_as<0, 0>(L, grid, smem, st);
     case 1: return launch_fast_as<0, 1>(L, grid, smem, st);
     case 2: return launch_fast_as<0, 2>(L, grid, smem, st);
-    case 4: return launch_fast_as<1, 0>(L, grid, smem, st);
-    case 6: return launch_fast_as<1, 2>(L, grid, smem, st);
-    case 8: return launch_fast_as<2, 0>(L, grid, smem, st);
-    case 10: return launch_fast_as<2, 2>(L, grid, smem, st);
-    case 13: return launch_fast_as<3, 1>(L, grid, smem, st);
+    case 3: return launch_fast_as<0, 3>(L, grid, smem, st);
+    case 4: return launch_fast_as<0, 4>(L, grid, smem, st);
+    case 8: return launch_fast_as<1, 0>(L, grid, smem, st);
+    case 10: return launch_fast_as<1, 2>(L, grid, smem, st);
+    case 11: return launch_fast_as<1, 3>(L, grid, smem, st);
+    case 12: return launch_fast_as<1, 4>(L, grid, smem, st);
+    case 16: return launch_fast_as<2, 0>(L, grid, smem, st);
+    case 18: return launch_fast_as<2, 2>(L, grid, smem, st);
+    case 19: return launch_fast_as<2, 3>(L, grid, smem, st);
+    case 20: return launch_fast_as<2, 4>(L, grid, smem, st);
+    case 25: return launch_fast_as<3, 1>(L, grid, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }

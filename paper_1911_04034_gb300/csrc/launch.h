@@ -40,11 +40,15 @@ struct GateLaunch {
   int list;                      // general kernel: 1 = run the items the streaming kernel left
   // streaming kernel arithmetic (the same values as the kept-term sums of GateCoef):
   int arith;                     // 0 dense: the four sums with every coefficient, zeros included;
-                                 // 1 diagonal (u01 = u10 = 0); 2 anti-diagonal (u00 = u11 = 0)
+                                 // 1 diagonal (u01 = u10 = 0); 2 anti-diagonal (u00 = u11 = 0);
+                                 // 3 real (every imaginary part zero): the real products only;
+                                 // 4 every coefficient part +-2^sk, none zero: signed sums, then scaled
   int rop[2];                    // diagonal / anti-diagonal, per output row: 0 complex product, 1 copy
                                  // (the entry is exactly 1), 2 negation (exactly -1)
   double cf[16];                 // dense: row r's coefficients of (ar, ai, br, bi) / (ai, ar, bi, br) at 4r
   double du[4];                  // diagonal: u00, u11; anti-diagonal: u01, u10 (re, im)
+  uint32_t sgn;                  // arith 4: bit q set if coefficient cf[q] is negative
+  int sk;                        // arith 4: log2 of the coefficients' common magnitude
 };
 
 // One gate of one simulator inside a batched launch; its work items are the global

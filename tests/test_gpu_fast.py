@@ -111,3 +111,30 @@ def test_streaming_kernel_takes_the_lossy_random_circuit():
     orc = O.CSim(n, n, kc, 1e-4, (16 << n) // 4)
     orc.apply(gates)
     assert all_images(s) == [orc.image(c) for c in range(orc.nchunks)]
+
+
+def test_power_of_two_gates_near_the_bottom_of_the_normal_range():
+    """sqrt(X) and sqrt(Y) (every coefficient part +-1/2) run as signed sums scaled by
+    1/2.  With qubit 3 at |0>, a rotation on it with cos = 1e-300 puts c * a, near
+    1e-300 (normal, exponent field below 64), beside every amplitude a: items holding
+    such values go to the general kernel, the rest stay on the streaming kernel; the
+    images equal the oracle's gate by gate."""
+    n, kc, eps = 13, 8, 1e-4
+    c = 1e-300
+    s_ = np.sqrt(1.0 - c * c)
+    g = [Cc.gate(q, Cc.H) for q in range(n) if q != 3]
+    g.append(Cc.gate(3, np.array([[c, -s_], [s_, c]], dtype=np.complex128)))
+    rng = np.random.default_rng(5)
+    for q in rng.permutation(n):
+        g.append(Cc.gate(int(q), Cc.SX))
+        g.append(Cc.gate(int(q), Cc.SY))
+    gates = Cc.to_array(g)
+    budget = (16 << n) // 4
+    orc = O.CSim(n, n, kc, eps, budget)
+    gpu = qc().Sim(n, n, eps, chunk_log2=kc, budget=budget, pool_bytes=2 * (16 << n) + (64 << 20))
+    for k in range(len(gates)):
+        gpu.apply_gate(gates[k])
+        orc.apply(gates[k])
+        assert all_images(gpu) == [orc.image(q) for q in range(orc.nchunks)], k
+    st = gpu.stats()
+    assert st["fast_items"] > 0 and st["fast_deferred"] > 0
