@@ -56,7 +56,8 @@ NCU_TRAFFIC = {"ratio_to_image_bytes": 1.113, "source_sha": "f6df44bc141445fb"}
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("paper_1911_04034_gb300/csrc/kernels.cu", "paper_1911_04034_gb300/csrc/device.cuh"):
+    for f in ("paper_1911_04034_gb300/csrc/fast.cu", "paper_1911_04034_gb300/csrc/kernels.cu",
+              "paper_1911_04034_gb300/csrc/gate_common.cuh", "paper_1911_04034_gb300/csrc/device.cuh"):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -399,8 +399,6 @@ def _oracle_pair_check(gpu, gate, before_imgs, chunks, eps, kc):
     orc = O.CSim(kc + 1, kc + 1, kc, eps, budget=1 if eps else (1 << 40))
     for k, c in enumerate(chunks):
         orc.set_image(k, before_imgs[c])
-    if eps == 0.0:
-        pass
     orc.apply(g2)
     return [orc.image(k) for k in range(len(chunks))]
 
