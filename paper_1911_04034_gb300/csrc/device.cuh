@@ -1666,7 +1666,10 @@ __device__ __forceinline__ bool alloc_pages_warp(const Pool& P, const CtaCache& 
     if (lane == 0)
       old = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top), (unsigned long long)(-(long long)need));
     old = __shfl_sync(0xffffffffu, old, 0);
-    if (old - (long long)need < 0) return false;
+    if (old - (long long)need < 0) {  // dry: give the reservation back (top never stays below 0)
+      if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top), (unsigned long long)need);
+      return false;
+    }
   }
   for (uint32_t q = lane; q < tot; q += 32u) {
     const uint32_t id = q < take ? cc.ids[n - 1u - q] : P.stack[old - 1 - (long long)(q - take)];

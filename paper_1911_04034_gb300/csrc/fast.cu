@@ -62,7 +62,7 @@ struct WarpPages {
 };
 
 // All lanes: at least `want` (<= 32) ids in the cache, refilled 32 at a time from the
-// global stack.  False (E_OOM set) if the stack is dry.
+// global stack.  False (E_OOM set, the stack top restored) if the stack is dry.
 __device__ __forceinline__ bool wp_reserve(const Pool& P, const WarpPages& wp, uint32_t want) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t n = *wp.n;
@@ -71,8 +71,11 @@ __device__ __forceinline__ bool wp_reserve(const Pool& P, const WarpPages& wp, u
   if (lane == 0)
     old = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top), (unsigned long long)(-32ll));
   old = __shfl_sync(0xffffffffu, old, 0);
-  if (old - 32 < 0) {
-    if (lane == 0) atomicOr(&P.ctl->err, (unsigned)E_OOM);
+  if (old - 32 < 0) {  // the stack is dry: give the reservation back (top never stays below 0)
+    if (lane == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl->top), 32ull);
+      atomicOr(&P.ctl->err, (unsigned)E_OOM);
+    }
     return false;
   }
   wp.ids[n + lane] = P.stack[old - 1 - (long long)lane];

@@ -625,8 +625,16 @@ __global__ void __launch_bounds__(kThreads, VPT >= 16 ? 1 : QC_GATE_MIN_CTAS)
 __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, int grid_ctas) {
   DevCtl* ctl = P.ctl;
   __shared__ unsigned long long s_top;
-  if (threadIdx.x == 0) s_top = (unsigned long long)ctl->top;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    // after a device error (the pool ran dry, a corrupt image ...) the handle is
+    // finished: no bookkeeping, and never a stack index from a top below 0
+    const long long top = *(volatile long long*)&ctl->top;
+    s_skip = *(volatile unsigned int*)&ctl->err != 0u || top < 0;
+    s_top = s_skip ? 0ull : (unsigned long long)top;
+  }
   __syncthreads();
+  if (s_skip) return;
   // every warp takes its slots of the stack with one atomic (loop bounds rounded to whole
   // warps, so all lanes vote)
   const uint32_t lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
@@ -637,7 +645,11 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
     unsigned long long base = 0;
     if (lane == 0 && m) base = atomicAdd(&s_top, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (has) P.stack[base + __popc(m & below)] = P.cache[q];
+    if (has) {
+      const unsigned long long at = base + __popc(m & below);
+      if (at < P.npages) P.stack[at] = P.cache[q];
+      else atomicOr(&ctl->err, (unsigned)E_CORRUPT);
+    }
   }
   const unsigned long long nf = ctl->nfreed;
   for (unsigned long long i = threadIdx.x; i < ((nf + 31ull) & ~31ull); i += blockDim.x) {
@@ -646,7 +658,11 @@ __device__ __forceinline__ void post_body(const Pool& P, const CtlParams& cp, in
     unsigned long long base = 0;
     if (lane == 0 && m) base = atomicAdd(&s_top, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (has) P.stack[base + __popc(m & below)] = P.freed[i];
+    if (has) {
+      const unsigned long long at = base + __popc(m & below);
+      if (at < P.npages) P.stack[at] = P.freed[i];
+      else atomicOr(&ctl->err, (unsigned)E_CORRUPT);
+    }
   }
   __syncthreads();
   for (unsigned long long b = threadIdx.x; b < (unsigned long long)grid_ctas; b += blockDim.x) P.cache_n[b] = 0;

@@ -385,6 +385,23 @@ def test_oom_poisons_handle():
     assert ei.value.code == qc().ERR_STATE
 
 
+def test_oom_in_the_lossy_stage_poisons_handle():
+    """A lossy random circuit whose state outgrows a 4 MiB pool: the streaming kernel runs
+    (one CTA fits the pool's page-cache cap) and the pool runs dry in one of the gate
+    kernels; the failed reservation is given back, the bookkeeping kernel skips the stack,
+    and the call reports SIM_ERR_OOM, later calls SIM_ERR_STATE."""
+    n = 20
+    gpu = qc().Sim(n, n, 1e-4, chunk_log2=10, budget=1, pool_bytes=4 << 20)
+    with pytest.raises(qc().SimError) as ei:
+        gpu.apply_circuit(Cc.rcs_n(n, 6, seed=2))
+    assert ei.value.code == qc().ERR_OOM
+    with pytest.raises(qc().SimError) as ei:
+        gpu.apply_gate(Cc.gate(0, Cc.H))
+    assert ei.value.code == qc().ERR_STATE
+    ok = qc().Sim(12, 12, 1e-4, chunk_log2=8)  # the context is still usable
+    ok.apply_circuit(Cc.rcs_n(12, 3, seed=3))
+
+
 def _oracle_pair_check(gpu, gate, before_imgs, chunks, eps, kc):
     """Oracle applied to the sampled chunks alone: a state of kc+1 qubits made of the
     two chunks, the gate's target and controls remapped onto it."""
