@@ -1647,8 +1647,13 @@ __device__ __forceinline__ void free_pages_warp(const Pool& P, const CtaCache& c
   }
   for (uint32_t q = lane; q < tot; q += 32u) {
     const uint32_t id = q < np0 ? p0[q] : p1[q - np0];
-    if (q < room) cc.ids[n + q] = id;
-    else P.freed[base + (q - room)] = id;
+    if (q < room) {
+      cc.ids[n + q] = id;
+    } else {
+      const unsigned long long at = base + (q - room);
+      if (at < P.npages) P.freed[at] = id;  // the list holds every page at most once
+      else atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+    }
   }
   __syncwarp();
   if (lane == 0) *cc.n = n + min(tot, room);

@@ -97,8 +97,13 @@ __device__ __forceinline__ void wp_free(const Pool& P, const WarpPages& wp, cons
   }
   for (uint32_t q = lane; q < cnt; q += 32u) {
     const uint32_t id = ids[q];
-    if (q < room) wp.ids[n + q] = id;
-    else P.freed[base + (q - room)] = id;
+    if (q < room) {
+      wp.ids[n + q] = id;
+    } else {
+      const unsigned long long at = base + (q - room);
+      if (at < P.npages) P.freed[at] = id;  // the list holds every page at most once
+      else atomicOr(&P.ctl->err, (unsigned)E_CORRUPT);
+    }
   }
   __syncwarp();
   if (lane == 0) *wp.n = n + min(cnt, room);

@@ -159,7 +159,9 @@ __device__ __forceinline__ void cta_begin(const Pool& P, GateCta& st, bool prof,
     st.acc->dn64 = 0;
     st.acc->rd = st.acc->wr = 0;
   }
-  st.err = 0u;
+  // the error word as the launch finds it: after a device error even a CTA's first item
+  // stops before it touches the pool
+  st.err = threadIdx.x == 0 ? *(volatile unsigned int*)&P.ctl->err : 0u;
   st.pp = 0;
   st.cur = 0;
   st.next_item = ~0ull;
