@@ -1667,10 +1667,17 @@ sim_status sim_sv_apply_circuit(sim_sv_t* v, const sim_gate* gates, size_t n_gat
   std::string why;
   for (size_t k = 0; k < n_gates; ++k)
     if (!gate_ok(gates + k, v->n, &why)) return fail(SIM_ERR_INVALID, "invalid gate %zu: %s", k, why.c_str());
-  for (size_t k = 0; k < n_gates; ++k)
+  for (size_t k = 0; k < n_gates; ++k) {
+    // which amplitudes of a pair the gate reads and writes (see k_sv_gate)
+    const double* u = gates[k].u;
+    const bool z01 = u[2] == 0.0 && u[3] == 0.0, z10 = u[4] == 0.0 && u[5] == 0.0;
+    const bool wa = !(u[0] == 1.0 && u[1] == 0.0 && z01), wb = !(u[6] == 1.0 && u[7] == 0.0 && z10);
+    const uint32_t rows = (wa ? 1u : 0u) | (wb ? 2u : 0u) | ((wa || (wb && !z10)) ? 4u : 0u) |
+                          ((wb || (wa && !z01)) ? 8u : 0u);
     CK(qc::launch_sv_gate(v->psi, v->n, coef_of(gates + k), gates[k].target, gates[k].ctrl_mask, gates[k].ctrl_vals,
-                          v->st),
+                          rows, v->st),
        "state vector gate");
+  }
   CK(cudaStreamSynchronize(v->st), "sync");
   return SIM_OK;
 }

@@ -965,17 +965,23 @@ __global__ void k_sv_init(double2* psi, unsigned long long amps) {
     psi[i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
 }
 
+// rows: bit 0 / 1 = amplitude a / b is written (its row is not a plain copy [1, 0] /
+// [0, 1]), bit 2 / 3 = a / b is read (written, or the other row takes it with a nonzero
+// coefficient).  An amplitude left out is neither read nor written: T and CZ move half or
+// a quarter of the state.  A value not read enters only with an exactly zero
+// coefficient, which the kept-term sums leave out, so the results do not change.
 __global__ void __launch_bounds__(256) k_sv_gate(double2* psi, unsigned long long npairs, const GateCoef g, int target,
-                                                 unsigned long long cmask, unsigned long long cvals) {
+                                                 unsigned long long cmask, unsigned long long cvals, uint32_t rows) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long tb = 1ull << target, lowm = tb - 1ull;
   for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < npairs; p += stride) {
     const unsigned long long i0 = ((p & ~lowm) << 1) | (p & lowm);
     if ((i0 & cmask) != cvals) continue;
-    double2 a = psi[i0], b = psi[i0 | tb];
+    double2 a = (rows & 4u) ? psi[i0] : make_double2(0.0, 0.0);
+    double2 b = (rows & 8u) ? psi[i0 | tb] : make_double2(0.0, 0.0);
     apply_pair(g, a, b);
-    psi[i0] = a;
-    psi[i0 | tb] = b;
+    if (rows & 1u) psi[i0] = a;
+    if (rows & 2u) psi[i0 | tb] = b;
   }
 }
 
@@ -1214,11 +1220,12 @@ cudaError_t launch_sv_init(double* psi, unsigned long long amps, cudaStream_t st
 }
 
 cudaError_t launch_sv_gate(double* psi, int n, const GateCoef& g, int target, unsigned long long cmask,
-                           unsigned long long cvals, cudaStream_t st) {
+                           unsigned long long cvals, uint32_t rows, cudaStream_t st) {
   const unsigned long long npairs = 1ull << (n - 1);
   const unsigned long long want = (npairs + 255ull) / 256ull;
   const unsigned grid = (unsigned)(want < (unsigned long long)num_sms() * 16 ? want : (unsigned long long)num_sms() * 16);
-  k_sv_gate<<<grid, 256, 0, st>>>(reinterpret_cast<double2*>(psi), npairs, g, target, cmask, cvals);
+  if ((rows & 3u) == 0u) return cudaSuccess;  // the identity
+  k_sv_gate<<<grid, 256, 0, st>>>(reinterpret_cast<double2*>(psi), npairs, g, target, cmask, cvals, rows);
   return cudaGetLastError();
 }
 

@@ -110,7 +110,7 @@ cudaError_t launch_copy_image(const Pool& P, unsigned long long chunk, uint8_t* 
 
 cudaError_t launch_sv_init(double* psi, unsigned long long amps, cudaStream_t st);
 cudaError_t launch_sv_gate(double* psi, int n, const GateCoef& g, int target, unsigned long long cmask,
-                           unsigned long long cvals, cudaStream_t st);
+                           unsigned long long cvals, uint32_t rows, cudaStream_t st);
 
 // Checkpoint: image lengths, gather of all images, and the rebuild of directory and
 // page arena from saved images (pages [0, used) in chunk order).

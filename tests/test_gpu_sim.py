@@ -298,14 +298,17 @@ def test_lossless_equals_exact_state():
 
 @pytest.mark.parametrize("n", [10, 16])
 def test_uncompressed_path_within_1e12(n):
-    gates = Cc.rcs_n(n, 8, seed=n)
-    psi = O.sv_init(n)
-    O.sv_run(psi, n, gates)
-    sv = qc().StateVector(n)
-    sv.apply_circuit(gates)
-    got = sv.amplitudes()
-    assert np.max(np.abs(got - psi)) <= 1e-12
-    assert np.array_equal(got, psi)
+    """The uncompressed comparator equals the oracle's state vector bit for bit: random
+    circuit (T and CZ leave one or three amplitudes of four untouched, which the kernel
+    neither reads nor writes), Grover (multi-controlled Z, X) and QAOA (RZ, CNOT, RX)."""
+    for gates in (Cc.rcs_n(n, 8, seed=n), Cc.grover(n, 2, seed=n)[0], Cc.qaoa_maxcut(n, 1, 3, seed=n)[0]):
+        psi = O.sv_init(n)
+        O.sv_run(psi, n, gates)
+        sv = qc().StateVector(n)
+        sv.apply_circuit(gates)
+        got = sv.amplitudes()
+        assert np.max(np.abs(got - psi)) <= 1e-12
+        assert np.array_equal(got, psi)
 
 
 def test_edge_shapes_and_controls():
