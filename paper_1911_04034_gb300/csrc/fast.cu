@@ -4,11 +4,12 @@
 // into shared-memory tiles, apply, encode, each step a CTA-wide pass with barriers.
 // For the case that dominates a lossy run -- both input chunks coded as STREAM at a
 // width S <= 32 and the output again a STREAM image at the gate's S <= 32 -- this
-// kernel gives a work item to one warp instead, which walks the two chunks in passes
-// of 256 values (8 per lane) and keeps every value in registers from the decoder
-// through the gate arithmetic to the encoder:
+// kernel gives a work item to a pair of warps instead, one chunk each; a warp walks its
+// chunk in passes of 256 values (8 per lane) and keeps every value in registers from
+// the decoder through the gate arithmetic to the encoder (a cross-chunk gate swaps the
+// partner values of each pass with the other warp through shared memory):
 //
-//   per pass: codes -> residual lengths -> warp scan of both chunks' offsets ->
+//   per pass: codes -> residual lengths -> warp scan of the offsets ->
 //             explicit parts from the staged input window -> warp scan of the
 //             leading bytes (Section 4.2, Solution C decoding) -> the 2x2 unitary on
 //             the amplitude pairs (Section 3.1, Eq. matrix1/matrix2) -> truncation to
@@ -27,8 +28,9 @@
 // constant, possibly periodic -- Section 4.2's period rule needs the whole chunk; a
 // chunk whose sampled values all equal their partners half a chunk away is left to
 // the general kernel, which runs the full test -- or holding a subnormal or non-finite
-// value) is appended to a device list before any of its state changes, and k_gate runs
-// the list right after this kernel.  Both kernels write the bytes the oracle writes.
+// value), or one whose chunk the learned selector granted a SPLIT / PALETTE trial, is
+// appended to a device list before any of its state changes, and k_gate runs the list
+// right after this kernel.  Both kernels write the bytes the oracle writes.
 #include "gate_common.cuh"
 
 namespace qc {
