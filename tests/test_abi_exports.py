@@ -64,3 +64,44 @@ def test_codec_entry_points_reject_sizes_that_would_wrap():
         assert lib.sim_codec_encode_ex(p, big, 10, 1e-4, -1, 0x1F, p, stride, p, 0) == qcsim.ERR_INVALID
         assert lib.sim_codec_decode(p, stride, p, big, 10, p, 0) == qcsim.ERR_INVALID
     assert lib.sim_codec_encode_noalloc(p, 1, 10, 1e-4, -1, p, (1 << 64) - 16, p) == qcsim.ERR_INVALID
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None, reason="nvcc not available to build the library")
+def test_entry_points_reject_bad_arguments_before_any_device_call():
+    """NULL handles and out-of-range settings are refused on the host (so this runs
+    without a GPU): sim_reset, sim_batch_apply, sim_set_selector and sim_autotune's lists
+    (a chunk size above 11, a ladder above 2, a mode set without Solution C's modes, an
+    empty list, a gate on a missing qubit)."""
+    import numpy as np
+
+    from paper_1911_04034_gb300 import build, circuits, qcsim
+
+    lib = ctypes.CDLL(build.build())
+    vp = ctypes.c_void_p
+    lib.sim_reset.argtypes = [vp]
+    lib.sim_batch_apply.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
+    lib.sim_set_selector.argtypes = [vp, ctypes.c_int, vp]
+    lib.sim_autotune.argtypes = [ctypes.c_int, ctypes.c_double, vp, ctypes.c_size_t, vp, ctypes.c_int, vp, ctypes.c_int,
+                                 vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_size_t, vp]
+    assert lib.sim_reset(None) == qcsim.ERR_INVALID
+    assert lib.sim_batch_apply(None, 1, None, None, 1) == qcsim.ERR_INVALID
+    assert lib.sim_set_selector(None, 2, None) == qcsim.ERR_INVALID
+    g = qcsim.gates_array(circuits.rcs_n(10, 2, seed=1))
+    best = qcsim.TunePoint()
+
+    def tune(bs, cs, ls, ms, gates=g, n=10):
+        arr = lambda t, v: (t * max(1, len(v)))(*v)
+        return lib.sim_autotune(n, 1e-4, vp(gates.ctypes.data), gates.shape[0],
+                                ctypes.cast(arr(ctypes.c_int32, bs), vp), len(bs),
+                                ctypes.cast(arr(ctypes.c_int32, cs), vp), len(cs),
+                                ctypes.cast(arr(ctypes.c_int32, ls), vp), len(ls),
+                                ctypes.cast(arr(ctypes.c_uint32, ms), vp), len(ms), ctypes.byref(best), None, 0, None)
+
+    assert tune([10], [12], [0], [0x1F]) == qcsim.ERR_INVALID
+    assert tune([10], [8], [3], [0x1F]) == qcsim.ERR_INVALID
+    assert tune([10], [8], [0], [0x0F]) == qcsim.ERR_INVALID
+    assert tune([10], [8], [0], [0x80 | 0x1F]) == qcsim.ERR_INVALID
+    assert tune([], [8], [0], [0x1F]) == qcsim.ERR_INVALID
+    bad = g.copy()
+    bad[0]["target"] = 10
+    assert tune([10], [8], [0], [0x1F], gates=bad) == qcsim.ERR_INVALID
