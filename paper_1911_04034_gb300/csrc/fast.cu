@@ -372,23 +372,23 @@ __device__ __forceinline__ double2 real_rows(const double* cf, double2 a, double
 // sqrt(Y)): every product of the chains above is exact, so each chain equals 2^k times
 // the chain of the signed inputs in the same order (scaling by a power of two commutes
 // with rounding while no partial sum leaves the normal range): three additions per
-// output part, then the scale added to the exponent field.  An input below 2^-959 could
-// put a partial sum out of the normal range: such an item goes to the general kernel,
-// as does an output out of range.  Bit q of L.sgn is the sign of coefficient cf[q].
+// output part, then the scale added to the exponent field.  The inputs are checked
+// once per pass (an item holding a value below 2^-959 goes to the general kernel), and
+// then no partial sum leaves the normal range: inputs of at least 2^-959 truncated to at
+// most 20 mantissa bits are multiples of 2^-979, so a nonzero sum is at least that, and
+// 2^k <= 1.  Only an overflow to infinity is left to catch.  Bit q of L.sgn is the sign
+// of coefficient cf[q].
 __device__ __forceinline__ void signed_rows(const GateLaunch& L, uint32_t r, uint32_t ar, uint32_t ai, uint32_t br,
                                             uint32_t bi, uint32_t mh, uint32_t& outr, uint32_t& outi, bool& spec) {
   const uint32_t sg = L.sgn >> (8u * r);
   auto t = [&](int q, uint32_t h) { return hi_as_double(h ^ ((sg >> q) << 31)); };
-  auto tiny = [](uint32_t h) { return (h & 0x7fffffffu) != 0u && (h & 0x7ff00000u) < (64u << 20); };
-  spec |= tiny(ar) || tiny(ai) || tiny(br) || tiny(bi);
   const double re = __dadd_rn(__dadd_rn(__dadd_rn(t(0, ar), t(1, ai)), t(2, br)), t(3, bi));
   const double im = __dadd_rn(__dadd_rn(__dadd_rn(t(4, ai), t(5, ar)), t(6, bi)), t(7, br));
   auto scaled = [&](double y) -> uint32_t {
     const uint64_t u = (uint64_t)__double_as_longlong(y);
-    const uint32_t hi = (uint32_t)(u >> 32), e = (hi >> 20) & 0x7ffu;
+    const uint32_t hi = (uint32_t)(u >> 32);
     if ((hi & 0x7fffffffu) == 0u && (uint32_t)u == 0u) return 0u;
-    const int es = (int)e + L.sk;
-    spec |= e == 0u || e == 0x7ffu || es < 1 || es > 2046;
+    spec |= (hi & 0x7ff00000u) == 0x7ff00000u;
     return (hi + ((uint32_t)L.sk << 20)) & mh;
   };
   outr = scaled(re);
@@ -580,6 +580,12 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
       const uint32_t Pl = lead_scan_warp(W, lead, after);
       lead = after;
       fast_rebuild(v, cw, Pl);
+    }
+    if constexpr (ARITH == 4) {
+      // signed_rows needs every input at least 2^-959 (or zero): each warp checks its own
+      // values, and the pair's agreement defers the item if either chunk has one below
+#pragma unroll
+      for (int k = 0; k < 8; ++k) spec |= ((v[k] & 0x7fffffffu) - 1u) < ((64u << 20) - 1u);  // nonzero, exponent < 64
     }
     ph.mark(1);
     // the gate on every amplitude pair whose in-chunk control bits match; results
