@@ -47,13 +47,12 @@ ROWS, COLS, BLOCK_LOG2, CHUNK_LOG2, SEED = 5, 6, 20, 10, 2024  # defaults; --row
 # DRAM traffic of a gate's launches from the last ncu capture, with the hash of the kernel
 # sources it applies to.  A 30-qubit launch is too large to capture, so the capture ran the
 # 26-qubit 2 x 13 grid in its steady state (k_gate_fast launches 801-804, every item on the
-# streaming kernel): dram__bytes_read.sum + dram__bytes_write.sum = 831 MB per launch
-# against 860.5 MB of image bytes per gate, a ratio of 0.966 (reads 447 MB: the input
+# streaming kernel): dram__bytes_read.sum + dram__bytes_write.sum = 832 MB per launch
+# against 860.5 MB of image bytes per gate, a ratio of 0.968 (reads 447 MB: the input
 # images plus directory entries; writes 384 MB, the rest of the output images still dirty
 # in L2 when the launch ends); traffic scales with the image bytes, so a 30-qubit gate's
-# traffic is that ratio times its image bytes.  (Taken on sources that differ from the
-# hashed ones only by a comment of fast.cu.)
-NCU_TRAFFIC = {"ratio_to_image_bytes": 0.966, "source_sha": "9185bb72595b1c8b"}
+# traffic is that ratio times its image bytes.
+NCU_TRAFFIC = {"ratio_to_image_bytes": 0.968, "source_sha": "4880ea788b2bc48a"}
 
 
 def kernel_sha() -> str:
