@@ -69,7 +69,6 @@ class _Stats(C.Structure):
         ("guard_fit", C.c_int32),
         ("pad", C.c_int32),
         ("wide_images", C.c_uint64),
-        ("fallback_gates", C.c_uint64),
     ]
 
 
@@ -341,16 +340,9 @@ class CSim:
             raise OracleError(rc, "csim_amplitudes")
         return out
 
-    def set_modes(self, modes: int) -> None:
-        """Mode set of later gates (bit m = mode m; must contain 0x1F)."""
-        rc = lib().orc_csim_set_modes(self._h, int(modes))
-        if rc:
-            raise OracleError(rc, "csim_set_modes")
-
     def set_mlp(self, params_flat) -> None:
-        """Each chunk gets Solution C's modes plus the SPLIT / PALETTE trials the selector
-        network grants it (every mode on a gate under memory pressure); params_flat: the
-        network's 1864 parameters (bfloat16 values) in W1 b1 W2 b2 W3 b3 order."""
+        """Solution D is tried for a chunk only where the selector network says so;
+        params_flat: the network's 1864 parameters (bfloat16 values) in W1 b1 W2 b2 W3 b3 order."""
         v = np.ascontiguousarray(params_flat, dtype=np.float32)
         assert v.size == 1864
         lib().orc_csim_set_mlp(self._h, 1, _ptr(v, C.c_float))

@@ -44,7 +44,6 @@
 #define ORC_MODE_PALETTE 6
 #define ORC_NMODES 7
 #define ORC_DEFAULT_MODES 0x1F /* Solution C: ZERO..RAW; SPLIT (Solution D) and PALETTE on request */
-#define ORC_ALL_MODES 0x7F     /* every mode: the exhaustive trial */
 #define ORC_PALETTE_MAX 256    /* most distinct values a PALETTE image lists */
 
 /* Planted-mistake switch used only by the mutation tests: each nonzero value
@@ -778,7 +777,6 @@ typedef struct {
   int32_t guard_fit; /* guarded ladder: 1 if the last gate's level was chosen because its worst case fits */
   int32_t pad;
   uint64_t wide_images; /* images whose header says S = 64 */
-  uint64_t fallback_gates; /* gates the selector network left to the exhaustive trial (memory pressure) */
 } orc_stats;
 
 typedef struct {
@@ -793,7 +791,6 @@ typedef struct {
   double lb_sum, lb_prod;
   int guard_fit;
   uint64_t n64; /* images whose header says S = 64 */
-  uint64_t fallback_gates;
   uint8_t** img;
   uint32_t* len;
   int poisoned;
@@ -944,11 +941,6 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
   size_t A = (size_t)1 << kc, N = 2 * A;
   uint64_t hi_mask = g->ctrl_mask >> kc, hi_vals = g->ctrl_vals >> kc;
   controller(s, s->nchunks >> __builtin_popcountll(hi_mask & (s->nchunks - 1)), gate_is_wide(g));
-  /* Memory pressure (not from the paper): with the bound at its last level and E above
-   * three quarters of floor(tau * budget), the selector network gives way to the
-   * exhaustive trial of every mode, its fallback, for this gate. */
-  const int fallback = s->use_mlp && s->level == s->nlevels && 4 * s->E > 3 * s->thresh;
-  if (fallback) s->fallback_gates += 1;
   uint64_t lo_mask = g->ctrl_mask & (A - 1), lo_vals = g->ctrl_vals & (A - 1);
   uint64_t* x0 = (uint64_t*)malloc(N * 8);
   uint64_t* x1 = (uint64_t*)malloc(N * 8);
@@ -964,7 +956,7 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
         if ((i & lo_mask) != lo_vals) continue;
         apply_pair(g->u, d + 2 * i, d + 2 * (i | ((size_t)1 << t)));
       }
-      if (s->use_mlp) m0 = fallback ? ORC_ALL_MODES : mlp_mask(s->mlp, s->img[q], s->len[q], kc, g, s->S_cur);
+      if (s->use_mlp) m0 = mlp_mask(s->mlp, s->img[q], s->len[q], kc, g, s->S_cur);
       rc = csim_store(s, q, x0, m0);
     } else {
       uint64_t qb = (uint64_t)1 << (t - kc);
@@ -979,8 +971,8 @@ int orc_csim_apply(orc_csim* s, const orc_gate* g) {
         apply_pair(g->u, d0 + 2 * i, d1 + 2 * i);
       }
       if (s->use_mlp) {
-        m0 = fallback ? ORC_ALL_MODES : mlp_mask(s->mlp, s->img[q], s->len[q], kc, g, s->S_cur);
-        m1 = fallback ? ORC_ALL_MODES : mlp_mask(s->mlp, s->img[q1], s->len[q1], kc, g, s->S_cur);
+        m0 = mlp_mask(s->mlp, s->img[q], s->len[q], kc, g, s->S_cur);
+        m1 = mlp_mask(s->mlp, s->img[q1], s->len[q1], kc, g, s->S_cur);
       }
       rc = csim_store(s, q, x0, m0);
       if (!rc) rc = csim_store(s, q1, x1, m1);
@@ -1061,14 +1053,12 @@ void orc_csim_stats(const orc_csim* s, orc_stats* st) {
   st->level = s->level;
   st->guard_fit = s->guard_fit;
   st->wide_images = s->n64;
-  st->fallback_gates = s->fallback_gates;
 }
 
 uint64_t orc_csim_nchunks(const orc_csim* s) { return s->nchunks; }
 
-/* Selector for later gates: use_mlp = 0 keeps the mode set; 1 gives each chunk
- * Solution C's modes plus the trials the network (params, ORC_MLP_NPARAMS floats)
- * grants it, or every mode on a gate under memory pressure (see orc_csim_apply). */
+/* Selector for later gates: use_mlp = 0 keeps the mode set; 1 tries Solution D for a
+ * chunk only when the network (params, ORC_MLP_NPARAMS floats) says so. */
 int orc_csim_set_mlp(orc_csim* s, int use_mlp, const float* params) {
   s->use_mlp = use_mlp;
   if (use_mlp) memcpy(s->mlp, params, sizeof(s->mlp));

@@ -150,37 +150,3 @@ def test_features_c_equal_python_definition():
     # PALETTE one-hot, k = 2 -> 2 / 16, palette size 4 (0.5, -0.5, 0.25 and the zero imaginary parts)
     assert x[6] == 1.0 and x[10] == np.float32(2 / 16) and x[9] == np.float32(4 / (64 * 2048))
     assert x[11] == 1.0 and x[12] == 0.0 and x[13] == 1.0 and x[14] == 1.0 and x[15] == np.float32(26 / 64)
-
-
-def test_selector_gives_way_to_the_exhaustive_trial_under_memory_pressure():
-    """A network that grants no trial (zero output weights; biases: STREAM logit 10, SPLIT
-    and PALETTE -10, budget 1) leaves every chunk to Solution C until the bound is at its
-    last level and E is above three quarters of floor(tau * budget); each such gate runs
-    the exhaustive trial instead.  A second simulator that switches its mode set by hand
-    at exactly those gates (Solution C, else every mode) ends every gate with the same
-    images; the fallback covers some gates but not all."""
-    import oracle as O
-    from paper_1911_04034_gb300 import circuits as Cc
-
-    n, kc = 12, 7
-    gates, _ = Cc.grover(n, 3, seed=5)
-    p = M.init_params(0)
-    p["W3"] = np.zeros_like(p["W3"])
-    p["b3"] = np.array([0, 0, 0, 10.0, 0, -10.0, -10.0, 1.0], dtype=np.float32)
-    flat = M.bf16_round(M.flatten(p))
-    budget = (16 << n) // 3
-    a = O.CSim(n, n, kc, 1e-4, budget)
-    a.set_mlp(flat)
-    b = O.CSim(n, n, kc, 1e-4, budget)
-    flags = []
-    for g in gates:
-        before = a.stats()["fallback_gates"]
-        a.apply([g])
-        fb = a.stats()["fallback_gates"] - before
-        flags.append(fb)
-        b.set_modes(0x7F if fb else 0x1F)
-        b.apply([g])
-        assert [a.image(c) for c in range(a.nchunks)] == [b.image(c) for c in range(b.nchunks)]
-        if fb:
-            assert a.stats()["level"] == 1  # the last level of the jump ladder
-    assert flags[0] == 0 and 0 < sum(flags) < len(flags)
