@@ -537,6 +537,18 @@ __device__ __forceinline__ int fast_item(const GateLaunch& L, unsigned long long
     if ((mine | other) & 2u) return 2;
     if (!((mine & other) & 1u)) return 1;
   }
+  if constexpr (KIND == 0 && ARITH == 1) {
+    // A diagonal row that is an exact copy (T's and CZ's first row) leaves this chunk's
+    // values as they are; already coded at the gate's S, they would be re-encoded to the
+    // same bytes (truncation is idempotent, and the smallest-image choice sees the same
+    // values), so the image stays and the warp only joins the pair's final agreement
+    // (there are no meetings in between for a diagonal gate).
+    if (L.rop[side] == 1 && Sin == S) {
+      const uint32_t other = pair_agree(slots, seq, phase, side, 1u, P.ctl, 3u);
+      if (other & 2u) return 2;
+      return (other & 1u) ? 0 : 1;
+    }
+  }
   const uint32_t nbs = (ib - 16u - cb) >> 4;
   // the code word of this lane's values in pass p (image byte 16 + 64 p + 4 (lane / 2))
   auto code_word_at = [&](uint32_t p) -> uint32_t {
