@@ -146,7 +146,11 @@ sim_status sim_set_stream(sim_t* sim, void* cuda_stream);
 
 /* Applies one gate (Section 3.1).  Queued on the stream; device-side failures are
  * reported by this call only if they are already known, otherwise by the next
- * synchronising call. */
+ * synchronising call.  Kernels per gate: the selector's decisions (selector 2 only);
+ * at chunk sizes 2^7..2^11 and widths S <= 32 the streaming kernel (a warp pair per
+ * work item, STREAM images in and out); the general kernel over the items the
+ * streaming kernel left, or the whole gate; the bookkeeping kernel.  Every path writes
+ * the same bytes. */
 sim_status sim_apply_gate(sim_t* sim, const sim_gate* gate);
 
 /* Applies n_gates gates in order.  All gates are validated first (none runs if one
