@@ -345,3 +345,18 @@ def test_palette_corrupt_images_rejected():
     bad[16 + pa + 7] = 0xFF  # first index 0b111 = 7 >= P
     with pytest.raises(O.OracleError):
         O.decode_chunk(bytes(bad), 7)
+
+
+@pytest.mark.parametrize("kc", [2, 7, 10])
+def test_reencoding_at_the_same_width_is_the_identity(kc):
+    """Encoding the decoded values of an image again at the same S gives the same bytes
+    (truncation is idempotent and the smallest-image choice sees the same values).  The
+    streaming kernel relies on it to leave untouched a chunk whose gate row is an exact copy
+    when the chunk is already coded at the gate's S."""
+    rng = np.random.default_rng(40 + kc)
+    for name, a in _chunks(rng, kc):
+        for S in (19, 26, 32, 64):
+            for modes in (O.DEFAULT_MODES, O.ALL_MODES):
+                img = O.encode_chunk(a, kc, S, modes=modes)
+                again = O.encode_chunk(O.decode_chunk(img, kc), kc, S, modes=modes)
+                assert again == img, (name, S, modes)
